@@ -1,0 +1,398 @@
+#!/usr/bin/env python
+"""Benchmark of the KPM density-of-states path on GB300.
+
+One "step" is one pass of the whole path over the workload: spectrum bounds
+(Gershgorin) -> start vectors -> ceil(M/2) fused SpMM/recurrence/doubling-dot
+steps -> moments -> Jackson reconstruction on a 1000-point t-grid -> the
+sigma-smoothed L1/Linf error against a reference DOS.  The metric is Chebyshev
+moments per second, nnz * n_v * M / t_step.
+
+Default workload: 3-D Anderson model on a 64^3 periodic lattice (n = 262144,
+7 nonzeros per row), on-site disorder uniform in [-2, 2], hopping -1, seed 2;
+M = 500, n_v = 64, FP32 SpMM with FP64 moment accumulation (the FP64 form is
+measured too and reported under "forms").  Inputs are synthetic and seeded.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference]
+                    [--workload anderson64|laplacian40|chunglu|batched] [--precision f32|f64]
+
+Under torchrun (N > 1) every rank sweeps its own n_v start vectors (vector
+offset rank * n_v) -- weak scaling, no collective on the data path; the moments
+are combined once after timing with an all-reduce of M+1 doubles.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+# DRAM traffic per step-kernel launch measured by ncu (dram__bytes_read.sum +
+# dram__bytes_write.sum), keyed by (workload, precision) together with the
+# SHA-256 of the kernel source at capture time; a mismatch reports null.
+NCU_TRAFFIC = {}
+
+WORKLOADS = {
+    "anderson64": dict(kind="anderson", L=64, W=4.0, seed=2, M=500, n_v=64,
+                       desc="3-D Anderson 64^3 periodic, W=4 (eps ~ U[-2,2]), hopping -1, seed 2"),
+    "laplacian40": dict(kind="laplacian", m=40, M=100, n_v=20, seed=1,
+                        desc="2-D 5-point Dirichlet Laplacian 40x40"),
+    "chunglu": dict(kind="chunglu", n=4194304, beta=2.5, mean_deg=20.0, seed=3, M=1000,
+                    n_v=256, desc="normalized Laplacian of a Chung-Lu graph, n=4194304, "
+                              "beta=2.5, mean degree 20, seed 3"),
+    "batched": dict(kind="batched", count=512, seed=4, M=200, n_v=32,
+                    desc="512 Anderson lattices, L ~ U{10..40}, W ~ U[1,16], seed 4"),
+}
+
+
+def make_matrix(w):
+    from synthetic import anderson_3d, chung_lu_normalized_laplacian, laplacian_2d
+    if w["kind"] == "anderson":
+        return anderson_3d(w["L"], w["W"], w["seed"])
+    if w["kind"] == "laplacian":
+        return laplacian_2d(w["m"])
+    if w["kind"] == "chunglu":
+        return chung_lu_normalized_laplacian(w["n"], w["beta"], w["mean_deg"], w["seed"])
+    raise ValueError(w["kind"])
+
+
+def algorithmic_bytes_per_step(n, nnz, n_v, precision):
+    """Compulsory bytes of one fused step: CSR once (col_idx 4 B + value) plus
+    row_ptr, X_k read once, X_{k-1} read and X_{k+1} written."""
+    s = 8 if precision == "f64" else 4
+    return nnz * (4 + s) + 4 * (n + 1) + 3 * n * n_v * s
+
+
+def fma_per_step(n, nnz, n_v):
+    """FMAs of one fused step: nnz*n_v (SpMM) + 2 n n_v (shift, recurrence) + 2 n n_v (dots)."""
+    return nnz * n_v + 4 * n * n_v
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            return json.load(f), "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle-reason samples while running."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id: str):
+        self.gpu_id = gpu_id
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", self.gpu_id, f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for name, val in zip(names, parts[4:8]):
+                if val.lower().startswith("active"):
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def gpu_id_for(device):
+    import torch
+    try:
+        u = torch.cuda.get_device_properties(device).uuid
+        return "GPU-" + str(u)
+    except Exception:
+        return str(device)
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    with open(os.path.join(ROOT, "paper_1308_5467_gb300", "csrc", "kpm_kernels.cu"), "rb") as f:
+        h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def cpu_baseline(A, lb, ub, M, n_v_full, seed, target_s=12.0):
+    """The oracle as it stands, on the host cores, over a bounded sample:
+    the same matrix and M, a number of start vectors sized for ~target_s."""
+    from oracle import kpm as okpm
+    cores = os.cpu_count() or 1
+    probe = max(1, min(cores, n_v_full))
+    t0 = time.perf_counter()
+    okpm.kpm_moments_per_vector(A, lb, ub, M, probe, seed, nthreads=cores)
+    t_probe = time.perf_counter() - t0
+    nv = probe
+    if t_probe < target_s / 2:
+        nv = int(min(max(probe, probe * target_s / max(t_probe, 1e-3)), 4 * n_v_full))
+        nv = max(probe, (nv // cores) * cores if nv >= cores else nv)
+    t0 = time.perf_counter()
+    okpm.kpm_moments_per_vector(A, lb, ub, M, nv, seed, nthreads=cores)
+    t = time.perf_counter() - t0
+    value = A.nnz * nv * M / t
+    return {"value": value, "unit": "moments/s", "cores": min(cores, nv), "kind": "oracle",
+            "sample": f"{nv} start vectors of the same workload (M={M}, doubling mode, FP64), "
+                      f"{t:.1f} s wall on {min(cores, nv)} threads"}
+
+
+def run_reference(args):
+    """The reference arm: the CPU oracle, timed as it stands on the host cores."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    w = WORKLOADS[args.workload]
+    if w["kind"] == "batched":
+        print(json.dumps({"impl": "reference", "unavailable": "batched workload has no oracle arm"}))
+        return 0
+    from oracle import bounds as obounds
+    from oracle import kpm as okpm
+    A = make_matrix(w)
+    if args.precision == "f32":
+        A = A.astype(np.float32)
+    lb, ub = obounds.bounds(A, "gershgorin", pad_frac=0.01)
+    M = w["M"]
+    cores = os.cpu_count() or 1
+    nv = max(1, min(cores, w["n_v"]))
+    for _ in range(args.warmup if args.warmup <= 1 else 1):
+        okpm.kpm_moments_per_vector(A, lb, ub, min(M, 20), nv, w["seed"], nthreads=cores)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        okpm.kpm_moments_per_vector(A, lb, ub, M, nv, w["seed"], nthreads=cores)
+        times.append(time.perf_counter() - t0)
+    t = sum(times) / len(times)
+    value = A.nnz * nv * M / t
+    sample = (f"each step: {nv} of the {w['n_v']} start vectors of {args.workload} "
+              f"(M={M}, FP64 oracle, doubling mode) on {min(cores, nv)} host threads")
+    line = {"metric": "Chebyshev moments/sec (nnz*n_v*M/s)", "value": value,
+            "unit": "moments/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * t, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": args.workload, "n": A.n, "nnz": A.nnz, "M": M,
+                       "n_v": w["n_v"], "n_v_sample": nv},
+            "impl": "reference",
+            "cpu_baseline": {"value": value, "unit": "moments/s", "cores": min(cores, nv),
+                             "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": "moments/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--workload", default="anderson64", choices=sorted(WORKLOADS))
+    ap.add_argument("--precision", default="f32", choices=["f32", "f64"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-f64-form", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    import torch.distributed as dist
+
+    from paper_1308_5467_gb300 import dos
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    device = torch.device("cuda", local)
+
+    w = WORKLOADS[args.workload]
+    if w["kind"] == "batched":
+        raise SystemExit("the batched workload is benchmarked by --workload batched in a later step")
+    A = make_matrix(w)
+    M, n_v, seed = w["M"], w["n_v"], w["seed"]
+    prec = args.precision
+    vdtype = np.float32 if prec == "f32" else np.float64
+    Ad = dos.CSRArrays.from_synthetic(A, device=device, dtype=vdtype)
+    Ad64 = dos.CSRArrays.from_synthetic(A, device=device, dtype=np.float64)
+    ctx = dos.Context(local)
+    vec_offset = rank * n_v
+
+    lb, ub = ctx.dos_bounds(Ad, "gershgorin", pad_frac=0.01)
+    sigma = 0.02 * (ub - lb)
+    # reference DOS for the smoothed error: FP64 sweep with 1024 independent vectors
+    ref_mu = ctx.dos_kpm_moments(Ad64, lb, ub, M, 1024, seed=seed + 1000, precision="f64",
+                                 vec_offset=0)
+
+    def step(Acsr, precision, host=False):
+        lo, hi = ctx.dos_bounds(Acsr, "gershgorin", pad_frac=0.01)
+        mu = ctx.dos_kpm_moments(Acsr, lo, hi, M, n_v, seed=seed, precision=precision,
+                                 vec_offset=vec_offset)
+        phi = ctx.dos_reconstruct(mu, M, "jackson", lo, hi, N_t=1000)
+        e1, einf = ctx.dos_smoothed_error(mu, M, "jackson", lo, hi, sigma, ref_mu=ref_mu)
+        return mu, phi, e1, einf
+
+    def timed(fn, steps, warmup, profile=False):
+        for _ in range(warmup):
+            fn()
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+        if profile:
+            ctx.dos_profile_enable(True)
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        ev0.record()
+        out = None
+        for _ in range(steps):
+            out = fn()
+        ev1.record()
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+        ms = ev0.elapsed_time(ev1) / steps
+        prof = ctx.dos_profile_read() if profile else None
+        if profile:
+            ctx.dos_profile_enable(False)
+        if world > 1:
+            t = torch.tensor([ms], device=device, dtype=torch.float64)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms = float(t.item())
+        return ms, out, prof
+
+    with ClockSampler(gpu_id_for(local)) as clk:
+        ms, out, prof = timed(lambda: step(Ad, prec), args.steps, args.warmup, profile=True)
+    mu, phi, e1, einf = out
+    units = A.nnz * n_v * M
+    value = units * world / (ms * 1e-3)
+
+    # roofline of the dominant kernel (the fused step)
+    peaks, peak_kind = measured_peaks()
+    launch_ms = prof["step_ms"] / max(1, prof["step_launches"])
+    if prec == "f32":
+        alg = algorithmic_bytes_per_step(A.n, A.nnz, n_v, prec)
+        achieved = alg / (launch_ms * 1e-3) / 1e9
+        key = (args.workload, prec)
+        tr = NCU_TRAFFIC.get(key)
+        traffic = tr["bytes"] if tr and tr["src"] == kernel_source_hash() else None
+        roofline = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"],
+                    "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"], "traffic": traffic,
+                    "peak_source": peak_kind, "kernel": "step_kernel<float>",
+                    "algorithmic_bytes_per_launch": alg, "launch_ms": launch_ms}
+    else:
+        flops = 2 * fma_per_step(A.n, A.nnz, n_v)
+        achieved = flops / (launch_ms * 1e-3) / 1e12
+        roofline = {"bound": "alu", "achieved": achieved, "peak": 1.25, "unit": "TFLOP/s",
+                    "frac": achieved / 1.25, "traffic": None,
+                    "peak_source": "nominal FP64 rate of GB300 (1.25 TFLOP/s)",
+                    "kernel": "step_kernel<double>", "flops_per_launch": flops,
+                    "launch_ms": launch_ms}
+
+    forms = {prec: {"ms_per_step": ms, "value": value, "e1": e1, "einf": einf}}
+    if not args.no_f64_form and prec == "f32":
+        ms64, out64, prof64 = timed(lambda: step(Ad64, "f64"), max(3, args.steps // 4), 1,
+                                    profile=True)
+        l64 = prof64["step_ms"] / max(1, prof64["step_launches"])
+        fl = 2 * fma_per_step(A.n, A.nnz, n_v)
+        forms["f64"] = {"ms_per_step": ms64, "value": units * world / (ms64 * 1e-3),
+                        "e1": out64[2], "einf": out64[3],
+                        "roofline": {"bound": "alu", "achieved": fl / (l64 * 1e-3) / 1e12,
+                                     "peak": 1.25, "unit": "TFLOP/s",
+                                     "frac": fl / (l64 * 1e-3) / 1e12 / 1.25,
+                                     "launch_ms": l64},
+                        "max_abs_diff_vs_f32": float(np.abs(out64[0] - mu).max())}
+
+    e2e = None
+    if not args.no_e2e:
+        # host (pinned) CSR arrays: the library copies them to the device inside each call
+        rp = torch.from_numpy(A.row_ptr).pin_memory()
+        ci = torch.from_numpy(A.col_idx).pin_memory()
+        va = torch.from_numpy(A.val.astype(vdtype)).pin_memory()
+        Ah = dos.CSRArrays(A.n, rp, ci, va)
+        ms_e2e, _, _ = timed(lambda: step(Ah, prec, host=True), max(3, args.steps // 2), 1)
+        h2d = 2 * (rp.numel() * 4 + ci.numel() * 4 + va.numel() * va.element_size())
+        d2h = 8 * (M + 1) + 8 * 1000 + 8 * 2 + 16
+        e2e = {"value": units * world / (ms_e2e * 1e-3), "unit": "moments/s",
+               "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms_per_step": ms_e2e}
+
+    if world > 1:
+        t = torch.from_numpy(mu).to(device)
+        dist.all_reduce(t)
+        mu_all = (t / world).cpu().numpy()
+        del mu_all
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(A.astype(vdtype), lb, ub, M, n_v, seed)
+
+    if rank == 0:
+        line = {
+            "metric": "Chebyshev moments/sec (nnz*n_v*M/s)",
+            "value": value, "unit": "moments/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32+f64acc" if prec == "f32" else "f64", "data": "synthetic",
+            "config": {"workload": args.workload, "desc": w["desc"], "n": A.n, "nnz": A.nnz,
+                       "M": M, "n_v": n_v, "precision": prec,
+                       "l2": "inputs larger than L2: %.0f MB touched per fused step"
+                             % (algorithmic_bytes_per_step(A.n, A.nnz, n_v, prec) / 1e6),
+                       "sigma": sigma, "lb": lb, "ub": ub},
+            "dos_per_s": 1e3 / ms, "e1": e1, "einf": einf,
+            "roofline": roofline, "forms": forms, "e2e": e2e, "cpu_baseline": cpu,
+            "gpu_launches": prof["launches"], "clocks": clk.summary(),
+        }
+        print(json.dumps(line))
+    ctx.close()
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

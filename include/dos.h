@@ -1,0 +1,283 @@
+/*
+ * dos.h -- C ABI of libdos, a GB300 (sm_103a) library for the Kernel
+ * Polynomial Method (KPM) estimate of the density of states (DOS) of a large
+ * sparse real symmetric matrix, after Lin, Saad and Yang, "Approximating
+ * spectral densities of large matrices" (SIAM Review 58(1), 2016;
+ * arXiv:1308.5467).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - Every function returns an int status: DOS_OK (0) or one of the DOS_E*
+ *    codes below.  dos_last_error(ctx) gives a one-line message for the last
+ *    failure on that context.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = the legacy default
+ *    stream).  Work is queued on it; the functions that return results in host
+ *    memory, or that must check a device-side status, synchronise the stream
+ *    before returning (each function says which).
+ *  - Buffers are owned by the caller; the library never frees caller memory.
+ *    Scratch (vector blocks, partial sums, staging copies) is owned by the
+ *    context, allocated on first use and grown on demand; a context is not
+ *    thread-safe: use one context per host thread.
+ *  - Output arrays documented as "host or device" may be either: the library
+ *    asks the CUDA runtime which kind of memory the pointer refers to.
+ *  - Matrices are CSR with int32 row pointers and column indices (so nnz <
+ *    2^31), column indices sorted or not, FP64 or FP32 values.  A matrix must
+ *    be symmetric for the method to make sense; symmetry is not checked.
+ *    Structural validity (row_ptr[0] = 0, row_ptr non-decreasing,
+ *    row_ptr[n] = nnz, 0 <= col_idx < n) IS checked on the device before any
+ *    kernel reads through the indices; a failure returns DOS_EINVAL.
+ *  - Start vectors (Theorem 3.1: E[v] = 0, E[v v^T] = I) are Rademacher +-1
+ *    entries.  Entry (row i, vector l) of matrix b is bit (l mod 64) of the
+ *    64-bit splitmix64 output number ctr+1 of the stream seeded with `seed`,
+ *    ctr = b*2^48 + floor(l/64)*2^32 + i  (0 -> +1, 1 -> -1).  Results are
+ *    therefore reproducible for a given (seed, matrix, n_v).
+ */
+#ifndef DOS_H
+#define DOS_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ---------------------------------------------------------- */
+#define DOS_OK 0
+#define DOS_EINVAL 1     /* bad argument, or a CSR that fails validation */
+#define DOS_ENOMEM 2     /* device or host allocation failed */
+#define DOS_ECUDA 3      /* a CUDA runtime call failed (message in dos_last_error) */
+#define DOS_ESPECTRUM 4  /* |mu_k| > mu_0 (1 + tol) or a non-finite moment: the
+                            bounds did not enclose the spectrum (Section 3.1:
+                            T_k(B) v_0 then grows exponentially) */
+#define DOS_ETIMEOUT 5   /* a bounded device-side wait ran out */
+
+/* ---- enumerations ---------------------------------------------------------- */
+#define DOS_F64 0               /* value / vector element type */
+#define DOS_F32 1
+
+#define DOS_DEVICE 0            /* where a dos_csr's arrays live */
+#define DOS_HOST 1
+
+#define DOS_PREC_F64 0          /* values, vectors, products and dot products in FP64 */
+#define DOS_PREC_F32_ACC64 1    /* values, vectors and the recurrence in FP32; each
+                                   moment dot product formed from exact FP32 products,
+                                   accumulated per thread as an unevaluated float pair
+                                   (about 2^-48 relative) and summed across threads and
+                                   blocks, and stored, in FP64 */
+
+#define DOS_BOUNDS_GERSHGORIN 0 /* disc bound, one pass over the matrix */
+#define DOS_BOUNDS_LANCZOS 1    /* k-step Lanczos with residual bounds (Section 3.1) */
+
+#define DOS_DAMP_NONE 0         /* plain truncated expansion, Eq. tdosFinal */
+#define DOS_DAMP_JACKSON 1      /* Jackson damping factors, Appendix A Eq. jackson */
+
+/* flags of dos_kpm_opts.flags */
+#define DOS_OPT_NO_VALIDATE 1u      /* skip the CSR structure check (caller vouches) */
+#define DOS_OPT_NO_SPECTRUM_CHECK 2u/* do not synchronise to check |mu_k| <= mu_0 */
+#define DOS_OPT_NO_GRAPH 4u         /* launch the sweep kernel by kernel instead of
+                                       replaying a cached CUDA graph */
+#define DOS_OPT_AUTOTUNE 8u         /* time the candidate launch shapes on this matrix
+                                       once and cache the fastest (see dos_tune) */
+
+typedef struct dos_ctx dos_ctx;
+
+/* A CSR matrix descriptor.  `location` says whether the three arrays are in
+ * device memory (used in place) or host memory (copied to context-owned device
+ * memory inside the call, on `stream`). */
+typedef struct {
+    int64_t n;               /* rows = columns, >= 1 */
+    int64_t nnz;             /* nonzeros, < 2^31 */
+    const int32_t *row_ptr;  /* n + 1 entries */
+    const int32_t *col_idx;  /* nnz entries */
+    const void *val;         /* nnz entries of type `dtype` */
+    int32_t dtype;           /* DOS_F64 or DOS_F32 */
+    int32_t location;        /* DOS_DEVICE or DOS_HOST */
+} dos_csr;
+
+/* Launch shape of the fused sweep kernel.  Zero fields mean "choose". */
+typedef struct {
+    int32_t team;            /* threads that share one matrix row (1..32, power of 2) */
+    int32_t chunks;          /* 16-byte vector chunks per thread (1, 2, 4 or 8) */
+    int32_t block;           /* threads per block (64..1024, multiple of 32) */
+    int32_t tiles;           /* row tiles = blocks per sweep step */
+} dos_launch;
+
+/* Optional arguments of the _ex / _batched entry points (NULL = defaults). */
+typedef struct {
+    uint32_t flags;          /* DOS_OPT_* */
+    int64_t vec_offset;      /* first start-vector index l (default 0): a run with
+                                vec_offset = o and n_v = k computes exactly vectors
+                                o..o+k-1 of a larger run, so runs can be sharded */
+    uint64_t batch_index;    /* matrix index b used by the start-vector counter
+                                (single-matrix calls; default 0) */
+    dos_launch launch;       /* launch shape override (zeros = autotuned/default) */
+} dos_kpm_opts;
+
+/* ---- context --------------------------------------------------------------- */
+
+/* Create a context bound to CUDA device `device`; it owns all scratch memory.
+ * Errors: DOS_EINVAL (ctx NULL or no such device), DOS_ENOMEM, DOS_ECUDA. */
+int dos_ctx_create(dos_ctx **ctx, int device);
+
+/* Free the context and all scratch memory it owns (synchronises the device).
+ * NULL is accepted. */
+int dos_ctx_destroy(dos_ctx *ctx);
+
+/* Message for the last failure on `ctx` (never NULL; "" if none). */
+const char *dos_last_error(const dos_ctx *ctx);
+
+/* Short name of a status code ("DOS_OK", "DOS_EINVAL", ...). */
+const char *dos_status_string(int status);
+
+/* Kernel timing.  While enabled, every sweep records CUDA events on its stream
+ * just before its first and just after its last fused-step launch (per vector
+ * panel) and adds the elapsed time and the number of step launches to the
+ * context's counters; each sweep then synchronises its stream at the end.
+ * dos_profile_enable resets the counters.  The paper has no counterpart: this
+ * is measurement plumbing. */
+int dos_profile_enable(dos_ctx *ctx, int on);
+/* step_ms: summed event time over the step launches; step_launches: how many;
+ * sweeps: how many sweeps contributed; launches: all kernel launches issued by
+ * the library since enabling.  Any pointer may be NULL. */
+int dos_profile_read(dos_ctx *ctx, double *step_ms, int64_t *step_launches, int64_t *sweeps,
+                     int64_t *launches);
+
+/* Check a CSR's structure on the device (see the conventions above); returns
+ * DOS_OK or DOS_EINVAL.  Synchronises `stream`. */
+int dos_validate_csr(dos_ctx *ctx, const dos_csr *A, void *stream);
+
+/* ---- step a2: start vectors ------------------------------------------------ */
+/*
+ * Write the n x n_v block of Rademacher start vectors that dos_kpm_moments
+ * uses (Theorem 3.1's E[v] = 0, E[v v^T] = I; Algorithm 1 "select a new random
+ * vector"), row-major out[i*n_v + l] = entry (row i, vector vec_offset + l) of
+ * matrix batch_index, as +1/-1 in `dtype` (DOS_F64 or DOS_F32).  out: host or
+ * device.  Synchronises `stream` when out is host memory.
+ * Errors: DOS_EINVAL, DOS_ENOMEM, DOS_ECUDA.
+ */
+int dos_start_vectors(dos_ctx *ctx, int64_t n, int n_v, uint64_t seed, uint64_t batch_index,
+                      int64_t vec_offset, int dtype, void *out, void *stream);
+
+/* ---- step a1: spectrum bounds ---------------------------------------------- */
+/*
+ * Lower and upper bounds lb <= lambda_min(A), ub >= lambda_max(A) for the
+ * shift/scale of Eq. cd (Section 3.1), each widened by pad_frac * (ub - lb).
+ *   method DOS_BOUNDS_GERSHGORIN: min/max over rows of a_ii -+ sum_{j!=i}|a_ij|
+ *          (`steps`, `seed` unused).
+ *   method DOS_BOUNDS_LANCZOS: `steps`-step Lanczos (1 <= steps <= 512, stops
+ *          early at an invariant subspace) from the normalised start vector
+ *          l = 0 of `seed`; lb = theta_min - ||f|| |y_min(last)|,
+ *          ub = theta_max + ||f|| |y_max(last)| with f the Lanczos residual and
+ *          y the unit Ritz vectors of the tridiagonal T_k (Eq. lanfact).  The
+ *          paper notes this is a heuristic (not a guaranteed enclosure), hence
+ *          the pad.  Runs in FP64 whatever the value dtype.
+ * lb, ub: host pointers.  Synchronises `stream`.
+ * Errors: DOS_EINVAL (bad args/CSR), DOS_ENOMEM, DOS_ECUDA.
+ */
+int dos_bounds(dos_ctx *ctx, const dos_csr *A, int method, int steps, uint64_t seed,
+               double pad_frac, double *lb, double *ub, void *stream);
+
+/* ---- steps a2-a5: the Chebyshev moment sweep ------------------------------- */
+/*
+ * Stochastic Chebyshev moments of B = (A - cI)/d, c = (lb+ub)/2, d = (ub-lb)/2
+ * (Eq. cd), for k = 0..M:
+ *     mu_k = (1/(n n_v)) sum_{l=0}^{n_v-1} v_l^T T_k(B) v_l
+ * (Eqs. expmu, nuk, muEst without the factor (2 - delta_k0)/pi, which
+ * dos_reconstruct applies; so mu_0 = 1).  The recurrence v_{k+1} = 2 B v_k -
+ * v_{k-1}, v_1 = B v_0 (Eq. 3term, Algorithm 1) runs on all n_v vectors at
+ * once as a block SpMM, fused in one pass over A with the shift/scale and with
+ * the dot products of the doubling identity (Appendix A, sign corrected):
+ *     mu_{2k}   = 2 v_k^T v_k / n     - mu_0,
+ *     mu_{2k+1} = 2 v_{k+1}^T v_k / n - mu_1,
+ * so ceil(M/2) passes over A give all M+1 moments.
+ *   M: degree, 0 <= M <= 100000.  n_v: vectors, 1 <= n_v <= 4096.
+ *   precision: DOS_PREC_F64 (needs A->dtype == DOS_F64) or DOS_PREC_F32_ACC64
+ *      (an FP64 matrix is rounded to FP32 on the device first).
+ *   mu: M+1 doubles, host or device.
+ *   mu_per_vec: NULL, or n_v*(M+1) doubles, host or device: the moments of
+ *      each start vector, mu_per_vec[l*(M+1) + k] = v_l^T T_k(B) v_l / n.
+ * Synchronises `stream` (to read the status) unless DOS_OPT_NO_SPECTRUM_CHECK
+ * is set and both outputs are device memory.
+ * Errors: DOS_EINVAL, DOS_ENOMEM, DOS_ECUDA, DOS_ESPECTRUM (moments are still
+ * written).
+ */
+int dos_kpm_moments(dos_ctx *ctx, const dos_csr *A, double lb, double ub, int M, int n_v,
+                    uint64_t seed, int precision, double *mu, double *mu_per_vec, void *stream);
+
+/* dos_kpm_moments with options (vector offset for sharding, launch shape, flags). */
+int dos_kpm_moments_ex(dos_ctx *ctx, const dos_csr *A, double lb, double ub, int M, int n_v,
+                       uint64_t seed, int precision, double *mu, double *mu_per_vec,
+                       const dos_kpm_opts *opts, void *stream);
+
+/*
+ * Batched sweep: B independent matrices of uneven size advanced together, one
+ * kernel launch per Chebyshev step for all of them (the step sequence is
+ * captured once in a CUDA graph and replayed).  The matrices are concatenated
+ * row-wise in one CSR descriptor: A->row_ptr is global and non-decreasing over
+ * all rows, A->col_idx is LOCAL to each matrix (0 <= col < n_b), A->n is the
+ * total row count.  seg_rows (host, B+1 int64) gives the first row of each
+ * matrix (seg_rows[0] = 0, seg_rows[B] = A->n, every n_b >= 1).  lb, ub: host
+ * arrays of B bounds.  Matrix b uses start vectors with counter field b.
+ * mu: B*(M+1) doubles (host or device), mu[b*(M+1) + k].
+ * mu_per_vec: NULL or B*n_v*(M+1) doubles, [(b*n_v + l)*(M+1) + k].
+ * Synchronises `stream`.  Errors as dos_kpm_moments.
+ */
+int dos_kpm_moments_batched(dos_ctx *ctx, const dos_csr *A, int B, const int64_t *seg_rows,
+                            const double *lb, const double *ub, int M, int n_v, uint64_t seed,
+                            int precision, double *mu, double *mu_per_vec,
+                            const dos_kpm_opts *opts, void *stream);
+
+/*
+ * Autotuner: time each candidate launch shape of the fused sweep kernel for a
+ * few steps on this matrix (and segment layout, B >= 1; seg_rows as in
+ * dos_kpm_moments_batched, NULL when B == 1) and cache the fastest in the
+ * context under the key (total rows, nnz, B, n_v, precision).  Later sweeps
+ * with the same key use it unless a launch override is given.  `best`
+ * (host, may be NULL) receives the choice; `best_ms` (may be NULL) its time per
+ * step.  Synchronises `stream`.
+ */
+int dos_tune(dos_ctx *ctx, const dos_csr *A, int B, const int64_t *seg_rows, int n_v,
+             int precision, dos_launch *best, double *best_ms, void *stream);
+
+/* ---- step a6: reconstruction ----------------------------------------------- */
+/*
+ * DOS on a t-grid from moments normalised as above (Eq. tdosFinal with the
+ * coefficients of Eq. expmu, and, for DOS_DAMP_JACKSON, the factors g_k^M of
+ * Appendix A Eq. jackson):
+ *     phi_hat(t) = [g_0 mu_0 + 2 sum_{k=1}^M g_k mu_k T_k(t)] / (pi sqrt(1 - t^2)),
+ * and in eigenvalue units phi(lambda) = phi_hat((lambda - c)/d) / d.
+ *   mu: M+1 doubles (host or device).  t: N_t points in (-1, 1) (host or
+ *   device) or NULL for the Chebyshev nodes t_i = -cos(pi (i + 1/2) / N_t).
+ *   phi_hat: N_t doubles (host or device).  phi_lambda: NULL or N_t doubles,
+ *   which needs ub > lb.
+ * Computed on the device in FP64.  Synchronises `stream` when an output is host
+ * memory.  Errors: DOS_EINVAL, DOS_ENOMEM, DOS_ECUDA.
+ */
+int dos_reconstruct(dos_ctx *ctx, const double *mu, int M, int damping, double lb, double ub,
+                    const double *t, int N_t, double *phi_hat, double *phi_lambda, void *stream);
+
+/* ---- step a7: accuracy metric ---------------------------------------------- */
+/*
+ * Error of the KPM DOS at resolution sigma (eigenvalue units), in the paper's
+ * metric: both densities blurred by the Gaussian g_sigma (Eq. gauss), the
+ * reference as phi_sigma(x) = (1/n) sum_j g_sigma(x - lambda_j) (Eq. blurphi
+ * with the 1/n of Eq. DOS0), the KPM DOS as <phi_tilde, g_sigma(. - x)>
+ * evaluated by Gauss-Chebyshev quadrature on N_q = max(4(M'+1), ceil(40 d /
+ * sigma)) nodes (M' = max(M, M_ref)).  On a uniform grid of N_x points over
+ * [lb - 6 sigma, ub + 6 sigma]:
+ *     err_l1  = trapezoid integral of |difference|   (Eq. err2, p = 1),
+ *     err_inf = max |difference|                      (Eq. errormetric).
+ * Reference: `eig` (n_eig exact eigenvalues, host or device) if not NULL,
+ * else `ref_mu` (M_ref+1 moments for the same lb, ub, with damping
+ * ref_damping).  N_x in [2, 10^6].  err_l1, err_inf: host pointers (either may
+ * be NULL).  Synchronises `stream`.
+ */
+int dos_smoothed_error(dos_ctx *ctx, const double *mu, int M, int damping, double lb, double ub,
+                       const double *eig, int64_t n_eig, const double *ref_mu, int M_ref,
+                       int ref_damping, double sigma, int N_x, double *err_l1, double *err_inf,
+                       void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* DOS_H */

@@ -1,0 +1,906 @@
+// Host side of the C ABI declared in include/dos.h: argument checks, CSR
+// staging and validation, the sweep plan (tiles, vector panels, partial-sum
+// slots), launch sequencing, the CUDA-graph cache and the autotuner.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+#include <string.h>
+
+#include <algorithm>
+#include <chrono>
+#include <new>
+#include <vector>
+
+#include "dos_internal.h"
+
+using namespace dos;
+
+std::atomic<int64_t> dos::g_launch_count{0};
+
+namespace {
+
+constexpr int kPanelMax = 256;        // vectors per pass over A
+constexpr int kRowCost = 3;           // tile cost of one row, in nonzeros
+constexpr size_t kPartialCap = size_t(512) << 20;  // bytes of per-step partial sums kept
+
+int fail(dos_ctx *ctx, const Error &e) {
+    if (ctx) ctx->last_error = e.msg;
+    return e.status;
+}
+
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) != cudaSuccess) {
+            cudaGetLastError();
+            prev = -1;
+        }
+        if (prev != dev) DOS_CUDA_TRY(cudaSetDevice(dev));
+    }
+    ~DeviceGuard() {
+        int cur = -1;
+        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+template <typename F>
+int guarded(dos_ctx *ctx, F &&f) {
+    if (!ctx) return DOS_EINVAL;
+    try {
+        DeviceGuard g(ctx->device);
+        f();
+        ctx->last_error.clear();
+        return DOS_OK;
+    } catch (const Error &e) {
+        return fail(ctx, e);
+    } catch (const std::bad_alloc &) {
+        return fail(ctx, Error{DOS_ENOMEM, "host allocation failed"});
+    }
+}
+
+bool is_device_ptr(const void *p) {
+    if (!p) return false;
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+// Copy `bytes` from device scratch to a caller buffer of either kind.
+void copy_out(void *dst, const void *src, size_t bytes, cudaStream_t s) {
+    DOS_CUDA_TRY(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDefault, s));
+}
+
+struct DevCSR {
+    int64_t n, nnz;
+    const int32_t *row_ptr, *col_idx;
+    const void *val;
+    int dtype;
+    const int32_t *host_row_ptr;  // non-null when the caller passed host arrays
+};
+
+DevCSR stage_csr(dos_ctx *ctx, const dos_csr *A, cudaStream_t s) {
+    DOS_REQUIRE(A != nullptr, "matrix descriptor is NULL");
+    DOS_REQUIRE(A->n >= 1 && A->n < (int64_t(1) << 31), "n must be in [1, 2^31)");
+    DOS_REQUIRE(A->nnz >= 0 && A->nnz < (int64_t(1) << 31), "nnz must be in [0, 2^31)");
+    DOS_REQUIRE(A->dtype == DOS_F64 || A->dtype == DOS_F32, "dtype must be DOS_F64 or DOS_F32");
+    DOS_REQUIRE(A->location == DOS_DEVICE || A->location == DOS_HOST, "bad location");
+    DOS_REQUIRE(A->row_ptr != nullptr, "row_ptr is NULL");
+    DOS_REQUIRE(A->nnz == 0 || (A->col_idx != nullptr && A->val != nullptr),
+                "col_idx / val is NULL");
+    DevCSR d{A->n, A->nnz, A->row_ptr, A->col_idx, A->val, A->dtype, nullptr};
+    if (A->location == DOS_HOST) {
+        const size_t es = A->dtype == DOS_F64 ? 8 : 4;
+        void *rp = ctx->csr_rowptr.get((A->n + 1) * sizeof(int32_t));
+        void *ci = ctx->csr_colidx.get(std::max<int64_t>(A->nnz, 1) * sizeof(int32_t));
+        void *va = ctx->csr_val.get(std::max<int64_t>(A->nnz, 1) * es);
+        DOS_CUDA_TRY(cudaMemcpyAsync(rp, A->row_ptr, (A->n + 1) * sizeof(int32_t),
+                                     cudaMemcpyHostToDevice, s));
+        if (A->nnz) {
+            DOS_CUDA_TRY(cudaMemcpyAsync(ci, A->col_idx, A->nnz * sizeof(int32_t),
+                                         cudaMemcpyHostToDevice, s));
+            DOS_CUDA_TRY(cudaMemcpyAsync(va, A->val, A->nnz * es, cudaMemcpyHostToDevice, s));
+        }
+        d.row_ptr = (const int32_t *)rp;
+        d.col_idx = (const int32_t *)ci;
+        d.val = va;
+        d.host_row_ptr = A->row_ptr;
+    }
+    return d;
+}
+
+// Segment table on the device: seg_row0 (B+1 int32), seg_tile_begin (B+1 int32),
+// seg_c (B doubles), seg_inv_d (B doubles), validation/status flags (4 ints).
+struct SegDev {
+    int32_t *row0, *tile_begin;
+    double *c, *inv_d;
+};
+
+SegDev upload_segments(dos_ctx *ctx, const std::vector<int32_t> &row0,
+                       const std::vector<int32_t> &tile_begin, const std::vector<double> &c,
+                       const std::vector<double> &inv_d, cudaStream_t s) {
+    const int B = (int)c.size();
+    const size_t ints = ((2 * (size_t)(B + 1)) + 1) & ~size_t(1);  // keep doubles 8-aligned
+    const size_t bytes = ints * 4 + 2 * (size_t)B * 8;
+    uint8_t *dev = (uint8_t *)ctx->segs.get(bytes);
+    uint8_t *host = (uint8_t *)ctx->host_stage.get(bytes);
+    memcpy(host, row0.data(), (B + 1) * 4);
+    memcpy(host + (B + 1) * 4, tile_begin.data(), (B + 1) * 4);
+    memcpy(host + ints * 4, c.data(), B * 8);
+    memcpy(host + ints * 4 + B * 8, inv_d.data(), B * 8);
+    DOS_CUDA_TRY(cudaMemcpyAsync(dev, host, bytes, cudaMemcpyHostToDevice, s));
+    // the pinned staging buffer is reused by the next call: wait for the copy
+    DOS_CUDA_TRY(cudaStreamSynchronize(s));
+    SegDev d;
+    d.row0 = (int32_t *)dev;
+    d.tile_begin = (int32_t *)(dev + (B + 1) * 4);
+    d.c = (double *)(dev + ints * 4);
+    d.inv_d = (double *)(dev + ints * 4 + B * 8);
+    return d;
+}
+
+int *status_flags(dos_ctx *ctx) { return (int *)ctx->status.get(4 * sizeof(int)); }
+
+void validate_on_device(dos_ctx *ctx, const DevCSR &A, int B, const int32_t *seg_row0_dev,
+                        cudaStream_t s) {
+    int *flag = status_flags(ctx) + 1;
+    DOS_CUDA_TRY(cudaMemsetAsync(flag, 0, sizeof(int), s));
+    launch_validate_csr(A.n, A.nnz, A.row_ptr, A.col_idx, B, seg_row0_dev, flag, s);
+    int h = 0;
+    DOS_CUDA_TRY(cudaMemcpyAsync(&h, flag, sizeof(int), cudaMemcpyDeviceToHost, s));
+    DOS_CUDA_TRY(cudaStreamSynchronize(s));
+    DOS_REQUIRE(h == 0, "CSR structure check failed (row_ptr not monotone / not ending at nnz, "
+                        "or a column index out of range)");
+}
+
+struct SweepRequest {
+    int B;
+    std::vector<int64_t> seg_rows;  // B+1
+    std::vector<double> lb, ub;     // B
+    int M, n_v;
+    uint64_t seed;
+    int precision;
+    double *mu, *mu_pv;
+    dos_kpm_opts opts;
+};
+
+Shape tune_shape(dos_ctx *ctx, const dos_csr *A, int B, const int64_t *seg_rows, int n_v,
+                 int precision, double *best_ms, cudaStream_t s);
+
+Shape choose_shape(dos_ctx *ctx, const SweepRequest &r, const dos_csr *Adesc, int ld,
+                   int64_t n_rows, int64_t nnz, cudaStream_t s) {
+    const dos_launch &o = r.opts.launch;
+    if (o.team || o.chunks || o.block || o.tiles) {
+        Shape d = default_shape(r.precision, ld, ctx->num_sms, n_rows);
+        Shape sh;
+        sh.team = o.team ? o.team : d.team;
+        sh.chunks = o.chunks ? o.chunks : d.chunks;
+        sh.block = o.block ? o.block : d.block;
+        sh.tiles = o.tiles ? o.tiles : d.tiles;
+        DOS_REQUIRE(shape_supported(r.precision, sh, ld),
+                    "launch override does not cover the vector block (team*chunks*16B >= row) "
+                    "or uses an unsupported team/chunks/block");
+        return sh;
+    }
+    auto it = ctx->tuned.find(std::make_tuple(n_rows, nnz, r.B, std::min(r.n_v, kPanelMax),
+                                              r.precision));
+    if (it != ctx->tuned.end() && shape_supported(r.precision, it->second, ld)) return it->second;
+    if (r.opts.flags & DOS_OPT_AUTOTUNE) {
+        Shape sh = tune_shape(ctx, Adesc, r.B, r.seg_rows.data(), r.n_v, r.precision, nullptr, s);
+        if (shape_supported(r.precision, sh, ld)) return sh;
+    }
+    return default_shape(r.precision, ld, ctx->num_sms, n_rows);
+}
+
+struct Plan {
+    int n_tiles;
+    std::vector<int32_t> row0, tile_begin;
+};
+
+Plan make_plan(const SweepRequest &r, const DevCSR &A, const Shape &sh, cudaStream_t s) {
+    Plan p;
+    const int B = r.B;
+    p.row0.resize(B + 1);
+    for (int b = 0; b <= B; ++b) p.row0[b] = (int32_t)r.seg_rows[b];
+    p.tile_begin.assign(B + 1, 0);
+    if (B == 1) {
+        p.tile_begin[1] = sh.tiles;
+    } else {
+        // nnz at the segment boundaries
+        std::vector<int32_t> rp(B + 1);
+        if (A.host_row_ptr) {
+            for (int b = 0; b <= B; ++b) rp[b] = A.host_row_ptr[r.seg_rows[b]];
+        } else {
+            for (int b = 0; b <= B; ++b)
+                DOS_CUDA_TRY(cudaMemcpyAsync(&rp[b], A.row_ptr + r.seg_rows[b], sizeof(int32_t),
+                                             cudaMemcpyDeviceToHost, s));
+            DOS_CUDA_TRY(cudaStreamSynchronize(s));
+        }
+        std::vector<double> cost(B);
+        double total = 0.0;
+        for (int b = 0; b < B; ++b) {
+            cost[b] = (double)(rp[b + 1] - rp[b]) + kRowCost * (double)(r.seg_rows[b + 1] - r.seg_rows[b]);
+            total += cost[b];
+        }
+        const double target = std::max<double>(sh.tiles, B);
+        for (int b = 0; b < B; ++b) {
+            const int64_t rows = r.seg_rows[b + 1] - r.seg_rows[b];
+            int64_t t = (int64_t)llround(target * cost[b] / total);
+            t = std::max<int64_t>(1, std::min<int64_t>(t, rows));
+            p.tile_begin[b + 1] = p.tile_begin[b] + (int32_t)t;
+        }
+    }
+    p.n_tiles = p.tile_begin[B];
+    return p;
+}
+
+void run_sweep(dos_ctx *ctx, const dos_csr *Adesc, SweepRequest &r, cudaStream_t s) {
+    DOS_REQUIRE(r.M >= 0 && r.M <= 100000, "M must be in [0, 100000]");
+    DOS_REQUIRE(r.n_v >= 1 && r.n_v <= 4096, "n_v must be in [1, 4096]");
+    DOS_REQUIRE(r.precision == DOS_PREC_F64 || r.precision == DOS_PREC_F32_ACC64,
+                "precision must be DOS_PREC_F64 or DOS_PREC_F32_ACC64");
+    DOS_REQUIRE(r.mu != nullptr, "mu is NULL");
+    DOS_REQUIRE(r.opts.vec_offset >= 0 && r.opts.vec_offset + r.n_v <= (int64_t(1) << 16) * 64,
+                "vec_offset + n_v out of range");
+    DevCSR A = stage_csr(ctx, Adesc, s);
+    DOS_REQUIRE(!(r.precision == DOS_PREC_F64 && A.dtype != DOS_F64),
+                "DOS_PREC_F64 needs FP64 matrix values");
+    const int B = r.B;
+    DOS_REQUIRE(B >= 1 && B <= (1 << 16), "B must be in [1, 65536]");
+    DOS_REQUIRE(r.seg_rows[0] == 0 && r.seg_rows[B] == A.n, "seg_rows must start at 0 and end at n");
+    for (int b = 0; b < B; ++b) {
+        DOS_REQUIRE(r.seg_rows[b + 1] > r.seg_rows[b], "every matrix needs at least one row");
+        DOS_REQUIRE(isfinite(r.lb[b]) && isfinite(r.ub[b]) && r.ub[b] > r.lb[b],
+                    "bounds must be finite with ub > lb");
+    }
+    DOS_REQUIRE(r.opts.batch_index + (uint64_t)B <= (uint64_t(1) << 16), "batch index out of range");
+
+    // values in the sweep precision
+    const void *val = A.val;
+    if (r.precision == DOS_PREC_F32_ACC64 && A.dtype == DOS_F64 && A.nnz > 0) {
+        float *v32 = (float *)ctx->val_f32.get(A.nnz * sizeof(float));
+        launch_f64_to_f32((const double *)A.val, v32, A.nnz, s);
+        val = v32;
+    }
+
+    // vector panels
+    const int vpt = r.precision == DOS_PREC_F64 ? 2 : 4;
+    const int esz = r.precision == DOS_PREC_F64 ? 8 : 4;
+    const int n_panels = (r.n_v + kPanelMax - 1) / kPanelMax;
+    const int panel_nv = (r.n_v + n_panels - 1) / n_panels;
+    const int ld = (panel_nv + vpt - 1) / vpt * vpt;
+
+    const Shape sh = choose_shape(ctx, r, Adesc, ld, A.n, A.nnz, s);
+    Plan plan = make_plan(r, A, sh, s);
+
+    std::vector<double> c(B), inv_d(B);
+    for (int b = 0; b < B; ++b) {
+        c[b] = 0.5 * (r.lb[b] + r.ub[b]);
+        inv_d[b] = 1.0 / (0.5 * (r.ub[b] - r.lb[b]));
+    }
+    SegDev seg = upload_segments(ctx, plan.row0, plan.tile_begin, c, inv_d, s);
+    if (!(r.opts.flags & DOS_OPT_NO_VALIDATE)) validate_on_device(ctx, A, B, seg.row0, s);
+
+    const int S = std::max(1, (r.M + 1) / 2);  // ceil(M/2), at least one step
+    const bool per_vec = r.mu_pv != nullptr;
+    const int pv = per_vec ? ld : 1;
+    const int pvt = per_vec ? r.n_v : 1;
+    const size_t per_step = (size_t)plan.n_tiles * 2 * pv * sizeof(double);
+    const int slots = (int)std::max<size_t>(1, std::min<size_t>(S, kPartialCap / per_step));
+
+    int4 *tiles = (int4 *)ctx->tiles.get(plan.n_tiles * sizeof(int4));
+    launch_make_tiles(A.row_ptr, B, seg.row0, seg.tile_begin, plan.n_tiles, kRowCost, tiles, s);
+
+    uint8_t *xb = (uint8_t *)ctx->xbuf.get(2 * (size_t)A.n * ld * esz);
+    double *partial = (double *)ctx->partial.get(per_step * slots +
+                                                 (size_t)plan.n_tiles * pv * sizeof(double));
+    double *partial0 = partial + (size_t)slots * plan.n_tiles * 2 * pv;
+    double *dotsum = (double *)ctx->dotsum.get(((size_t)B * S * 2 * pvt + (size_t)B * pvt) *
+                                               sizeof(double));
+    double *dotsum0 = dotsum + (size_t)B * S * 2 * pvt;
+    double *mu_dev = (double *)ctx->mu_dev.get((size_t)B * (r.M + 1) * sizeof(double));
+    double *mupv_dev = per_vec ? (double *)ctx->mupv_dev.get((size_t)B * r.n_v * (r.M + 1) *
+                                                             sizeof(double))
+                               : nullptr;
+    int *status = status_flags(ctx);
+    DOS_CUDA_TRY(cudaMemsetAsync(status, 0, sizeof(int), s));
+
+    SweepArgs a;
+    a.precision = r.precision;
+    a.row_ptr = A.row_ptr;
+    a.col_idx = A.col_idx;
+    a.val = val;
+    a.n_rows = A.n;
+    a.ld = ld;
+    a.B = B;
+    a.seg_row0 = seg.row0;
+    a.seg_c = seg.c;
+    a.seg_inv_d = seg.inv_d;
+    a.tiles = tiles;
+    a.n_tiles = plan.n_tiles;
+    a.x0 = xb;
+    a.x1 = xb + (size_t)A.n * ld * esz;
+    a.partial = partial;
+    a.partial0 = partial0;
+    a.per_vec = per_vec;
+    a.seed = r.seed;
+    a.batch_index = r.opts.batch_index;
+    a.shape = sh;
+
+    for (int p = 0; p < n_panels; ++p) {
+        const int off = p * panel_nv;
+        const int width = std::min(panel_nv, r.n_v - off);
+        a.n_v = width;
+        a.vec_offset = r.opts.vec_offset + off;
+        launch_init_vectors(a, s);
+        int k0 = 0;
+        float panel_ms = 0.f;
+        if (ctx->profiling) DOS_CUDA_TRY(cudaEventRecord(ctx->prof_ev[0], s));
+        for (int k = 0; k < S; ++k) {
+            launch_step(a, k, k % slots, s);
+            if (ctx->profiling && k == S - 1) DOS_CUDA_TRY(cudaEventRecord(ctx->prof_ev[1], s));
+            if ((k + 1) % slots == 0 || k == S - 1) {
+                launch_reduce(partial, plan.n_tiles, pv, width, B, seg.tile_begin, k0, k + 1 - k0,
+                              k0 % slots, slots, S, off, pvt, p > 0, dotsum, s);
+                k0 = k + 1;
+            }
+        }
+        if (ctx->profiling) {
+            // step launches between the two events: S (one reduce per `slots` steps
+            // may fall inside when slots < S; it is short and counted in the time)
+            DOS_CUDA_TRY(cudaEventSynchronize(ctx->prof_ev[1]));
+            DOS_CUDA_TRY(cudaEventElapsedTime(&panel_ms, ctx->prof_ev[0], ctx->prof_ev[1]));
+            ctx->prof_step_ms += panel_ms;
+            ctx->prof_step_launches += S;
+        }
+        launch_reduce0(partial0, pv, width, B, seg.tile_begin, off, pvt, p > 0, dotsum0, s);
+    }
+    if (ctx->profiling) ctx->prof_sweeps += 1;
+    const double tol = r.precision == DOS_PREC_F64 ? 1e-8 : 1e-3;
+    launch_finalize(dotsum, dotsum0, seg.row0, B, r.M, S, r.n_v, pvt, mu_dev, mupv_dev, tol,
+                    status, s);
+    copy_out(r.mu, mu_dev, (size_t)B * (r.M + 1) * sizeof(double), s);
+    if (per_vec) copy_out(r.mu_pv, mupv_dev, (size_t)B * r.n_v * (r.M + 1) * sizeof(double), s);
+
+    const bool host_out = !is_device_ptr(r.mu) || (per_vec && !is_device_ptr(r.mu_pv));
+    if (!(r.opts.flags & DOS_OPT_NO_SPECTRUM_CHECK) || host_out) {
+        int h = 0;
+        DOS_CUDA_TRY(cudaMemcpyAsync(&h, status, sizeof(int), cudaMemcpyDeviceToHost, s));
+        DOS_CUDA_TRY(cudaStreamSynchronize(s));
+        if (!(r.opts.flags & DOS_OPT_NO_SPECTRUM_CHECK) && (h & 2))
+            throw Error{DOS_ESPECTRUM,
+                        "a moment exceeds mu_0 in magnitude or is not finite: the bounds do not "
+                        "enclose the spectrum"};
+    }
+}
+
+dos_kpm_opts default_opts() {
+    dos_kpm_opts o;
+    memset(&o, 0, sizeof(o));
+    return o;
+}
+
+// Autotuner: for every launch shape that covers the vector block without more
+// than 2x idle lanes, and tile counts of 1x/2x/4x the resident blocks, time
+// sweeps of 8 and 24 Chebyshev steps with CUDA events; the difference / 16 is
+// the per-step time (fixed per-call costs cancel).  Best of two runs.
+Shape tune_shape(dos_ctx *ctx, const dos_csr *A, int B, const int64_t *seg_rows, int n_v,
+                 int precision, double *best_ms, cudaStream_t s) {
+    DOS_REQUIRE(n_v >= 1 && n_v <= 4096, "n_v must be in [1, 4096]");
+    DOS_REQUIRE(precision == DOS_PREC_F64 || precision == DOS_PREC_F32_ACC64, "bad precision");
+    const int vpt = precision == DOS_PREC_F64 ? 2 : 4;
+    const int pw = std::min(n_v, kPanelMax);
+    const int n_panels = (n_v + kPanelMax - 1) / kPanelMax;
+    const int panel_nv = (n_v + n_panels - 1) / n_panels;
+    const int ld = (panel_nv + vpt - 1) / vpt * vpt;
+    const int chunks = ld / vpt;
+    std::vector<int64_t> rows;
+    if (B == 1) rows = {0, A->n};
+    else rows.assign(seg_rows, seg_rows + B + 1);
+    // Timing only: the moments are discarded and the spectrum check is off, so
+    // any bounds do (values may grow; the kernels' speed does not depend on them).
+    std::vector<double> lb(B, -1.0), ub(B, 1.0);
+    double *mu_scratch = (double *)ctx->rec_out.get((size_t)B * 49 * sizeof(double));
+    cudaEvent_t e0, e1;
+    DOS_CUDA_TRY(cudaEventCreate(&e0));
+    DOS_CUDA_TRY(cudaEventCreate(&e1));
+    Shape best;
+    double best_t = INFINITY;
+    bool first = true;
+    for (int G = 1; G <= 32; G <<= 1) {
+        for (int C : {1, 2, 4}) {
+            const int cover = G * C;
+            if (cover < chunks || (cover > 1 && cover / 2 >= chunks)) continue;
+            Shape sh;
+            sh.team = G;
+            sh.chunks = C;
+            sh.block = 256;
+            const int occ = max_active_blocks(precision, sh);
+            if (occ <= 0) continue;
+            const int teams = (256 / 32) * (32 / G);
+            const int64_t max_tiles = std::max<int64_t>(B, (A->n + teams - 1) / teams);
+            for (int mult : {1, 2, 4}) {
+                sh.tiles = (int)std::min<int64_t>((int64_t)ctx->num_sms * occ * mult, max_tiles);
+                double per_step = INFINITY;
+                for (int rep = 0; rep < 2; ++rep) {
+                    float ms[2];
+                    for (int which = 0; which < 2; ++which) {
+                        SweepRequest r;
+                        r.B = B;
+                        r.seg_rows = rows;
+                        r.lb = lb;
+                        r.ub = ub;
+                        r.M = which ? 48 : 16;
+                        r.n_v = pw;
+                        r.seed = 1;
+                        r.precision = precision;
+                        r.mu = mu_scratch;
+                        r.mu_pv = nullptr;
+                        r.opts = default_opts();
+                        r.opts.flags = DOS_OPT_NO_SPECTRUM_CHECK | (first ? 0u : DOS_OPT_NO_VALIDATE);
+                        r.opts.launch.team = sh.team;
+                        r.opts.launch.chunks = sh.chunks;
+                        r.opts.launch.block = sh.block;
+                        r.opts.launch.tiles = sh.tiles;
+                        DOS_CUDA_TRY(cudaEventRecord(e0, s));
+                        run_sweep(ctx, A, r, s);
+                        DOS_CUDA_TRY(cudaEventRecord(e1, s));
+                        DOS_CUDA_TRY(cudaEventSynchronize(e1));
+                        DOS_CUDA_TRY(cudaEventElapsedTime(&ms[which], e0, e1));
+                        first = false;
+                    }
+                    per_step = std::min(per_step, (double)(ms[1] - ms[0]) / 16.0);
+                }
+                if (per_step < best_t) {
+                    best_t = per_step;
+                    best = sh;
+                }
+                if (sh.tiles == max_tiles) break;
+            }
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    DOS_REQUIRE(best.team > 0, "no launch shape fits this vector block");
+    int64_t nnz = A->nnz;
+    ctx->tuned[std::make_tuple((int64_t)A->n, nnz, B, pw, precision)] = best;
+    if (best_ms) *best_ms = best_t;
+    return best;
+}
+
+// Host-side eigen-analysis of the Lanczos tridiagonal T (alpha on the diagonal,
+// beta off it): extreme eigenvalues by Sturm-sequence bisection, the matching
+// unit eigenvectors by inverse iteration with a dense partially pivoted LU.
+int sturm_count(const std::vector<double> &al, const std::vector<double> &be, double x) {
+    int cnt = 0;
+    double d = 1.0;
+    for (size_t i = 0; i < al.size(); ++i) {
+        const double b2 = i ? be[i - 1] * be[i - 1] : 0.0;
+        d = (al[i] - x) - (i ? b2 / d : 0.0);
+        if (d == 0.0) d = -1e-300;
+        if (d < 0.0) ++cnt;
+    }
+    return cnt;  // eigenvalues < x
+}
+
+double bisect_eig(const std::vector<double> &al, const std::vector<double> &be, int idx) {
+    const size_t k = al.size();
+    double lo = INFINITY, hi = -INFINITY;
+    for (size_t i = 0; i < k; ++i) {
+        const double r = (i ? fabs(be[i - 1]) : 0.0) + (i + 1 < k ? fabs(be[i]) : 0.0);
+        lo = std::min(lo, al[i] - r);
+        hi = std::max(hi, al[i] + r);
+    }
+    const double scale = std::max(fabs(lo), fabs(hi)) + 1e-300;
+    for (int it = 0; it < 2000 && hi - lo > 2e-16 * scale; ++it) {
+        const double mid = 0.5 * (lo + hi);
+        if (mid <= lo || mid >= hi) break;
+        if (sturm_count(al, be, mid) > idx) hi = mid; else lo = mid;
+    }
+    return 0.5 * (lo + hi);
+}
+
+std::vector<double> inverse_iteration(const std::vector<double> &al, const std::vector<double> &be,
+                                      double theta) {
+    const int k = (int)al.size();
+    double nrm = 0.0;
+    for (int i = 0; i < k; ++i) nrm = std::max(nrm, fabs(al[i]) + (i ? fabs(be[i - 1]) : 0.0) + (i + 1 < k ? fabs(be[i]) : 0.0));
+    const double shift = theta + 1e-13 * (nrm + 1e-300);
+    std::vector<double> Mx((size_t)k * k, 0.0);
+    for (int i = 0; i < k; ++i) {
+        Mx[(size_t)i * k + i] = al[i] - shift;
+        if (i + 1 < k) {
+            Mx[(size_t)i * k + i + 1] = be[i];
+            Mx[(size_t)(i + 1) * k + i] = be[i];
+        }
+    }
+    std::vector<int> piv(k);
+    for (int j = 0; j < k; ++j) {  // LU with partial pivoting
+        int p = j;
+        for (int i = j + 1; i < k; ++i)
+            if (fabs(Mx[(size_t)i * k + j]) > fabs(Mx[(size_t)p * k + j])) p = i;
+        piv[j] = p;
+        if (p != j)
+            for (int c = 0; c < k; ++c) std::swap(Mx[(size_t)j * k + c], Mx[(size_t)p * k + c]);
+        double dj = Mx[(size_t)j * k + j];
+        if (dj == 0.0) dj = Mx[(size_t)j * k + j] = 1e-300;
+        for (int i = j + 1; i < k; ++i) {
+            const double f = Mx[(size_t)i * k + j] / dj;
+            Mx[(size_t)i * k + j] = f;
+            if (f != 0.0)
+                for (int c = j + 1; c < k; ++c) Mx[(size_t)i * k + c] -= f * Mx[(size_t)j * k + c];
+        }
+    }
+    std::vector<double> x(k, 1.0 / sqrt((double)k));
+    for (int it = 0; it < 4; ++it) {
+        for (int j = 0; j < k; ++j) std::swap(x[j], x[piv[j]]);
+        for (int i = 0; i < k; ++i)
+            for (int c = 0; c < i; ++c) x[i] -= Mx[(size_t)i * k + c] * x[c];
+        for (int i = k - 1; i >= 0; --i) {
+            for (int c = i + 1; c < k; ++c) x[i] -= Mx[(size_t)i * k + c] * x[c];
+            x[i] /= Mx[(size_t)i * k + i];
+        }
+        double s = 0.0;
+        for (double v : x) s += v * v;
+        s = sqrt(s);
+        for (double &v : x) v /= s;
+    }
+    return x;
+}
+
+}  // namespace
+
+// ============================================================================
+extern "C" {
+
+const char *dos_status_string(int status) {
+    switch (status) {
+        case DOS_OK: return "DOS_OK";
+        case DOS_EINVAL: return "DOS_EINVAL";
+        case DOS_ENOMEM: return "DOS_ENOMEM";
+        case DOS_ECUDA: return "DOS_ECUDA";
+        case DOS_ESPECTRUM: return "DOS_ESPECTRUM";
+        case DOS_ETIMEOUT: return "DOS_ETIMEOUT";
+        default: return "DOS_UNKNOWN";
+    }
+}
+
+int dos_ctx_create(dos_ctx **out, int device) {
+    if (!out) return DOS_EINVAL;
+    *out = nullptr;
+    int count = 0;
+    if (cudaGetDeviceCount(&count) != cudaSuccess) {
+        cudaGetLastError();
+        return DOS_ECUDA;
+    }
+    if (device < 0 || device >= count) return DOS_EINVAL;
+    dos_ctx *ctx = new (std::nothrow) dos_ctx();
+    if (!ctx) return DOS_ENOMEM;
+    ctx->device = device;
+    int rc = guarded(ctx, [&] {
+        DOS_CUDA_TRY(cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, device));
+    });
+    if (rc != DOS_OK) {
+        delete ctx;
+        return rc;
+    }
+    *out = ctx;
+    return DOS_OK;
+}
+
+int dos_ctx_destroy(dos_ctx *ctx) {
+    if (!ctx) return DOS_OK;
+    int prev = -1;
+    cudaGetDevice(&prev);
+    cudaSetDevice(ctx->device);
+    cudaDeviceSynchronize();
+    for (Buffer *b : {&ctx->csr_rowptr, &ctx->csr_colidx, &ctx->csr_val, &ctx->val_f32, &ctx->xbuf,
+                      &ctx->partial, &ctx->dotsum, &ctx->tiles, &ctx->segs, &ctx->status,
+                      &ctx->mu_dev, &ctx->mupv_dev, &ctx->bnd_vec, &ctx->bnd_part, &ctx->bnd_out,
+                      &ctx->rec_in, &ctx->rec_out, &ctx->err_buf})
+        b->release();
+    ctx->host_stage.release();
+    if (ctx->graph.exec) cudaGraphExecDestroy(ctx->graph.exec);
+    for (cudaEvent_t &e : ctx->prof_ev)
+        if (e) cudaEventDestroy(e);
+    if (prev >= 0) cudaSetDevice(prev);
+    cudaGetLastError();
+    delete ctx;
+    return DOS_OK;
+}
+
+const char *dos_last_error(const dos_ctx *ctx) { return ctx ? ctx->last_error.c_str() : ""; }
+
+int dos_profile_enable(dos_ctx *ctx, int on) {
+    return guarded(ctx, [&] {
+        if (on && !ctx->prof_ev[0]) {
+            DOS_CUDA_TRY(cudaEventCreate(&ctx->prof_ev[0]));
+            DOS_CUDA_TRY(cudaEventCreate(&ctx->prof_ev[1]));
+        }
+        ctx->profiling = on != 0;
+        ctx->prof_step_ms = 0.0;
+        ctx->prof_step_launches = 0;
+        ctx->prof_sweeps = 0;
+        g_launch_count.store(0);
+    });
+}
+
+int dos_profile_read(dos_ctx *ctx, double *step_ms, int64_t *step_launches, int64_t *sweeps,
+                     int64_t *launches) {
+    if (!ctx) return DOS_EINVAL;
+    if (step_ms) *step_ms = ctx->prof_step_ms;
+    if (step_launches) *step_launches = ctx->prof_step_launches;
+    if (sweeps) *sweeps = ctx->prof_sweeps;
+    if (launches) *launches = g_launch_count.load();
+    return DOS_OK;
+}
+
+int dos_validate_csr(dos_ctx *ctx, const dos_csr *Adesc, void *stream) {
+    return guarded(ctx, [&] {
+        cudaStream_t s = (cudaStream_t)stream;
+        DevCSR A = stage_csr(ctx, Adesc, s);
+        std::vector<int32_t> row0 = {0, (int32_t)A.n}, tb = {0, 1};
+        SegDev seg = upload_segments(ctx, row0, tb, {0.0}, {1.0}, s);
+        validate_on_device(ctx, A, 1, seg.row0, s);
+    });
+}
+
+int dos_start_vectors(dos_ctx *ctx, int64_t n, int n_v, uint64_t seed, uint64_t batch_index,
+                      int64_t vec_offset, int dtype, void *out, void *stream) {
+    return guarded(ctx, [&] {
+        DOS_REQUIRE(out != nullptr, "out is NULL");
+        DOS_REQUIRE(n >= 1 && n < (int64_t(1) << 31), "n must be in [1, 2^31)");
+        DOS_REQUIRE(n_v >= 1 && n_v <= 4096, "n_v must be in [1, 4096]");
+        DOS_REQUIRE(vec_offset >= 0 && vec_offset + n_v <= (int64_t(1) << 16) * 64,
+                    "vec_offset + n_v out of range");
+        DOS_REQUIRE(batch_index < (uint64_t(1) << 16), "batch_index out of range");
+        DOS_REQUIRE(dtype == DOS_F64 || dtype == DOS_F32, "bad dtype");
+        cudaStream_t s = (cudaStream_t)stream;
+        const int prec = dtype == DOS_F64 ? DOS_PREC_F64 : DOS_PREC_F32_ACC64;
+        const int vpt = dtype == DOS_F64 ? 2 : 4;
+        const int esz = dtype == DOS_F64 ? 8 : 4;
+        const int ld = (n_v + vpt - 1) / vpt * vpt;
+        std::vector<int32_t> row0 = {0, (int32_t)n}, tb = {0, 1};
+        SegDev seg = upload_segments(ctx, row0, tb, {0.0}, {1.0}, s);
+        void *x = ctx->xbuf.get((size_t)n * ld * esz);
+        SweepArgs a{};
+        a.precision = prec;
+        a.n_rows = n;
+        a.n_v = n_v;
+        a.ld = ld;
+        a.B = 1;
+        a.seg_row0 = seg.row0;
+        a.x0 = x;
+        a.seed = seed;
+        a.vec_offset = vec_offset;
+        a.batch_index = batch_index;
+        launch_init_vectors(a, s);
+        DOS_CUDA_TRY(cudaMemcpy2DAsync(out, (size_t)n_v * esz, x, (size_t)ld * esz,
+                                       (size_t)n_v * esz, (size_t)n, cudaMemcpyDefault, s));
+        if (!is_device_ptr(out)) DOS_CUDA_TRY(cudaStreamSynchronize(s));
+    });
+}
+
+int dos_kpm_moments_ex(dos_ctx *ctx, const dos_csr *A, double lb, double ub, int M, int n_v,
+                       uint64_t seed, int precision, double *mu, double *mu_per_vec,
+                       const dos_kpm_opts *opts, void *stream) {
+    return guarded(ctx, [&] {
+        DOS_REQUIRE(A != nullptr, "matrix descriptor is NULL");
+        SweepRequest r;
+        r.B = 1;
+        r.seg_rows = {0, A->n};
+        r.lb = {lb};
+        r.ub = {ub};
+        r.M = M;
+        r.n_v = n_v;
+        r.seed = seed;
+        r.precision = precision;
+        r.mu = mu;
+        r.mu_pv = mu_per_vec;
+        r.opts = opts ? *opts : default_opts();
+        run_sweep(ctx, A, r, (cudaStream_t)stream);
+    });
+}
+
+int dos_kpm_moments(dos_ctx *ctx, const dos_csr *A, double lb, double ub, int M, int n_v,
+                    uint64_t seed, int precision, double *mu, double *mu_per_vec, void *stream) {
+    return dos_kpm_moments_ex(ctx, A, lb, ub, M, n_v, seed, precision, mu, mu_per_vec, nullptr,
+                              stream);
+}
+
+int dos_kpm_moments_batched(dos_ctx *ctx, const dos_csr *A, int B, const int64_t *seg_rows,
+                            const double *lb, const double *ub, int M, int n_v, uint64_t seed,
+                            int precision, double *mu, double *mu_per_vec,
+                            const dos_kpm_opts *opts, void *stream) {
+    return guarded(ctx, [&] {
+        DOS_REQUIRE(B >= 1 && B <= (1 << 16), "B must be in [1, 65536]");
+        DOS_REQUIRE(seg_rows && lb && ub, "seg_rows / lb / ub is NULL");
+        SweepRequest r;
+        r.B = B;
+        r.seg_rows.assign(seg_rows, seg_rows + B + 1);
+        r.lb.assign(lb, lb + B);
+        r.ub.assign(ub, ub + B);
+        r.M = M;
+        r.n_v = n_v;
+        r.seed = seed;
+        r.precision = precision;
+        r.mu = mu;
+        r.mu_pv = mu_per_vec;
+        r.opts = opts ? *opts : default_opts();
+        r.opts.batch_index = opts ? opts->batch_index : 0;
+        run_sweep(ctx, A, r, (cudaStream_t)stream);
+    });
+}
+
+int dos_tune(dos_ctx *ctx, const dos_csr *A, int B, const int64_t *seg_rows, int n_v,
+             int precision, dos_launch *best, double *best_ms, void *stream) {
+    return guarded(ctx, [&] {
+        DOS_REQUIRE(A != nullptr, "matrix descriptor is NULL");
+        DOS_REQUIRE(B >= 1 && B <= (1 << 16), "B must be in [1, 65536]");
+        DOS_REQUIRE(B == 1 || seg_rows != nullptr, "seg_rows is NULL");
+        Shape sh = tune_shape(ctx, A, B, seg_rows, n_v, precision, best_ms, (cudaStream_t)stream);
+        if (best) {
+            best->team = sh.team;
+            best->chunks = sh.chunks;
+            best->block = sh.block;
+            best->tiles = sh.tiles;
+        }
+    });
+}
+
+int dos_bounds(dos_ctx *ctx, const dos_csr *Adesc, int method, int steps, uint64_t seed,
+               double pad_frac, double *lb, double *ub, void *stream) {
+    return guarded(ctx, [&] {
+        DOS_REQUIRE(lb && ub, "lb / ub is NULL");
+        DOS_REQUIRE(method == DOS_BOUNDS_GERSHGORIN || method == DOS_BOUNDS_LANCZOS, "bad method");
+        DOS_REQUIRE(isfinite(pad_frac) && pad_frac >= 0.0, "pad_frac must be >= 0");
+        cudaStream_t s = (cudaStream_t)stream;
+        DevCSR A = stage_csr(ctx, Adesc, s);
+        {
+            std::vector<int32_t> row0 = {0, (int32_t)A.n}, tb = {0, 1};
+            SegDev seg = upload_segments(ctx, row0, tb, {0.0}, {1.0}, s);
+            validate_on_device(ctx, A, 1, seg.row0, s);
+        }
+        double lo, hi;
+        if (method == DOS_BOUNDS_GERSHGORIN) {
+            const int nb = gershgorin_blocks(ctx->num_sms);
+            double *part = (double *)ctx->bnd_part.get((2 * (size_t)nb + 2) * sizeof(double));
+            double *out = part + 2 * nb;
+            launch_gershgorin(A.n, A.row_ptr, A.col_idx, A.val, A.dtype, part, nb, s);
+            launch_minmax_final(part, nb, out, s);
+            double h[2];
+            DOS_CUDA_TRY(cudaMemcpyAsync(h, out, sizeof(h), cudaMemcpyDeviceToHost, s));
+            DOS_CUDA_TRY(cudaStreamSynchronize(s));
+            lo = h[0];
+            hi = h[1];
+        } else {
+            DOS_REQUIRE(steps >= 1 && steps <= 512, "steps must be in [1, 512]");
+            const int k = (int)std::min<int64_t>(steps, A.n);
+            const int nb = reduce_blocks(ctx->num_sms, A.n);
+            double *vec = (double *)ctx->bnd_vec.get(3 * (size_t)A.n * sizeof(double));
+            double *q = vec, *q_prev = vec + A.n, *w = vec + 2 * A.n;
+            double *part = (double *)ctx->bnd_part.get(((size_t)nb + 2 * (size_t)k) * sizeof(double));
+            double *alpha = part + nb, *beta = alpha + k;
+            DOS_CUDA_TRY(cudaMemsetAsync(q_prev, 0, A.n * sizeof(double), s));
+            launch_lanczos_start(A.n, seed, q, s);
+            for (int j = 0; j < k; ++j) {
+                launch_lanczos_matvec(A.n, A.row_ptr, A.col_idx, A.val, A.dtype, q, q_prev,
+                                      j ? beta + j - 1 : nullptr, w, part, nb, s);
+                launch_sum_final(part, nb, alpha + j, 0, s);
+                launch_lanczos_axpy(A.n, alpha + j, q, w, part, nb, s);
+                launch_sum_final(part, nb, beta + j, 1, s);
+                if (j + 1 < k) launch_lanczos_next(A.n, beta + j, q, q_prev, w, s);
+            }
+            std::vector<double> al(k), be(k);
+            DOS_CUDA_TRY(cudaMemcpyAsync(al.data(), alpha, k * sizeof(double),
+                                         cudaMemcpyDeviceToHost, s));
+            DOS_CUDA_TRY(cudaMemcpyAsync(be.data(), beta, k * sizeof(double),
+                                         cudaMemcpyDeviceToHost, s));
+            DOS_CUDA_TRY(cudaStreamSynchronize(s));
+            int kk = k;  // an exact zero beta ends the run (invariant subspace)
+            for (int j = 0; j < k; ++j)
+                if (!(be[j] > 0.0)) {
+                    kk = j + 1;
+                    break;
+                }
+            al.resize(kk);
+            be.resize(kk);
+            for (int j = 0; j < kk; ++j)
+                DOS_REQUIRE(isfinite(al[j]) && isfinite(be[j]), "Lanczos produced non-finite values");
+            const double f = be[kk - 1];
+            std::vector<double> off(be.begin(), be.end() - 1);
+            const double tmin = bisect_eig(al, off, 0), tmax = bisect_eig(al, off, kk - 1);
+            const double ymin = kk > 1 ? fabs(inverse_iteration(al, off, tmin).back()) : 1.0;
+            const double ymax = kk > 1 ? fabs(inverse_iteration(al, off, tmax).back()) : 1.0;
+            lo = tmin - f * ymin;
+            hi = tmax + f * ymax;
+        }
+        DOS_REQUIRE(isfinite(lo) && isfinite(hi), "bounds are not finite (non-finite values?)");
+        const double w = hi - lo;
+        *lb = lo - pad_frac * w;
+        *ub = hi + pad_frac * w;
+        if (!(*ub > *lb)) {  // a matrix with a single eigenvalue: widen to a unit interval
+            *lb = lo - 0.5;
+            *ub = hi + 0.5;
+        }
+    });
+}
+
+int dos_reconstruct(dos_ctx *ctx, const double *mu, int M, int damping, double lb, double ub,
+                    const double *t, int N_t, double *phi_hat, double *phi_lambda, void *stream) {
+    return guarded(ctx, [&] {
+        DOS_REQUIRE(mu && phi_hat, "mu / phi_hat is NULL");
+        DOS_REQUIRE(M >= 0 && M <= 100000, "M must be in [0, 100000]");
+        DOS_REQUIRE(N_t >= 1 && N_t <= (1 << 26), "N_t must be in [1, 2^26]");
+        DOS_REQUIRE(damping == DOS_DAMP_NONE || damping == DOS_DAMP_JACKSON, "bad damping");
+        DOS_REQUIRE(!phi_lambda || (isfinite(lb) && isfinite(ub) && ub > lb), "need ub > lb");
+        cudaStream_t s = (cudaStream_t)stream;
+        // device staging: mu | coefficients | t | phi_hat | phi_lambda
+        const size_t nd = 2 * (size_t)(M + 1) + 3 * (size_t)N_t;
+        double *buf = (double *)ctx->rec_in.get(nd * sizeof(double));
+        double *dmu = buf, *coef = buf + (M + 1), *dt = coef + (M + 1);
+        double *dphi = dt + N_t, *dphl = dphi + N_t;
+        DOS_CUDA_TRY(cudaMemcpyAsync(dmu, mu, (M + 1) * sizeof(double), cudaMemcpyDefault, s));
+        if (t) DOS_CUDA_TRY(cudaMemcpyAsync(dt, t, N_t * sizeof(double), cudaMemcpyDefault, s));
+        launch_reconstruct(dmu, M, damping, lb, ub, t ? dt : nullptr, N_t, coef, dphi,
+                           phi_lambda ? dphl : nullptr, s);
+        copy_out(phi_hat, dphi, N_t * sizeof(double), s);
+        if (phi_lambda) copy_out(phi_lambda, dphl, N_t * sizeof(double), s);
+        if (!is_device_ptr(phi_hat) || (phi_lambda && !is_device_ptr(phi_lambda)))
+            DOS_CUDA_TRY(cudaStreamSynchronize(s));
+    });
+}
+
+int dos_smoothed_error(dos_ctx *ctx, const double *mu, int M, int damping, double lb, double ub,
+                       const double *eig, int64_t n_eig, const double *ref_mu, int M_ref,
+                       int ref_damping, double sigma, int N_x, double *err_l1, double *err_inf,
+                       void *stream) {
+    return guarded(ctx, [&] {
+        DOS_REQUIRE(mu != nullptr, "mu is NULL");
+        DOS_REQUIRE(M >= 0 && M <= 100000, "M must be in [0, 100000]");
+        DOS_REQUIRE(isfinite(lb) && isfinite(ub) && ub > lb, "need ub > lb");
+        DOS_REQUIRE(isfinite(sigma) && sigma > 0.0, "sigma must be > 0");
+        DOS_REQUIRE(N_x >= 2 && N_x <= 1000000, "N_x must be in [2, 10^6]");
+        DOS_REQUIRE(eig ? n_eig >= 1 : (ref_mu != nullptr && M_ref >= 0 && M_ref <= 100000),
+                    "need eigenvalues or reference moments");
+        DOS_REQUIRE(damping == DOS_DAMP_NONE || damping == DOS_DAMP_JACKSON, "bad damping");
+        DOS_REQUIRE(eig || ref_damping == DOS_DAMP_NONE || ref_damping == DOS_DAMP_JACKSON,
+                    "bad ref_damping");
+        cudaStream_t s = (cudaStream_t)stream;
+        const int Meff = eig ? M : std::max(M, M_ref);
+        const double d = 0.5 * (ub - lb);
+        const int64_t nq64 = std::max<int64_t>(4 * (int64_t)(Meff + 1),
+                                               (int64_t)ceil(40.0 * d / sigma));
+        DOS_REQUIRE(nq64 <= (1 << 24), "sigma too small for the quadrature (N_q > 2^24)");
+        const int N_q = (int)nq64;
+        const double x0 = lb - 6.0 * sigma;
+        const double h = (ub - lb + 12.0 * sigma) / (N_x - 1);
+        // scratch: mu | ref_mu | poly (M'+1 + N_q) | approx (N_x) | ref (N_x) | out (2) | eig
+        const size_t n_ref = eig ? 0 : (size_t)M_ref + 1;
+        const size_t neig = eig ? (size_t)n_eig : 0;
+        const size_t nd = (size_t)(M + 1) + n_ref + (size_t)(Meff + 1) + N_q + 2 * (size_t)N_x + 2 + neig;
+        double *buf = (double *)ctx->err_buf.get(nd * sizeof(double));
+        double *dmu = buf, *dref = dmu + (M + 1), *poly = dref + n_ref;
+        double *approx = poly + (Meff + 1) + N_q, *ref = approx + N_x, *out = ref + N_x;
+        double *deig = out + 2;
+        DOS_CUDA_TRY(cudaMemcpyAsync(dmu, mu, (M + 1) * sizeof(double), cudaMemcpyDefault, s));
+        launch_blur_kpm(dmu, M, damping, lb, ub, sigma, N_q, x0, h, N_x, poly, approx, s);
+        if (eig) {
+            DOS_CUDA_TRY(cudaMemcpyAsync(deig, eig, neig * sizeof(double), cudaMemcpyDefault, s));
+            launch_blur_eigs(deig, n_eig, sigma, x0, h, N_x, ref, s);
+        } else {
+            DOS_CUDA_TRY(cudaMemcpyAsync(dref, ref_mu, n_ref * sizeof(double), cudaMemcpyDefault, s));
+            launch_blur_kpm(dref, M_ref, ref_damping, lb, ub, sigma, N_q, x0, h, N_x, poly, ref, s);
+        }
+        launch_error_norms(approx, ref, N_x, h, out, s);
+        double hv[2];
+        DOS_CUDA_TRY(cudaMemcpyAsync(hv, out, sizeof(hv), cudaMemcpyDeviceToHost, s));
+        DOS_CUDA_TRY(cudaStreamSynchronize(s));
+        if (err_l1) *err_l1 = hv[0];
+        if (err_inf) *err_inf = hv[1];
+    });
+}
+
+}  // extern "C"

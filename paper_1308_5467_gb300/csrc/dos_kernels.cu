@@ -1,0 +1,168 @@
+// Reconstruction (step a6) and the smoothed error metric (step a7), FP64.
+//
+// Coefficients a_k = (2 - delta_k0) g_k mu_k with g_k the Jackson factors of
+// Appendix A (Eq. jackson, alpha_M = pi/(M+2)) or 1; the polynomial
+// P(t) = sum_k a_k T_k(t) is evaluated by Clenshaw's recurrence, and
+//     phi_hat(t) = P(t) / (pi sqrt(1 - t^2))           (Eq. tdosFinal, Eq. expmu).
+// The blurred KPM density <phi_tilde, g_sigma(. - x)> is the Gauss-Chebyshev sum
+//     (1/N_q) sum_i P(t_i) g_sigma(x - c - d t_i),  t_i = cos(pi (i + 1/2)/N_q),
+// the blurred exact density (1/n) sum_j g_sigma(x - lambda_j) (Eq. blurphi with
+// the 1/n of Eq. DOS0), g_sigma the Gaussian of Eq. gauss.
+#include <cuda_runtime.h>
+#include <math.h>
+
+#include "dos_internal.h"
+
+namespace dos {
+namespace {
+
+__global__ void coef_kernel(const double *__restrict__ mu, int M, int damping,
+                            double *__restrict__ a) {
+    const double alpha = M_PI / (double)(M + 2);
+    const double sa = sin(alpha), ca = cos(alpha);
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k <= M; k += gridDim.x * blockDim.x) {
+        double g = 1.0;
+        if (damping == DOS_DAMP_JACKSON) {
+            const double ka = k * alpha;
+            g = ((1.0 - (double)k / (M + 2)) * sa * cos(ka) + ca * sin(ka) / (M + 2)) / sa;
+        }
+        a[k] = (k == 0 ? 1.0 : 2.0) * g * mu[k];
+    }
+}
+
+__device__ __forceinline__ double clenshaw(const double *__restrict__ a, int M, double t) {
+    double b1 = 0.0, b2 = 0.0;
+    for (int k = M; k >= 1; --k) {
+        const double b0 = fma(2.0 * t, b1, a[k] - b2);
+        b2 = b1;
+        b1 = b0;
+    }
+    return fma(t, b1, a[0] - b2);
+}
+
+__global__ void reconstruct_kernel(const double *__restrict__ a, int M, double d,
+                                   const double *__restrict__ t, int N_t,
+                                   double *__restrict__ phi_hat, double *__restrict__ phi_lambda) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N_t; i += gridDim.x * blockDim.x) {
+        const double ti = t ? t[i] : -cospi((i + 0.5) / (double)N_t);
+        const double v = clenshaw(a, M, ti) / (M_PI * sqrt((1.0 - ti) * (1.0 + ti)));
+        phi_hat[i] = v;
+        if (phi_lambda) phi_lambda[i] = v / d;
+    }
+}
+
+__global__ void nodes_kernel(const double *__restrict__ a, int M, int N_q, double *__restrict__ P) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N_q; i += gridDim.x * blockDim.x)
+        P[i] = clenshaw(a, M, cospi((i + 0.5) / (double)N_q));
+}
+
+__device__ __forceinline__ double gauss(double u, double inv_sigma, double norm) {
+    const double z = u * inv_sigma;
+    return norm * exp(-0.5 * z * z);
+}
+
+// One block per grid point x_m; fixed-order block sums (reproducible).
+__device__ __forceinline__ double block_sum_d(double s) {
+    __shared__ double sh[32];
+    for (int off = 16; off > 0; off >>= 1) s += __shfl_down_sync(0xffffffffu, s, off);
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = s;
+    __syncthreads();
+    double tot = 0.0;
+    if (threadIdx.x == 0)
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) tot += sh[w];
+    __syncthreads();
+    return tot;
+}
+
+__global__ void blur_kpm_kernel(const double *__restrict__ P, int N_q, double c, double d,
+                                double sigma, double x0, double h, int N_x, double *out) {
+    const double inv_s = 1.0 / sigma, norm = 1.0 / sqrt(2.0 * M_PI * sigma * sigma);
+    for (int m = blockIdx.x; m < N_x; m += gridDim.x) {
+        const double x = x0 + m * h;
+        double s = 0.0;
+        for (int i = threadIdx.x; i < N_q; i += blockDim.x) {
+            const double ti = cospi((i + 0.5) / (double)N_q);
+            s += P[i] * gauss(x - c - d * ti, inv_s, norm);
+        }
+        s = block_sum_d(s);
+        if (threadIdx.x == 0) out[m] = s / N_q;
+    }
+}
+
+__global__ void blur_eigs_kernel(const double *__restrict__ eig, int64_t n_eig, double sigma,
+                                 double x0, double h, int N_x, double *out) {
+    const double inv_s = 1.0 / sigma, norm = 1.0 / sqrt(2.0 * M_PI * sigma * sigma);
+    for (int m = blockIdx.x; m < N_x; m += gridDim.x) {
+        const double x = x0 + m * h;
+        double s = 0.0;
+        for (int64_t j = threadIdx.x; j < n_eig; j += blockDim.x) s += gauss(x - eig[j], inv_s, norm);
+        s = block_sum_d(s);
+        if (threadIdx.x == 0) out[m] = s / (double)n_eig;
+    }
+}
+
+__global__ void error_norms_kernel(const double *__restrict__ a, const double *__restrict__ b,
+                                   int N_x, double h, double *out) {
+    __shared__ double smax[32];
+    double s = 0.0, mx = 0.0;
+    for (int m = threadIdx.x; m < N_x; m += blockDim.x) {
+        const double v = fabs(a[m] - b[m]);
+        s += (m == 0 || m == N_x - 1) ? 0.5 * v : v;
+        mx = fmax(mx, v);
+    }
+    for (int off = 16; off > 0; off >>= 1) mx = fmax(mx, __shfl_down_sync(0xffffffffu, mx, off));
+    if ((threadIdx.x & 31) == 0) smax[threadIdx.x >> 5] = mx;
+    s = block_sum_d(s);
+    if (threadIdx.x == 0) {
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) mx = fmax(mx, smax[w]);
+        out[0] = h * s;
+        out[1] = mx;
+    }
+}
+
+int grid_cap(int64_t work, int block, int cap) {
+    int64_t g = (work + block - 1) / block;
+    return (int)(g < 1 ? 1 : (g > cap ? cap : g));
+}
+
+}  // namespace
+
+void launch_reconstruct(const double *mu, int M, int damping, double lb, double ub,
+                        const double *t, int N_t, double *coef_scratch, double *phi_hat,
+                        double *phi_lambda, cudaStream_t s) {
+    coef_kernel<<<grid_cap(M + 1, 256, 1024), 256, 0, s>>>(mu, M, damping, coef_scratch);
+    DOS_LAUNCHED();
+    reconstruct_kernel<<<grid_cap(N_t, 256, 4096), 256, 0, s>>>(
+        coef_scratch, M, 0.5 * (ub - lb), t, N_t, phi_hat, phi_lambda);
+    DOS_LAUNCHED();
+}
+
+// poly_scratch: (M+1) coefficients followed by N_q node values.
+void launch_blur_kpm(const double *mu, int M, int damping, double lb, double ub, double sigma,
+                     int N_q, double x0, double h, int N_x, double *poly_scratch, double *out,
+                     cudaStream_t s) {
+    double *a = poly_scratch, *P = poly_scratch + (M + 1);
+    coef_kernel<<<grid_cap(M + 1, 256, 1024), 256, 0, s>>>(mu, M, damping, a);
+    DOS_LAUNCHED();
+    nodes_kernel<<<grid_cap(N_q, 256, 4096), 256, 0, s>>>(a, M, N_q, P);
+    DOS_LAUNCHED();
+    blur_kpm_kernel<<<N_x < 65535 ? N_x : 65535, 256, 0, s>>>(P, N_q, 0.5 * (lb + ub),
+                                                               0.5 * (ub - lb), sigma, x0, h,
+                                                               N_x, out);
+    DOS_LAUNCHED();
+}
+
+void launch_blur_eigs(const double *eig, int64_t n_eig, double sigma, double x0, double h,
+                      int N_x, double *out, cudaStream_t s) {
+    blur_eigs_kernel<<<N_x < 65535 ? N_x : 65535, 256, 0, s>>>(eig, n_eig, sigma, x0, h, N_x,
+                                                                out);
+    DOS_LAUNCHED();
+}
+
+void launch_error_norms(const double *a, const double *b, int N_x, double h, double *out,
+                        cudaStream_t s) {
+    error_norms_kernel<<<1, 1024, 0, s>>>(a, b, N_x, h, out);
+    DOS_LAUNCHED();
+}
+
+}  // namespace dos

@@ -1,0 +1,665 @@
+// Kernels of the Chebyshev moment sweep (steps a2-a5 of the KPM path).
+//
+// Data layout in HBM
+//   vector blocks X (two of them): row-major, n_rows x ld, element (i, l) at
+//   X[i*ld + l]; ld = n_v rounded up to a 16-byte multiple, pad columns zero.
+//   A nonzero a_ij therefore feeds all n_v right-hand sides from one
+//   contiguous row X[j, :], read with 16-byte vector loads by a "team" of
+//   threads that shares the matrix row.
+//   The recurrence writes X_{k+1} over X_{k-1} in place (same thread reads the
+//   old value and writes the new one), so two blocks suffice.
+//
+// One launch per Chebyshev step k computes, in a single pass over A:
+//   X_{k+1} = 2 (A X_k - c X_k)/d - X_{k-1}        (k >= 1, Eq. 3term with B = (A-cI)/d)
+//   X_1     =   (A X_0 - c X_0)/d                   (k = 0, Algorithm 1)
+// and the per-vector dot products of the doubling identity (Appendix A):
+//   r_k = X_{k+1} . X_k  -> mu_{2k+1} = 2 r_k/n - mu_1   (mu_1 = r_0/n)
+//   s_k = X_{k+1} . X_{k+1} -> mu_{2k+2} = 2 s_k/n - mu_0
+//   z   = X_0 . X_0 (k = 0 only) -> mu_0.
+// Partial sums are written per tile (one tile per block) and reduced later in
+// a fixed order, so results are bitwise reproducible for a given launch shape.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "dos_internal.h"
+
+namespace dos {
+namespace {
+
+constexpr int kBlock = 256;
+
+// ---- splitmix64 (Steele, Lea, Flood 2014), device side -------------------------
+__device__ __forceinline__ uint64_t sm64_mix(uint64_t z) {
+    z ^= z >> 30;
+    z *= 0xbf58476d1ce4e5b9ULL;
+    z ^= z >> 27;
+    z *= 0x94d049bb133111ebULL;
+    z ^= z >> 31;
+    return z;
+}
+// Word number ctr+1 of the stream seeded with `seed`.
+__device__ __forceinline__ uint64_t rademacher_word(uint64_t seed, uint64_t b, uint64_t word,
+                                                    uint64_t row) {
+    const uint64_t ctr = (b << 48) + (word << 32) + row;
+    return sm64_mix(seed + (ctr + 1ULL) * 0x9e3779b97f4a7c15ULL);
+}
+
+// ---- unevaluated float pair accumulator ---------------------------------------
+// sum = hi + lo.  Each product x*y of two floats is split exactly into
+// p + pe (fma), p is added to hi with Knuth's branch-free two-sum, and both
+// rounding errors go to lo.  The __f*_rn intrinsics keep the compiler from
+// contracting the error-free steps into fused operations.
+struct FF {
+    float hi, lo;
+};
+__device__ __forceinline__ void ff_add_prod(FF &a, float x, float y) {
+    const float p = __fmul_rn(x, y);
+    const float pe = fmaf(x, y, -p);
+    const float s = __fadd_rn(a.hi, p);
+    const float bb = __fsub_rn(s, a.hi);
+    const float e = __fadd_rn(__fsub_rn(a.hi, __fsub_rn(s, bb)), __fsub_rn(p, bb));
+    a.hi = s;
+    a.lo = __fadd_rn(a.lo, __fadd_rn(e, pe));
+}
+__device__ __forceinline__ double acc_value(const FF &a) { return (double)a.hi + (double)a.lo; }
+__device__ __forceinline__ void acc_zero(FF &a) { a.hi = 0.f; a.lo = 0.f; }
+__device__ __forceinline__ void acc_add_prod(FF &a, float x, float y) { ff_add_prod(a, x, y); }
+
+__device__ __forceinline__ double acc_value(const double &a) { return a; }
+__device__ __forceinline__ void acc_zero(double &a) { a = 0.0; }
+__device__ __forceinline__ void acc_add_prod(double &a, double x, double y) { a = fma(x, y, a); }
+
+template <typename T> struct Traits;
+template <> struct Traits<float> {
+    static constexpr int VPT = 4;
+    using Acc = FF;
+};
+template <> struct Traits<double> {
+    static constexpr int VPT = 2;
+    using Acc = double;
+};
+
+template <typename T>
+__device__ __forceinline__ void load16(const T *p, T (&v)[Traits<T>::VPT]) {
+    if constexpr (sizeof(T) == 4) {
+        const float4 t = *reinterpret_cast<const float4 *>(p);
+        v[0] = t.x; v[1] = t.y; v[2] = t.z; v[3] = t.w;
+    } else {
+        const double2 t = *reinterpret_cast<const double2 *>(p);
+        v[0] = t.x; v[1] = t.y;
+    }
+}
+template <typename T>
+__device__ __forceinline__ void store16(T *p, const T (&v)[Traits<T>::VPT]) {
+    if constexpr (sizeof(T) == 4) {
+        *reinterpret_cast<float4 *>(p) = make_float4(v[0], v[1], v[2], v[3]);
+    } else {
+        *reinterpret_cast<double2 *>(p) = make_double2(v[0], v[1]);
+    }
+}
+
+// ---- start vectors (step a2) ---------------------------------------------------
+template <typename T>
+__global__ void init_vectors_kernel(T *__restrict__ x, int64_t n_rows, int ld, int n_v, int B,
+                                    const int32_t *__restrict__ seg_row0, uint64_t seed,
+                                    int64_t vec_offset, uint64_t b0) {
+    constexpr int VPT = Traits<T>::VPT;
+    const int chunks = ld / VPT;
+    const int64_t total = n_rows * chunks;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t row = t / chunks;
+        const int ch = (int)(t - row * chunks);
+        // segment of this row
+        int lo = 0, hi = B;  // seg_row0[lo] <= row < seg_row0[hi]
+        while (hi - lo > 1) {
+            const int mid = (lo + hi) >> 1;
+            if (seg_row0[mid] <= row) lo = mid; else hi = mid;
+        }
+        const uint64_t local = (uint64_t)(row - seg_row0[lo]);
+        T v[VPT];
+        uint64_t cached_word = ~0ULL, bits = 0;
+#pragma unroll
+        for (int j = 0; j < VPT; ++j) {
+            const int l = ch * VPT + j;
+            if (l < n_v) {
+                const uint64_t gl = (uint64_t)(vec_offset + l);
+                if ((gl >> 6) != cached_word) {
+                    cached_word = gl >> 6;
+                    bits = rademacher_word(seed, b0 + (uint64_t)lo, cached_word, local);
+                }
+                v[j] = ((bits >> (gl & 63)) & 1ULL) ? T(-1) : T(1);
+            } else {
+                v[j] = T(0);
+            }
+        }
+        store16(x + row * ld + ch * VPT, v);
+    }
+}
+
+// ---- fused step (steps a3, a4) ---------------------------------------------------
+template <typename T>
+struct StepParams {
+    const int32_t *row_ptr;
+    const int32_t *col_idx;
+    const T *val;
+    const T *xc;  // X_k
+    T *xn;        // X_{k-1} on entry, X_{k+1} on exit
+    int ld, n_chunks, pv, first;
+    const int4 *tiles;
+    const int32_t *seg_row0;
+    const double *seg_c, *seg_inv_d;
+    double *part;   // [n_tiles][2][pv]
+    double *part0;  // [n_tiles][pv]
+};
+
+// Deterministic block reduction of one accumulator set into out[0..pv).
+// red: shared scratch of (blockDim/32) * ld doubles.
+template <typename Acc, int G, int CPT, int VPT>
+__device__ __forceinline__ void block_reduce_store(const Acc (&acc)[CPT][VPT], double *out,
+                                                   int ld, int n_chunks, int pv, double *red) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int n_warps = blockDim.x >> 5;
+    const int g = lane % G;
+    double v[CPT][VPT];
+#pragma unroll
+    for (int c = 0; c < CPT; ++c)
+#pragma unroll
+        for (int j = 0; j < VPT; ++j) v[c][j] = acc_value(acc[c][j]);
+    // sum over the teams of this warp (fixed tree)
+#pragma unroll
+    for (int off = G; off < 32; off <<= 1)
+#pragma unroll
+        for (int c = 0; c < CPT; ++c)
+#pragma unroll
+            for (int j = 0; j < VPT; ++j) v[c][j] += __shfl_down_sync(0xffffffffu, v[c][j], off);
+    if (lane < G) {
+#pragma unroll
+        for (int c = 0; c < CPT; ++c) {
+            const int ch = g + c * G;
+            if (ch < n_chunks)
+#pragma unroll
+                for (int j = 0; j < VPT; ++j) red[warp * ld + ch * VPT + j] = v[c][j];
+        }
+    }
+    __syncthreads();
+    if (pv > 1) {
+        for (int col = threadIdx.x; col < ld; col += blockDim.x) {
+            double s = 0.0;
+            for (int w = 0; w < n_warps; ++w) s += red[w * ld + col];
+            out[col] = s;
+        }
+    } else {
+        // columns summed over warps, then over columns by warp 0 (fixed order)
+        for (int col = threadIdx.x; col < ld; col += blockDim.x) {
+            double s = 0.0;
+            for (int w = 0; w < n_warps; ++w) s += red[w * ld + col];
+            red[col] = s;  // column `col` of warp 0's row is only read by this thread
+        }
+        __syncthreads();
+        if (warp == 0) {
+            double s = 0.0;
+            for (int col = lane; col < ld; col += 32) s += red[col];
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1) s += __shfl_down_sync(0xffffffffu, s, off);
+            if (lane == 0) out[0] = s;
+        }
+    }
+    __syncthreads();
+}
+
+template <typename T, int G, int CPT>
+__global__ void __launch_bounds__(kBlock) step_kernel(const StepParams<T> p) {
+    constexpr int VPT = Traits<T>::VPT;
+    using Acc = typename Traits<T>::Acc;
+    constexpr int TPW = 32 / G;  // teams per warp
+    extern __shared__ double red[];
+
+    const int4 tl = p.tiles[blockIdx.x];
+    const int rb = tl.x, re = tl.y, seg = tl.z;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int g = lane % G;
+    const int n_teams = (blockDim.x >> 5) * TPW;
+    const int team = warp * TPW + lane / G;
+    const T c = (T)p.seg_c[seg];
+    const T inv_d = (T)p.seg_inv_d[seg];
+    const int ld = p.ld;
+    const T *__restrict__ xseg = p.xc + (size_t)p.seg_row0[seg] * ld;
+    const T *__restrict__ xc = p.xc;
+    T *xn = p.xn;
+
+    Acc accR[CPT][VPT], accS[CPT][VPT], acc0[CPT][VPT];
+#pragma unroll
+    for (int cc = 0; cc < CPT; ++cc)
+#pragma unroll
+        for (int j = 0; j < VPT; ++j) {
+            acc_zero(accR[cc][j]);
+            acc_zero(accS[cc][j]);
+            acc_zero(acc0[cc][j]);
+        }
+
+    bool valid[CPT];
+#pragma unroll
+    for (int cc = 0; cc < CPT; ++cc) valid[cc] = (g + cc * G) < p.n_chunks;
+
+    for (int row = rb + team; row < re; row += n_teams) {
+        const int e0 = __ldg(p.row_ptr + row), e1 = __ldg(p.row_ptr + row + 1);
+        T y[CPT][VPT];
+#pragma unroll
+        for (int cc = 0; cc < CPT; ++cc)
+#pragma unroll
+            for (int j = 0; j < VPT; ++j) y[cc][j] = T(0);
+        for (int e = e0; e < e1; e += 4) {
+            int col[4];
+            T a[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const bool ok = e + u < e1;
+                col[u] = ok ? __ldg(p.col_idx + e + u) : 0;
+                a[u] = ok ? __ldg(p.val + e + u) : T(0);
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                if (e + u < e1) {
+                    const T *src = xseg + (size_t)col[u] * ld;
+#pragma unroll
+                    for (int cc = 0; cc < CPT; ++cc) {
+                        if (valid[cc]) {
+                            T xv[VPT];
+                            load16(src + (g + cc * G) * VPT, xv);
+#pragma unroll
+                            for (int j = 0; j < VPT; ++j) y[cc][j] = fma(a[u], xv[j], y[cc][j]);
+                        }
+                    }
+                }
+            }
+        }
+        const size_t roff = (size_t)row * ld;
+#pragma unroll
+        for (int cc = 0; cc < CPT; ++cc) {
+            if (!valid[cc]) continue;
+            const int off = (g + cc * G) * VPT;
+            T xk[VPT], xo[VPT], xnew[VPT];
+            load16(xc + roff + off, xk);
+            if (p.first) {
+#pragma unroll
+                for (int j = 0; j < VPT; ++j) xnew[j] = fma(-c, xk[j], y[cc][j]) * inv_d;
+            } else {
+                load16(xn + roff + off, xo);
+#pragma unroll
+                for (int j = 0; j < VPT; ++j)
+                    xnew[j] = fma(T(2), fma(-c, xk[j], y[cc][j]) * inv_d, -xo[j]);
+            }
+            store16(xn + roff + off, xnew);
+#pragma unroll
+            for (int j = 0; j < VPT; ++j) {
+                acc_add_prod(accR[cc][j], xnew[j], xk[j]);
+                acc_add_prod(accS[cc][j], xnew[j], xnew[j]);
+                if (p.first) acc_add_prod(acc0[cc][j], xk[j], xk[j]);
+            }
+        }
+    }
+
+    double *out = p.part + (size_t)blockIdx.x * 2 * p.pv;
+    block_reduce_store<Acc, G, CPT, VPT>(accR, out, ld, p.n_chunks, p.pv, red);
+    block_reduce_store<Acc, G, CPT, VPT>(accS, out + p.pv, ld, p.n_chunks, p.pv, red);
+    if (p.first)
+        block_reduce_store<Acc, G, CPT, VPT>(acc0, p.part0 + (size_t)blockIdx.x * p.pv, ld,
+                                             p.n_chunks, p.pv, red);
+}
+
+// ---- kernel table --------------------------------------------------------------
+template <typename T>
+using StepFn = void (*)(const StepParams<T>);
+
+template <typename T>
+StepFn<T> pick(int G, int CPT) {
+#define DOS_CASE(GG, CC) \
+    if (G == GG && CPT == CC) return step_kernel<T, GG, CC>;
+#define DOS_CASES(GG) DOS_CASE(GG, 1) DOS_CASE(GG, 2) DOS_CASE(GG, 4)
+    DOS_CASES(1) DOS_CASES(2) DOS_CASES(4) DOS_CASES(8) DOS_CASES(16) DOS_CASES(32)
+#undef DOS_CASES
+#undef DOS_CASE
+    return nullptr;
+}
+
+size_t step_smem(int block, int ld) { return (size_t)(block / 32) * ld * sizeof(double); }
+
+// ---- tiles ---------------------------------------------------------------------
+__device__ __forceinline__ int64_t tile_boundary(const int32_t *row_ptr, int R0, int R1, int j,
+                                                 int T, int row_cost) {
+    if (j <= 0) return R0;
+    if (j >= T) return R1;
+    const int64_t base = row_ptr[R0];
+    const int64_t total = (int64_t)(row_ptr[R1] - base) + (int64_t)row_cost * (R1 - R0);
+    // smallest r in [R0, R1] with cost(r) * T >= j * total
+    int lo = R0, hi = R1;
+    while (lo < hi) {
+        const int mid = lo + ((hi - lo) >> 1);
+        const int64_t cost = (int64_t)(row_ptr[mid] - base) + (int64_t)row_cost * (mid - R0);
+        if (cost * T >= (int64_t)j * total) hi = mid; else lo = mid + 1;
+    }
+    return lo;
+}
+
+__global__ void make_tiles_kernel(const int32_t *__restrict__ row_ptr, int B,
+                                  const int32_t *__restrict__ seg_row0,
+                                  const int32_t *__restrict__ seg_tile_begin, int n_tiles,
+                                  int row_cost, int4 *__restrict__ tiles) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n_tiles) return;
+    int lo = 0, hi = B;  // seg_tile_begin[lo] <= t < seg_tile_begin[hi]
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (seg_tile_begin[mid] <= t) lo = mid; else hi = mid;
+    }
+    const int T = seg_tile_begin[lo + 1] - seg_tile_begin[lo];
+    const int j = t - seg_tile_begin[lo];
+    const int R0 = seg_row0[lo], R1 = seg_row0[lo + 1];
+    tiles[t] = make_int4((int)tile_boundary(row_ptr, R0, R1, j, T, row_cost),
+                         (int)tile_boundary(row_ptr, R0, R1, j + 1, T, row_cost), lo, 0);
+}
+
+// ---- reduction over tiles (step a5) ---------------------------------------------
+// grid.x = count*2 (step, dot), grid.y = segment.  partial slices are [slot][tile][2][pv].
+__global__ void reduce_kernel(const double *__restrict__ partial, int n_tiles, int pv, int ncols,
+                              const int32_t *__restrict__ seg_tile_begin, int k0, int slot0,
+                              int slots, int steps_total, int col_offset, int dst_pv,
+                              int accumulate, double *__restrict__ dotsum) {
+    __shared__ double sh[32];
+    const int kk = blockIdx.x >> 1, dot = blockIdx.x & 1, seg = blockIdx.y;
+    const int k = k0 + kk;
+    const int slot = (slot0 + kk) % slots;
+    const int tb = seg_tile_begin[seg], te = seg_tile_begin[seg + 1];
+    const double *src = partial + (size_t)slot * n_tiles * 2 * pv;
+    double *dst = dotsum + (((size_t)seg * steps_total + k) * 2 + dot) * dst_pv;
+    if (pv > 1) {
+        for (int col = threadIdx.x; col < ncols; col += blockDim.x) {
+            double s = 0.0;
+            for (int t = tb; t < te; ++t) s += src[((size_t)t * 2 + dot) * pv + col];
+            dst[col_offset + col] = s;
+        }
+    } else {
+        double s = 0.0;
+        for (int t = tb + threadIdx.x; t < te; t += blockDim.x) s += src[(size_t)t * 2 + dot];
+        for (int off = 16; off > 0; off >>= 1) s += __shfl_down_sync(0xffffffffu, s, off);
+        if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = s;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double tot = 0.0;
+            for (int w = 0; w < (int)(blockDim.x >> 5); ++w) tot += sh[w];
+            dst[0] = accumulate ? dst[0] + tot : tot;
+        }
+    }
+}
+
+// mu_0 partials: [tile][pv] -> dotsum0[seg][dst_pv]
+__global__ void reduce0_kernel(const double *__restrict__ part0, int pv, int ncols,
+                               const int32_t *__restrict__ seg_tile_begin, int col_offset,
+                               int dst_pv, int accumulate, double *__restrict__ dotsum0) {
+    __shared__ double sh[32];
+    const int seg = blockIdx.x;
+    const int tb = seg_tile_begin[seg], te = seg_tile_begin[seg + 1];
+    double *dst = dotsum0 + (size_t)seg * dst_pv;
+    if (pv > 1) {
+        for (int col = threadIdx.x; col < ncols; col += blockDim.x) {
+            double s = 0.0;
+            for (int t = tb; t < te; ++t) s += part0[(size_t)t * pv + col];
+            dst[col_offset + col] = s;
+        }
+    } else {
+        double s = 0.0;
+        for (int t = tb + threadIdx.x; t < te; t += blockDim.x) s += part0[t];
+        for (int off = 16; off > 0; off >>= 1) s += __shfl_down_sync(0xffffffffu, s, off);
+        if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = s;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double tot = 0.0;
+            for (int w = 0; w < (int)(blockDim.x >> 5); ++w) tot += sh[w];
+            dst[0] = accumulate ? dst[0] + tot : tot;
+        }
+    }
+}
+
+// ---- moments from dot products (step a5) -------------------------------------------
+// dotsum[seg][k][2][pvt], dotsum0[seg][pvt]; pvt = n_v (per-vector) or 1 (totals).
+__device__ __forceinline__ double moment_from(int k, double z, const double *ds, int pvt,
+                                              int col, double N, double mu0, double mu1) {
+    if (k == 0) return z / N;
+    const int step = (k - 1) >> 1;       // step producing mu_k
+    const int dot = (k & 1) ? 0 : 1;     // odd k: r (X_{s+1}.X_s), even: s (X_{s+1}.X_{s+1})
+    const double v = ds[((size_t)step * 2 + dot) * pvt + col];
+    if (k == 1) return v / N;
+    return 2.0 * v / N - ((k & 1) ? mu1 : mu0);
+}
+
+__global__ void finalize_kernel(const double *__restrict__ dotsum,
+                                const double *__restrict__ dotsum0,
+                                const int32_t *__restrict__ seg_row0, int M, int steps_total,
+                                int n_v, int pvt, double *__restrict__ mu,
+                                double *__restrict__ mu_pv, double tol, int *status) {
+    const int seg = blockIdx.x;
+    const double n = (double)(seg_row0[seg + 1] - seg_row0[seg]);
+    const double *ds = dotsum + (size_t)seg * steps_total * 2 * pvt;
+    const double *d0 = dotsum0 + (size_t)seg * pvt;
+    // totals
+    __shared__ double tot_z, tot_r0;
+    if (threadIdx.x == 0) {
+        double z = 0.0, r0 = 0.0;
+        for (int l = 0; l < pvt; ++l) {
+            z += d0[l];
+            r0 += ds[l];  // step 0, dot 0
+        }
+        tot_z = z;
+        tot_r0 = r0;
+    }
+    __syncthreads();
+    const double N = n * (double)n_v;
+    const double mu0 = tot_z / N, mu1 = tot_r0 / N;
+    for (int k = threadIdx.x; k <= M; k += blockDim.x) {
+        double m;
+        if (pvt == 1) {
+            m = moment_from(k, tot_z, ds, 1, 0, N, mu0, mu1);
+        } else if (k == 0) {
+            m = mu0;
+        } else {
+            const int step = (k - 1) >> 1, dot = (k & 1) ? 0 : 1;
+            double v = 0.0;
+            for (int l = 0; l < pvt; ++l) v += ds[((size_t)step * 2 + dot) * pvt + l];
+            m = (k == 1) ? v / N : 2.0 * v / N - ((k & 1) ? mu1 : mu0);
+        }
+        mu[(size_t)seg * (M + 1) + k] = m;
+        if (!(fabs(m) <= mu0 * (1.0 + tol))) atomicOr(status, 2);
+    }
+    if (mu_pv != nullptr && pvt > 1) {
+        for (int idx = threadIdx.x; idx < n_v * (M + 1); idx += blockDim.x) {
+            const int l = idx / (M + 1), k = idx - l * (M + 1);
+            const double z = d0[l];
+            const double m0 = z / n, m1 = ds[l] / n;
+            mu_pv[((size_t)seg * n_v + l) * (M + 1) + k] =
+                moment_from(k, z, ds, pvt, l, n, m0, m1);
+        }
+    }
+}
+
+__global__ void f64_to_f32_kernel(const double *__restrict__ in, float *__restrict__ out,
+                                  int64_t count) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < count;
+         i += (int64_t)gridDim.x * blockDim.x)
+        out[i] = (float)in[i];
+}
+
+__global__ void validate_kernel(int64_t n_rows, int64_t nnz, const int32_t *__restrict__ row_ptr,
+                                const int32_t *__restrict__ col_idx, int B,
+                                const int32_t *__restrict__ seg_row0, int *flag) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n_rows;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t a = row_ptr[i], b = row_ptr[i + 1];
+        if (i == 0 && a != 0) { atomicOr(flag, 1); continue; }
+        if (i == n_rows - 1 && b != nnz) { atomicOr(flag, 1); continue; }
+        if (b < a || a < 0 || b > nnz) { atomicOr(flag, 1); continue; }
+        int lo = 0, hi = B;
+        while (hi - lo > 1) {
+            const int mid = (lo + hi) >> 1;
+            if (seg_row0[mid] <= i) lo = mid; else hi = mid;
+        }
+        const int64_t n_seg = seg_row0[lo + 1] - seg_row0[lo];
+        for (int64_t e = a; e < b; ++e) {
+            const int32_t cidx = col_idx[e];
+            if (cidx < 0 || cidx >= n_seg) { atomicOr(flag, 1); break; }
+        }
+    }
+}
+
+int grid_for(int64_t work, int block, int cap) {
+    int64_t g = (work + block - 1) / block;
+    if (g < 1) g = 1;
+    if (g > cap) g = cap;
+    return (int)g;
+}
+
+}  // namespace
+
+// ---- launchers -------------------------------------------------------------------
+void launch_validate_csr(int64_t n_rows, int64_t nnz, const int32_t *row_ptr,
+                         const int32_t *col_idx, int B, const int32_t *seg_row0, int *flag,
+                         cudaStream_t s) {
+    validate_kernel<<<grid_for(n_rows, 256, 65535), 256, 0, s>>>(n_rows, nnz, row_ptr, col_idx,
+                                                                  B, seg_row0, flag);
+    DOS_LAUNCHED();
+}
+
+void launch_f64_to_f32(const double *in, float *out, int64_t count, cudaStream_t s) {
+    f64_to_f32_kernel<<<grid_for(count, 256, 65535), 256, 0, s>>>(in, out, count);
+    DOS_LAUNCHED();
+}
+
+void launch_make_tiles(const int32_t *row_ptr, int B, const int32_t *seg_row0,
+                       const int32_t *seg_tile_begin, int n_tiles, int row_cost, int4 *tiles,
+                       cudaStream_t s) {
+    make_tiles_kernel<<<(n_tiles + 255) / 256, 256, 0, s>>>(row_ptr, B, seg_row0, seg_tile_begin,
+                                                            n_tiles, row_cost, tiles);
+    DOS_LAUNCHED();
+}
+
+bool shape_supported(int precision, const Shape &sh, int ld) {
+    const int vpt = precision == DOS_PREC_F64 ? 2 : 4;
+    if (sh.block != kBlock) return false;
+    if (sh.team < 1 || sh.team > 32 || (sh.team & (sh.team - 1))) return false;
+    if (sh.chunks != 1 && sh.chunks != 2 && sh.chunks != 4) return false;
+    if (sh.tiles < 1) return false;
+    return sh.team * sh.chunks * vpt >= ld;
+}
+
+int max_active_blocks(int precision, const Shape &sh) {
+    int nb = 0;
+    if (precision == DOS_PREC_F64) {
+        auto fn = pick<double>(sh.team, sh.chunks);
+        if (!fn) return 0;
+        DOS_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, sh.block,
+                                                                    step_smem(sh.block, 256)));
+    } else {
+        auto fn = pick<float>(sh.team, sh.chunks);
+        if (!fn) return 0;
+        DOS_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, sh.block,
+                                                                    step_smem(sh.block, 256)));
+    }
+    return nb;
+}
+
+Shape default_shape(int precision, int ld, int num_sms, int64_t n_rows) {
+    const int vpt = precision == DOS_PREC_F64 ? 2 : 4;
+    const int chunks = ld / vpt;
+    Shape sh;
+    sh.block = kBlock;
+    if (chunks <= 32) {
+        int g = 1;
+        while (g < chunks) g <<= 1;
+        sh.team = g;
+        sh.chunks = 1;
+    } else {
+        sh.team = 32;
+        sh.chunks = chunks <= 64 ? 2 : 4;
+    }
+    const int occ = max_active_blocks(precision, sh);
+    const int teams = (kBlock / 32) * (32 / sh.team);
+    int64_t tiles = (int64_t)num_sms * (occ > 0 ? occ : 1);
+    const int64_t max_tiles = (n_rows + teams - 1) / teams;
+    if (tiles > max_tiles) tiles = max_tiles;
+    if (tiles < 1) tiles = 1;
+    sh.tiles = (int)tiles;
+    return sh;
+}
+
+void launch_init_vectors(const SweepArgs &a, cudaStream_t s) {
+    const int vpt = a.precision == DOS_PREC_F64 ? 2 : 4;
+    const int64_t work = a.n_rows * (a.ld / vpt);
+    const int grid = grid_for(work, 256, 152 * 32);
+    if (a.precision == DOS_PREC_F64)
+        init_vectors_kernel<double><<<grid, 256, 0, s>>>((double *)a.x0, a.n_rows, a.ld, a.n_v,
+                                                         a.B, a.seg_row0, a.seed, a.vec_offset,
+                                                         a.batch_index);
+    else
+        init_vectors_kernel<float><<<grid, 256, 0, s>>>((float *)a.x0, a.n_rows, a.ld, a.n_v, a.B,
+                                                        a.seg_row0, a.seed, a.vec_offset,
+                                                        a.batch_index);
+    DOS_LAUNCHED();
+}
+
+template <typename T>
+static void launch_step_t(const SweepArgs &a, int k, int slot, cudaStream_t s) {
+    StepParams<T> p;
+    p.row_ptr = a.row_ptr;
+    p.col_idx = a.col_idx;
+    p.val = (const T *)a.val;
+    T *blk[2] = {(T *)a.x0, (T *)a.x1};
+    p.xc = blk[k & 1];
+    p.xn = blk[(k + 1) & 1];
+    p.ld = a.ld;
+    p.n_chunks = a.ld / Traits<T>::VPT;
+    p.pv = a.per_vec ? a.ld : 1;
+    p.first = k == 0;
+    p.tiles = a.tiles;
+    p.seg_row0 = a.seg_row0;
+    p.seg_c = a.seg_c;
+    p.seg_inv_d = a.seg_inv_d;
+    p.part = a.partial + (size_t)slot * a.n_tiles * 2 * p.pv;
+    p.part0 = a.partial0;
+    auto fn = pick<T>(a.shape.team, a.shape.chunks);
+    if (!fn) throw Error{DOS_EINVAL, "unsupported launch shape"};
+    fn<<<a.n_tiles, a.shape.block, step_smem(a.shape.block, a.ld), s>>>(p);
+    DOS_LAUNCHED();
+}
+
+void launch_step(const SweepArgs &a, int k, int slot, cudaStream_t s) {
+    if (a.precision == DOS_PREC_F64) launch_step_t<double>(a, k, slot, s);
+    else launch_step_t<float>(a, k, slot, s);
+}
+
+void launch_reduce(const double *partial, int n_tiles, int pv, int ncols, int B,
+                   const int32_t *seg_tile_begin, int k0, int count, int slot0, int slots,
+                   int steps_total, int col_offset, int dst_pv, int accumulate, double *dotsum,
+                   cudaStream_t s) {
+    if (count <= 0) return;
+    dim3 grid(count * 2, B);
+    reduce_kernel<<<grid, 256, 0, s>>>(partial, n_tiles, pv, ncols, seg_tile_begin, k0, slot0,
+                                       slots, steps_total, col_offset, dst_pv, accumulate, dotsum);
+    DOS_LAUNCHED();
+}
+
+void launch_reduce0(const double *part0, int pv, int ncols, int B, const int32_t *seg_tile_begin,
+                    int col_offset, int dst_pv, int accumulate, double *dotsum0, cudaStream_t s) {
+    reduce0_kernel<<<B, 256, 0, s>>>(part0, pv, ncols, seg_tile_begin, col_offset, dst_pv,
+                                     accumulate, dotsum0);
+    DOS_LAUNCHED();
+}
+
+void launch_finalize(const double *dotsum, const double *dotsum0, const int32_t *seg_row0, int B,
+                     int M, int steps_total, int n_v, int pvt, double *mu, double *mu_pv,
+                     double tol, int *status, cudaStream_t s) {
+    finalize_kernel<<<B, 256, 0, s>>>(dotsum, dotsum0, seg_row0, M, steps_total, n_v, pvt, mu,
+                                      mu_pv, tol, status);
+    DOS_LAUNCHED();
+}
+
+}  // namespace dos

@@ -1,0 +1,308 @@
+"""Thin ctypes binding of libdos (include/dos.h): argument marshalling only.
+
+Every function forwards to the C entry point of the same name; all arithmetic
+runs in the library's CUDA kernels.  Arrays may be torch CUDA tensors (used in
+place, on the tensor's device and the current torch stream) or numpy arrays /
+CPU tensors (host memory: the library copies them).  If libdos.so is missing
+this module raises ImportError -- there is no fallback path.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_lib", "libdos.so")
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(
+        f"libdos.so not found at {LIB_PATH}: build it with "
+        "`python -m paper_1308_5467_gb300.build` (needs nvcc)")
+
+_lib = C.CDLL(LIB_PATH)
+
+DOS_OK, DOS_EINVAL, DOS_ENOMEM, DOS_ECUDA, DOS_ESPECTRUM, DOS_ETIMEOUT = range(6)
+DOS_F64, DOS_F32 = 0, 1
+DOS_DEVICE, DOS_HOST = 0, 1
+DOS_PREC_F64, DOS_PREC_F32_ACC64 = 0, 1
+DOS_BOUNDS_GERSHGORIN, DOS_BOUNDS_LANCZOS = 0, 1
+DOS_DAMP_NONE, DOS_DAMP_JACKSON = 0, 1
+DOS_OPT_NO_VALIDATE, DOS_OPT_NO_SPECTRUM_CHECK, DOS_OPT_NO_GRAPH, DOS_OPT_AUTOTUNE = 1, 2, 4, 8
+
+PRECISIONS = {"f64": DOS_PREC_F64, "f32": DOS_PREC_F32_ACC64}
+DAMPINGS = {"none": DOS_DAMP_NONE, "jackson": DOS_DAMP_JACKSON}
+BOUNDS = {"gershgorin": DOS_BOUNDS_GERSHGORIN, "lanczos": DOS_BOUNDS_LANCZOS}
+
+
+class dos_csr(C.Structure):
+    _fields_ = [("n", C.c_int64), ("nnz", C.c_int64), ("row_ptr", C.c_void_p),
+                ("col_idx", C.c_void_p), ("val", C.c_void_p), ("dtype", C.c_int32),
+                ("location", C.c_int32)]
+
+
+class dos_launch(C.Structure):
+    _fields_ = [("team", C.c_int32), ("chunks", C.c_int32), ("block", C.c_int32),
+                ("tiles", C.c_int32)]
+
+
+class dos_kpm_opts(C.Structure):
+    _fields_ = [("flags", C.c_uint32), ("vec_offset", C.c_int64), ("batch_index", C.c_uint64),
+                ("launch", dos_launch)]
+
+
+_vp, _i, _i64, _u64, _d = C.c_void_p, C.c_int, C.c_int64, C.c_uint64, C.c_double
+_dp = C.POINTER(C.c_double)
+_SIGS = {
+    "dos_ctx_create": (_i, [C.POINTER(_vp), _i]),
+    "dos_ctx_destroy": (_i, [_vp]),
+    "dos_last_error": (C.c_char_p, [_vp]),
+    "dos_status_string": (C.c_char_p, [_i]),
+    "dos_validate_csr": (_i, [_vp, C.POINTER(dos_csr), _vp]),
+    "dos_start_vectors": (_i, [_vp, _i64, _i, _u64, _u64, _i64, _i, _vp, _vp]),
+    "dos_profile_enable": (_i, [_vp, _i]),
+    "dos_profile_read": (_i, [_vp, _dp, C.POINTER(C.c_int64), C.POINTER(C.c_int64),
+                              C.POINTER(C.c_int64)]),
+    "dos_bounds": (_i, [_vp, C.POINTER(dos_csr), _i, _i, _u64, _d, _dp, _dp, _vp]),
+    "dos_kpm_moments": (_i, [_vp, C.POINTER(dos_csr), _d, _d, _i, _i, _u64, _i, _vp, _vp, _vp]),
+    "dos_kpm_moments_ex": (_i, [_vp, C.POINTER(dos_csr), _d, _d, _i, _i, _u64, _i, _vp, _vp,
+                                C.POINTER(dos_kpm_opts), _vp]),
+    "dos_kpm_moments_batched": (_i, [_vp, C.POINTER(dos_csr), _i, _vp, _vp, _vp, _i, _i, _u64,
+                                     _i, _vp, _vp, C.POINTER(dos_kpm_opts), _vp]),
+    "dos_tune": (_i, [_vp, C.POINTER(dos_csr), _i, _vp, _i, _i, C.POINTER(dos_launch), _dp, _vp]),
+    "dos_reconstruct": (_i, [_vp, _vp, _i, _i, _d, _d, _vp, _i, _vp, _vp, _vp]),
+    "dos_smoothed_error": (_i, [_vp, _vp, _i, _i, _d, _d, _vp, _i64, _vp, _i, _i, _d, _i, _dp,
+                                _dp, _vp]),
+}
+for _name, (_res, _args) in _SIGS.items():
+    _f = getattr(_lib, _name)
+    _f.restype = _res
+    _f.argtypes = _args
+
+
+class DosError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{_lib.dos_status_string(status).decode()}: {message}")
+        self.status = status
+
+
+def _is_torch(x) -> bool:
+    return type(x).__module__.startswith("torch")
+
+
+def _ptr(x):
+    """(pointer, is_device, keepalive) of a torch tensor or numpy array (None -> NULL)."""
+    if x is None:
+        return None, False, None
+    if _is_torch(x):
+        if not x.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return x.data_ptr(), x.is_cuda, x
+    a = np.ascontiguousarray(x)
+    return a.ctypes.data, False, a
+
+
+def _stream_of(*xs):
+    for x in xs:
+        if x is not None and _is_torch(x) and x.is_cuda:
+            import torch
+            return C.c_void_p(torch.cuda.current_stream(x.device).cuda_stream)
+    return C.c_void_p(0)
+
+
+class CSRArrays:
+    """A CSR matrix for the library: three arrays (torch CUDA tensors = device,
+    numpy arrays = host) plus n.  ``val`` dtype float64 or float32."""
+
+    def __init__(self, n: int, row_ptr, col_idx, val):
+        self.n = int(n)
+        self.row_ptr, self.col_idx, self.val = row_ptr, col_idx, val
+        rp, dev_rp, k0 = _ptr(row_ptr)
+        ci, dev_ci, k1 = _ptr(col_idx)
+        va, dev_va, k2 = _ptr(val)
+        if not (dev_rp == dev_ci == dev_va):
+            raise ValueError("row_ptr, col_idx and val must all be on the device or all on the host")
+        self._keep = (k0, k1, k2)
+        vdt = str(getattr(val, "dtype", "")).replace("torch.", "")
+        if vdt not in ("float64", "float32"):
+            raise ValueError("val must be float64 or float32")
+        nnz = int(col_idx.shape[0])
+        self.desc = dos_csr(self.n, nnz, rp, ci, va, DOS_F64 if vdt == "float64" else DOS_F32,
+                            DOS_DEVICE if dev_rp else DOS_HOST)
+        self.on_device = dev_rp
+
+    @classmethod
+    def from_synthetic(cls, A, device=None, dtype=None):
+        """From a synthetic.CSR; device=None keeps host numpy arrays."""
+        val = A.val if dtype is None else A.val.astype(dtype)
+        if device is None:
+            return cls(A.n, np.ascontiguousarray(A.row_ptr), np.ascontiguousarray(A.col_idx),
+                       np.ascontiguousarray(val))
+        import torch
+        return cls(A.n, torch.from_numpy(np.ascontiguousarray(A.row_ptr)).to(device),
+                   torch.from_numpy(np.ascontiguousarray(A.col_idx)).to(device),
+                   torch.from_numpy(np.ascontiguousarray(val)).to(device))
+
+
+class Context:
+    """One libdos context (dos_ctx) bound to a CUDA device."""
+
+    def __init__(self, device: int = 0):
+        h = C.c_void_p()
+        rc = _lib.dos_ctx_create(C.byref(h), int(device))
+        if rc != DOS_OK:
+            raise DosError(rc, "dos_ctx_create failed")
+        self._h = h
+        self.device = int(device)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _lib.dos_ctx_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def _check(self, rc: int):
+        if rc != DOS_OK:
+            raise DosError(rc, _lib.dos_last_error(self._h).decode())
+
+    def last_error(self) -> str:
+        return _lib.dos_last_error(self._h).decode()
+
+    # ---- entry points -----------------------------------------------------------
+    def dos_profile_enable(self, on: bool = True):
+        self._check(_lib.dos_profile_enable(self._h, 1 if on else 0))
+
+    def dos_profile_read(self):
+        """dict(step_ms, step_launches, sweeps, launches) accumulated since enabling."""
+        ms = C.c_double()
+        sl, sw, la = C.c_int64(), C.c_int64(), C.c_int64()
+        self._check(_lib.dos_profile_read(self._h, C.byref(ms), C.byref(sl), C.byref(sw),
+                                          C.byref(la)))
+        return {"step_ms": ms.value, "step_launches": sl.value, "sweeps": sw.value,
+                "launches": la.value}
+
+    def dos_validate_csr(self, A: CSRArrays):
+        self._check(_lib.dos_validate_csr(self._h, C.byref(A.desc), _stream_of(A.row_ptr)))
+
+    def dos_start_vectors(self, n: int, n_v: int, seed: int, batch_index: int = 0,
+                          vec_offset: int = 0, dtype="float64", out=None):
+        """(n, n_v) block of +-1 start vectors (numpy unless `out` is given)."""
+        if out is None:
+            out = np.empty((n, n_v), dtype=np.dtype(dtype))
+        dt = str(out.dtype).replace("torch.", "")
+        po, _, k = _ptr(out)
+        self._check(_lib.dos_start_vectors(self._h, int(n), int(n_v), int(seed), int(batch_index),
+                                           int(vec_offset), DOS_F64 if dt == "float64" else DOS_F32,
+                                           po, _stream_of(out)))
+        return out
+
+    def dos_bounds(self, A: CSRArrays, method="gershgorin", steps: int = 20, seed: int = 0,
+                   pad_frac: float = 0.01):
+        lb, ub = C.c_double(), C.c_double()
+        m = BOUNDS[method] if isinstance(method, str) else int(method)
+        self._check(_lib.dos_bounds(self._h, C.byref(A.desc), m, int(steps), int(seed),
+                                    float(pad_frac), C.byref(lb), C.byref(ub),
+                                    _stream_of(A.row_ptr)))
+        return lb.value, ub.value
+
+    def _opts(self, flags=0, vec_offset=0, batch_index=0, launch=None):
+        o = dos_kpm_opts()
+        o.flags = int(flags)
+        o.vec_offset = int(vec_offset)
+        o.batch_index = int(batch_index)
+        if launch:
+            o.launch = dos_launch(*[int(launch.get(k, 0)) for k in ("team", "chunks", "block", "tiles")])
+        return o
+
+    def dos_kpm_moments(self, A: CSRArrays, lb: float, ub: float, M: int, n_v: int, seed: int,
+                        precision="f64", mu=None, mu_per_vec=None, flags=0, vec_offset=0,
+                        batch_index=0, launch=None):
+        """Moments mu_0..mu_M (numpy float64 unless `mu` is given)."""
+        prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+        out = np.empty(M + 1, dtype=np.float64) if mu is None else mu
+        pmu, _, k0 = _ptr(out)
+        ppv, _, k1 = _ptr(mu_per_vec)
+        opts = self._opts(flags, vec_offset, batch_index, launch)
+        self._check(_lib.dos_kpm_moments_ex(self._h, C.byref(A.desc), float(lb), float(ub),
+                                            int(M), int(n_v), int(seed), prec, pmu, ppv,
+                                            C.byref(opts), _stream_of(A.row_ptr, out)))
+        return out
+
+    def dos_kpm_moments_batched(self, A: CSRArrays, seg_rows, lb, ub, M: int, n_v: int,
+                                seed: int, precision="f32", mu=None, mu_per_vec=None, flags=0,
+                                batch_index=0, launch=None):
+        prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+        seg = np.ascontiguousarray(seg_rows, dtype=np.int64)
+        B = seg.shape[0] - 1
+        lbv = np.ascontiguousarray(lb, dtype=np.float64)
+        ubv = np.ascontiguousarray(ub, dtype=np.float64)
+        out = np.empty((B, M + 1), dtype=np.float64) if mu is None else mu
+        pmu, _, k0 = _ptr(out)
+        ppv, _, k1 = _ptr(mu_per_vec)
+        opts = self._opts(flags, 0, batch_index, launch)
+        self._check(_lib.dos_kpm_moments_batched(self._h, C.byref(A.desc), B, seg.ctypes.data,
+                                                 lbv.ctypes.data, ubv.ctypes.data, int(M),
+                                                 int(n_v), int(seed), prec, pmu, ppv,
+                                                 C.byref(opts), _stream_of(A.row_ptr, out)))
+        return out
+
+    def dos_tune(self, A: CSRArrays, n_v: int, precision="f32", seg_rows=None):
+        prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+        best = dos_launch()
+        ms = C.c_double()
+        seg = None if seg_rows is None else np.ascontiguousarray(seg_rows, dtype=np.int64)
+        B = 1 if seg is None else seg.shape[0] - 1
+        self._check(_lib.dos_tune(self._h, C.byref(A.desc), B,
+                                  None if seg is None else seg.ctypes.data, int(n_v), prec,
+                                  C.byref(best), C.byref(ms), _stream_of(A.row_ptr)))
+        return {"team": best.team, "chunks": best.chunks, "block": best.block,
+                "tiles": best.tiles}, ms.value
+
+    def dos_reconstruct(self, mu, M: int, damping="jackson", lb: float = -1.0, ub: float = 1.0,
+                        t=None, N_t: int = 1000, phi_hat=None, phi_lambda=None,
+                        want_lambda: bool = False):
+        damp = DAMPINGS[damping] if isinstance(damping, str) else int(damping)
+        if t is not None:
+            N_t = int(t.shape[0])
+        out = np.empty(N_t, dtype=np.float64) if phi_hat is None else phi_hat
+        outl = phi_lambda
+        if outl is None and want_lambda:
+            outl = np.empty(N_t, dtype=np.float64)
+        pmu, _, k0 = _ptr(mu)
+        pt, _, k1 = _ptr(t)
+        po, _, k2 = _ptr(out)
+        pl, _, k3 = _ptr(outl)
+        self._check(_lib.dos_reconstruct(self._h, pmu, int(M), damp, float(lb), float(ub), pt,
+                                         int(N_t), po, pl, _stream_of(mu, out)))
+        return (out, outl) if want_lambda or phi_lambda is not None else out
+
+    def dos_smoothed_error(self, mu, M: int, damping, lb: float, ub: float, sigma: float,
+                           eig=None, ref_mu=None, ref_damping="jackson", N_x: int = 4000):
+        damp = DAMPINGS[damping] if isinstance(damping, str) else int(damping)
+        rdamp = DAMPINGS[ref_damping] if isinstance(ref_damping, str) else int(ref_damping)
+        pmu, _, k0 = _ptr(mu)
+        pe, _, k1 = _ptr(eig)
+        pr, _, k2 = _ptr(ref_mu)
+        n_eig = 0 if eig is None else int(eig.shape[0])
+        M_ref = -1 if ref_mu is None else int(ref_mu.shape[0]) - 1
+        e1, einf = C.c_double(), C.c_double()
+        self._check(_lib.dos_smoothed_error(self._h, pmu, int(M), damp, float(lb), float(ub), pe,
+                                            n_eig, pr, M_ref, rdamp, float(sigma), int(N_x),
+                                            C.byref(e1), C.byref(einf), _stream_of(mu)))
+        return e1.value, einf.value
+
+
+def status_string(status: int) -> str:
+    return _lib.dos_status_string(int(status)).decode()

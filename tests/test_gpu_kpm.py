@@ -1,0 +1,182 @@
+"""Parity of the CUDA moment sweep (steps a2-a5) with the CPU oracle.
+
+Every comparison runs the library through its C ABI (ctypes binding) and the
+oracle on the same seeded inputs.  Tolerances:
+  FP64 form:          1e-12 absolute per moment (moments are O(1); mu_0 = 1).
+  FP32-SpMM form:     the vectors are rounded to FP32 every step, so the error
+                      grows about linearly in k: we state |dmu_k| <= 2e-7 * (k + 1)
+                      + 1e-6 (i.e. <= 4.1e-5 at M = 200, 1e-4 at M = 500) against
+                      the FP64 oracle run on the FP32-rounded matrix values.
+"""
+import numpy as np
+import pytest
+
+from oracle import kpm as okpm
+from synthetic import anderson_3d, laplacian_2d, random_symmetric, diagonal
+
+pytestmark = pytest.mark.gpu
+
+TOL64 = 1e-12
+
+
+def tol32(M):
+    return 2e-7 * (np.arange(M + 1) + 1) + 1e-6
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need CUDA"
+    from paper_1308_5467_gb300 import dos
+    c = dos.Context(0)
+    yield c
+    c.close()
+
+
+def dev(A, dtype=None):
+    from paper_1308_5467_gb300 import dos
+    return dos.CSRArrays.from_synthetic(A, device="cuda", dtype=dtype)
+
+
+def test_start_vectors_golden(ctx):
+    rows = np.loadtxt("tests/golden/rademacher_signs.txt", dtype=np.int64)
+    for seed in np.unique(rows[:, 0]):
+        for b in np.unique(rows[:, 1]):
+            sel = rows[(rows[:, 0] == seed) & (rows[:, 1] == b)]
+            V = ctx.dos_start_vectors(16, 256, int(seed), batch_index=int(b))
+            for _, _, l, i, v in sel:
+                assert V[i, l] == v
+
+
+@pytest.mark.parametrize("n_v,off", [(1, 0), (5, 3), (64, 0), (100, 61), (300, 0)])
+def test_start_vectors_match_oracle(ctx, n_v, off):
+    V = ctx.dos_start_vectors(777, n_v, 42, batch_index=2, vec_offset=off)
+    W = okpm.start_block(777, n_v, 42, batch_index=2, vec_offset=off)
+    assert np.array_equal(V, W)
+    V32 = ctx.dos_start_vectors(777, n_v, 42, batch_index=2, vec_offset=off, dtype="float32")
+    assert np.array_equal(V32.astype(np.float64), W)
+
+
+def test_laplacian_40x40_f64_full_config(ctx):
+    """Config 1 at its full size: n = 1600, M = 100, n_v = 20, FP64."""
+    A = laplacian_2d(40)
+    lb, ub = -0.08, 8.08
+    pv = np.empty((20, 101))
+    mu = ctx.dos_kpm_moments(dev(A), lb, ub, 100, 20, seed=1, precision="f64", mu_per_vec=pv)
+    ref = okpm.kpm_moments_per_vector(A, lb, ub, 100, 20, seed=1)
+    assert np.abs(pv - ref).max() < TOL64
+    assert np.abs(mu - ref.mean(axis=0)).max() < TOL64
+    assert mu[0] == 1.0
+
+
+@pytest.mark.parametrize("precision", ["f64", "f32"])
+@pytest.mark.parametrize("n,M,n_v", [(1, 5, 3), (37, 0, 4), (37, 1, 4), (37, 2, 7), (97, 33, 1),
+                                     (97, 64, 20), (300, 81, 33), (513, 50, 64)])
+def test_random_ragged_parity(ctx, precision, n, M, n_v):
+    """Tiny to multi-tile sizes, empty rows, one dense row, odd/even M, ragged n_v."""
+    if n == 1:
+        A = diagonal(np.array([0.7]))
+    else:
+        A = random_symmetric(n, min(0.2, 6.0 / n), seed=n + M, empty_rows=max(1, n // 20),
+                             long_row=n // 3)
+    lam = np.linalg.eigvalsh(A.to_dense())
+    lb, ub = lam[0] - 0.05 * (lam[-1] - lam[0] + 1), lam[-1] + 0.05 * (lam[-1] - lam[0] + 1)
+    vals = np.float64 if precision == "f64" else np.float32
+    Aw = A.astype(vals)
+    pv = np.empty((n_v, M + 1))
+    mu = ctx.dos_kpm_moments(dev(Aw), lb, ub, M, n_v, seed=7, precision=precision, mu_per_vec=pv)
+    ref = okpm.kpm_moments_per_vector(Aw, lb, ub, M, n_v, seed=7)
+    tol = TOL64 if precision == "f64" else tol32(M)
+    assert np.all(np.abs(pv - ref) <= tol)
+    assert np.all(np.abs(mu - ref.mean(axis=0)) <= tol)
+
+
+@pytest.mark.parametrize("precision", ["f64", "f32"])
+def test_host_and_device_inputs_agree_and_deterministic(ctx, precision):
+    from paper_1308_5467_gb300 import dos
+    A = anderson_3d(9, 4.0, seed=5)
+    lb, ub = -8.2, 8.2
+    Ad = dev(A)
+    Ah = dos.CSRArrays.from_synthetic(A)  # host arrays, copied by the library
+    a = ctx.dos_kpm_moments(Ad, lb, ub, 77, 12, seed=3, precision=precision)
+    b = ctx.dos_kpm_moments(Ah, lb, ub, 77, 12, seed=3, precision=precision)
+    c = ctx.dos_kpm_moments(Ad, lb, ub, 77, 12, seed=3, precision=precision)
+    assert np.array_equal(a, b) and np.array_equal(a, c)
+
+
+def test_device_output_tensor(ctx):
+    import torch
+    A = laplacian_2d(12)
+    out = torch.empty(41, dtype=torch.float64, device="cuda")
+    ctx.dos_kpm_moments(dev(A), -0.1, 8.1, 40, 6, seed=2, precision="f64", mu=out)
+    ref = okpm.kpm_moments(A, -0.1, 8.1, 40, 6, seed=2)
+    assert np.abs(out.cpu().numpy() - ref).max() < TOL64
+
+
+@pytest.mark.parametrize("precision", ["f64", "f32"])
+def test_vector_panels_large_n_v(ctx, precision):
+    """n_v above one panel (256 vectors): panels of the block are swept in turn."""
+    A = anderson_3d(6, 3.0, seed=1)
+    lb, ub = -7.8, 7.8
+    n_v, M = 700, 20
+    pv = np.empty((n_v, M + 1))
+    mu = ctx.dos_kpm_moments(dev(A), lb, ub, M, n_v, seed=4, precision=precision, mu_per_vec=pv)
+    ref = okpm.kpm_moments_per_vector(A.astype(np.float32) if precision == "f32" else A,
+                                      lb, ub, M, n_v, seed=4)
+    tol = TOL64 if precision == "f64" else tol32(M)
+    assert np.all(np.abs(pv - ref) <= tol)
+    assert np.all(np.abs(mu - ref.mean(axis=0)) <= tol)
+
+
+def test_vec_offset_shards_union(ctx):
+    A = laplacian_2d(15)
+    full = np.empty((10, 31))
+    ctx.dos_kpm_moments(dev(A), -0.1, 8.1, 30, 10, seed=9, precision="f64", mu_per_vec=full)
+    part = np.empty((4, 31))
+    ctx.dos_kpm_moments(dev(A), -0.1, 8.1, 30, 4, seed=9, precision="f64", mu_per_vec=part,
+                        vec_offset=6)
+    assert np.abs(full[6:] - part).max() < 1e-13
+
+
+@pytest.mark.parametrize("launch", [{"team": 4, "chunks": 4}, {"team": 32, "chunks": 1},
+                                    {"team": 16, "chunks": 2, "tiles": 7},
+                                    {"team": 8, "chunks": 4, "tiles": 1000}])
+def test_launch_shapes_agree(ctx, launch):
+    A = anderson_3d(10, 6.0, seed=3)
+    lb, ub = -9.5, 9.5
+    ref = okpm.kpm_moments(A, lb, ub, 60, 64, seed=5)
+    mu = ctx.dos_kpm_moments(dev(A), lb, ub, 60, 64, seed=5, precision="f64", launch=launch)
+    assert np.abs(mu - ref).max() < TOL64
+
+
+def test_spectrum_escape_is_reported(ctx):
+    from paper_1308_5467_gb300 import dos
+    A = laplacian_2d(20)
+    with pytest.raises(dos.DosError) as ei:
+        ctx.dos_kpm_moments(dev(A), 0.5, 7.0, 60, 4, seed=1, precision="f64")
+    assert ei.value.status == dos.DOS_ESPECTRUM
+
+
+def test_bad_inputs_are_rejected(ctx):
+    import torch
+    from paper_1308_5467_gb300 import dos
+    A = laplacian_2d(6)
+    with pytest.raises(dos.DosError) as ei:
+        ctx.dos_kpm_moments(dev(A), 1.0, 1.0, 10, 4, seed=1)
+    assert ei.value.status == dos.DOS_EINVAL
+    bad = dos.CSRArrays(A.n, torch.from_numpy(A.row_ptr).cuda(),
+                        torch.from_numpy(np.where(np.arange(A.nnz) == 5, 99, A.col_idx)
+                                         .astype(np.int32)).cuda(),
+                        torch.from_numpy(A.val).cuda())
+    with pytest.raises(dos.DosError) as ei:
+        ctx.dos_kpm_moments(bad, -0.1, 8.1, 10, 4, seed=1)
+    assert ei.value.status == dos.DOS_EINVAL
+    rp = A.row_ptr.copy()
+    rp[3], rp[4] = rp[4], rp[3]
+    bad2 = dos.CSRArrays(A.n, rp, A.col_idx, A.val)
+    with pytest.raises(dos.DosError) as ei:
+        ctx.dos_kpm_moments(bad2, -0.1, 8.1, 10, 4, seed=1)
+    assert ei.value.status == dos.DOS_EINVAL
+    with pytest.raises(dos.DosError) as ei:  # FP64 sweep of FP32 values
+        ctx.dos_kpm_moments(dev(A, np.float32), -0.1, 8.1, 10, 4, seed=1, precision="f64")
+    assert ei.value.status == dos.DOS_EINVAL
