@@ -305,7 +305,6 @@ void run_sweep(dos_ctx *ctx, const dos_csr *Adesc, SweepRequest &r, cudaStream_t
                                                              sizeof(double))
                                : nullptr;
     int *status = status_flags(ctx);
-    DOS_CUDA_TRY(cudaMemsetAsync(status, 0, sizeof(int), s));
 
     SweepArgs a;
     a.precision = r.precision;
@@ -329,46 +328,121 @@ void run_sweep(dos_ctx *ctx, const dos_csr *Adesc, SweepRequest &r, cudaStream_t
     a.batch_index = r.opts.batch_index;
     a.shape = sh;
 
-    for (int p = 0; p < n_panels; ++p) {
-        const int off = p * panel_nv;
-        const int width = std::min(panel_nv, r.n_v - off);
-        a.n_v = width;
-        a.vec_offset = r.opts.vec_offset + off;
-        launch_init_vectors(a, s);
-        int k0 = 0;
-        float panel_ms = 0.f;
-        if (ctx->profiling) DOS_CUDA_TRY(cudaEventRecord(ctx->prof_ev[0], s));
-        for (int k = 0; k < S; ++k) {
-            launch_step(a, k, k % slots, s);
-            if (ctx->profiling && k == S - 1) DOS_CUDA_TRY(cudaEventRecord(ctx->prof_ev[1], s));
-            if ((k + 1) % slots == 0 || k == S - 1) {
-                launch_reduce(partial, plan.n_tiles, pv, width, B, seg.tile_begin, k0, k + 1 - k0,
-                              k0 % slots, slots, S, off, pvt, p > 0, dotsum, s);
-                k0 = k + 1;
-            }
-        }
-        if (ctx->profiling) {
-            // step launches between the two events: S (one reduce per `slots` steps
-            // may fall inside when slots < S; it is short and counted in the time)
-            DOS_CUDA_TRY(cudaEventSynchronize(ctx->prof_ev[1]));
-            DOS_CUDA_TRY(cudaEventElapsedTime(&panel_ms, ctx->prof_ev[0], ctx->prof_ev[1]));
-            ctx->prof_step_ms += panel_ms;
-            ctx->prof_step_launches += S;
-        }
-        launch_reduce0(partial0, pv, width, B, seg.tile_begin, off, pvt, p > 0, dotsum0, s);
-    }
-    if (ctx->profiling) ctx->prof_sweeps += 1;
     const double tol = r.precision == DOS_PREC_F64 ? 1e-8 : 1e-3;
-    launch_finalize(dotsum, dotsum0, seg.row0, B, r.M, S, r.n_v, pvt, mu_dev, mupv_dev, tol,
-                    status, s);
+    const bool profiling = ctx->profiling;
+    if (profiling) {  // two events per panel, around its step launches
+        while ((int)ctx->prof_events.size() < 2 * n_panels) {
+            cudaEvent_t e;
+            DOS_CUDA_TRY(cudaEventCreate(&e));
+            ctx->prof_events.push_back(e);
+        }
+    }
+    // Everything from here to the moments is pure device work on stream s, so it
+    // can be captured once into a CUDA graph and replayed.
+    auto enqueue = [&](cudaStream_t s) {
+        DOS_CUDA_TRY(cudaMemsetAsync(status, 0, sizeof(int), s));
+        for (int p = 0; p < n_panels; ++p) {
+            const int off = p * panel_nv;
+            const int width = std::min(panel_nv, r.n_v - off);
+            a.n_v = width;
+            a.vec_offset = r.opts.vec_offset + off;
+            launch_init_vectors(a, s);
+            int k0 = 0;
+            if (profiling) DOS_CUDA_TRY(cudaEventRecord(ctx->prof_events[2 * p], s));
+            for (int k = 0; k < S; ++k) {
+                launch_step(a, k, k % slots, s);
+                if (profiling && k == S - 1)
+                    DOS_CUDA_TRY(cudaEventRecord(ctx->prof_events[2 * p + 1], s));
+                if ((k + 1) % slots == 0 || k == S - 1) {
+                    launch_reduce(partial, plan.n_tiles, pv, width, B, seg.tile_begin, k0,
+                                  k + 1 - k0, k0 % slots, slots, S, off, pvt, p > 0, dotsum, s);
+                    k0 = k + 1;
+                }
+            }
+            launch_reduce0(partial0, pv, width, B, seg.tile_begin, off, pvt, p > 0, dotsum0, s);
+        }
+        launch_finalize(dotsum, dotsum0, seg.row0, B, r.M, S, r.n_v, pvt, mu_dev, mupv_dev, tol,
+                        status, s);
+    };
+    // Graph policy: the first call with a given configuration launches kernel by
+    // kernel and remembers the configuration; an identical second call captures a
+    // graph, and later identical calls replay it.
+    const std::vector<uint64_t> key = {
+        (uint64_t)r.precision, (uint64_t)(uintptr_t)A.row_ptr, (uint64_t)(uintptr_t)A.col_idx,
+        (uint64_t)(uintptr_t)val, (uint64_t)A.n, (uint64_t)A.nnz, (uint64_t)B, (uint64_t)ld,
+        (uint64_t)r.n_v, (uint64_t)r.M, r.seed, (uint64_t)r.opts.vec_offset, r.opts.batch_index,
+        (uint64_t)sh.team, (uint64_t)sh.chunks, (uint64_t)sh.block, (uint64_t)plan.n_tiles,
+        (uint64_t)per_vec, (uint64_t)slots, (uint64_t)(uintptr_t)xb, (uint64_t)(uintptr_t)partial,
+        (uint64_t)(uintptr_t)dotsum, (uint64_t)(uintptr_t)mu_dev, (uint64_t)(uintptr_t)mupv_dev,
+        (uint64_t)(uintptr_t)tiles, (uint64_t)(uintptr_t)seg.row0, (uint64_t)(uintptr_t)status,
+        (uint64_t)profiling, (uint64_t)(uintptr_t)s};
+    GraphCache &gc = ctx->graph;
+    const bool use_graph = !(r.opts.flags & DOS_OPT_NO_GRAPH);
+    // The graph runs on a context-owned stream ordered after `s` by events, so
+    // callers on the legacy default stream (which cannot be captured) get it too.
+    auto launch_graph = [&]() {
+        DOS_CUDA_TRY(cudaEventRecord(gc.ev_in, s));
+        DOS_CUDA_TRY(cudaStreamWaitEvent(gc.stream, gc.ev_in, 0));
+        DOS_CUDA_TRY(cudaGraphLaunch(gc.exec, gc.stream));
+        DOS_CUDA_TRY(cudaEventRecord(gc.ev_out, gc.stream));
+        DOS_CUDA_TRY(cudaStreamWaitEvent(s, gc.ev_out, 0));
+        count_launches(gc.kernel_nodes);
+    };
+    if (use_graph && gc.exec && gc.key == key) {
+        launch_graph();
+    } else if (use_graph && gc.pending == key) {
+        if (!gc.stream) {
+            DOS_CUDA_TRY(cudaStreamCreateWithFlags(&gc.stream, cudaStreamNonBlocking));
+            DOS_CUDA_TRY(cudaEventCreateWithFlags(&gc.ev_in, cudaEventDisableTiming));
+            DOS_CUDA_TRY(cudaEventCreateWithFlags(&gc.ev_out, cudaEventDisableTiming));
+        }
+        if (gc.exec) {
+            cudaGraphExecDestroy(gc.exec);
+            gc.exec = nullptr;
+            gc.key.clear();
+        }
+        const int64_t before = g_launch_count.load();
+        DOS_CUDA_TRY(cudaStreamBeginCapture(gc.stream, cudaStreamCaptureModeThreadLocal));
+        try {
+            enqueue(gc.stream);
+        } catch (...) {
+            cudaGraph_t g = nullptr;
+            cudaStreamEndCapture(gc.stream, &g);
+            if (g) cudaGraphDestroy(g);
+            cudaGetLastError();
+            throw;
+        }
+        cudaGraph_t g = nullptr;
+        DOS_CUDA_TRY(cudaStreamEndCapture(gc.stream, &g));
+        gc.kernel_nodes = g_launch_count.load() - before;
+        g_launch_count.fetch_sub(gc.kernel_nodes);
+        cudaError_t ie = cudaGraphInstantiate(&gc.exec, g, 0);
+        cudaGraphDestroy(g);
+        DOS_CUDA_TRY(ie);
+        gc.key = key;
+        launch_graph();
+    } else {
+        enqueue(s);
+        gc.pending = key;
+    }
     copy_out(r.mu, mu_dev, (size_t)B * (r.M + 1) * sizeof(double), s);
     if (per_vec) copy_out(r.mu_pv, mupv_dev, (size_t)B * r.n_v * (r.M + 1) * sizeof(double), s);
 
     const bool host_out = !is_device_ptr(r.mu) || (per_vec && !is_device_ptr(r.mu_pv));
-    if (!(r.opts.flags & DOS_OPT_NO_SPECTRUM_CHECK) || host_out) {
+    if (!(r.opts.flags & DOS_OPT_NO_SPECTRUM_CHECK) || host_out || profiling) {
         int h = 0;
         DOS_CUDA_TRY(cudaMemcpyAsync(&h, status, sizeof(int), cudaMemcpyDeviceToHost, s));
         DOS_CUDA_TRY(cudaStreamSynchronize(s));
+        if (profiling) {
+            for (int p = 0; p < n_panels; ++p) {
+                float ms = 0.f;
+                DOS_CUDA_TRY(cudaEventElapsedTime(&ms, ctx->prof_events[2 * p],
+                                                  ctx->prof_events[2 * p + 1]));
+                ctx->prof_step_ms += ms;
+                ctx->prof_step_launches += S;
+            }
+            ctx->prof_sweeps += 1;
+        }
         if (!(r.opts.flags & DOS_OPT_NO_SPECTRUM_CHECK) && (h & 2))
             throw Error{DOS_ESPECTRUM,
                         "a moment exceeds mu_0 in magnitude or is not finite: the bounds do not "
@@ -603,8 +677,10 @@ int dos_ctx_destroy(dos_ctx *ctx) {
         b->release();
     ctx->host_stage.release();
     if (ctx->graph.exec) cudaGraphExecDestroy(ctx->graph.exec);
-    for (cudaEvent_t &e : ctx->prof_ev)
-        if (e) cudaEventDestroy(e);
+    if (ctx->graph.stream) cudaStreamDestroy(ctx->graph.stream);
+    if (ctx->graph.ev_in) cudaEventDestroy(ctx->graph.ev_in);
+    if (ctx->graph.ev_out) cudaEventDestroy(ctx->graph.ev_out);
+    for (cudaEvent_t e : ctx->prof_events) cudaEventDestroy(e);
     if (prev >= 0) cudaSetDevice(prev);
     cudaGetLastError();
     delete ctx;
@@ -615,10 +691,6 @@ const char *dos_last_error(const dos_ctx *ctx) { return ctx ? ctx->last_error.c_
 
 int dos_profile_enable(dos_ctx *ctx, int on) {
     return guarded(ctx, [&] {
-        if (on && !ctx->prof_ev[0]) {
-            DOS_CUDA_TRY(cudaEventCreate(&ctx->prof_ev[0]));
-            DOS_CUDA_TRY(cudaEventCreate(&ctx->prof_ev[1]));
-        }
         ctx->profiling = on != 0;
         ctx->prof_step_ms = 0.0;
         ctx->prof_step_launches = 0;

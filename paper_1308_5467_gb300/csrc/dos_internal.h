@@ -87,7 +87,11 @@ struct Shape {
 // Cached CUDA graph for one sweep configuration.
 struct GraphCache {
     cudaGraphExec_t exec = nullptr;
-    std::vector<uint64_t> key;
+    std::vector<uint64_t> key;      // configuration of `exec`
+    std::vector<uint64_t> pending;  // configuration of the previous direct-launch call
+    int64_t kernel_nodes = 0;
+    cudaStream_t stream = nullptr;  // replay stream (ordered after the caller's by events)
+    cudaEvent_t ev_in = nullptr, ev_out = nullptr;
 };
 
 }  // namespace dos
@@ -110,7 +114,7 @@ struct dos_ctx {
     dos::GraphCache graph;
     // profiling counters (dos_profile_enable / dos_profile_read)
     bool profiling = false;
-    cudaEvent_t prof_ev[2] = {nullptr, nullptr};
+    std::vector<cudaEvent_t> prof_events;  // two per vector panel
     double prof_step_ms = 0.0;
     int64_t prof_step_launches = 0, prof_sweeps = 0;
 };

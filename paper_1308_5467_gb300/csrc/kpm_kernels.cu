@@ -471,7 +471,7 @@ __global__ void finalize_kernel(const double *__restrict__ dotsum,
         mu[(size_t)seg * (M + 1) + k] = m;
         if (!(fabs(m) <= mu0 * (1.0 + tol))) atomicOr(status, 2);
     }
-    if (mu_pv != nullptr && pvt > 1) {
+    if (mu_pv != nullptr) {  // per-vector dot sums are stored (pvt == n_v, also when 1)
         for (int idx = threadIdx.x; idx < n_v * (M + 1); idx += blockDim.x) {
             const int l = idx / (M + 1), k = idx - l * (M + 1);
             const double z = d0[l];
