@@ -33,13 +33,16 @@ def gershgorin(A) -> tuple[float, float]:
 def lanczos_tridiagonal(A, steps: int, seed: int, batch_index: int = 0):
     """Plain k-step Lanczos (no reorthogonalisation) from the normalised
     Rademacher start vector l = 0.  Returns (alpha[k], beta[k]) where beta[-1]
-    is ||f_k||; k may be smaller than ``steps`` if an invariant subspace is hit."""
+    is ||f_k||.  The run stops early at an invariant subspace, taken as
+    beta_j <= 1e-12 * max_{i<=j}(|alpha_i| + beta_i + beta_{i-1}) (the paper is
+    silent on breakdown)."""
     n = A.n
     q = kpm.start_block(n, 1, seed, batch_index)[:, 0]
     q = q / np.sqrt(q @ q)
     q_prev = np.zeros(n)
     beta_prev = 0.0
     alpha, beta = [], []
+    scale = 0.0
     for j in range(min(steps, n)):
         w = kpm.spmv(A, q) - beta_prev * q_prev
         a = float(q @ w)
@@ -47,7 +50,8 @@ def lanczos_tridiagonal(A, steps: int, seed: int, batch_index: int = 0):
         b = float(np.sqrt(w @ w))
         alpha.append(a)
         beta.append(b)
-        if b == 0.0:
+        scale = max(scale, abs(a) + b + beta_prev)
+        if b <= 1e-12 * scale:
             break
         q_prev, q = q, w / b
         beta_prev = b

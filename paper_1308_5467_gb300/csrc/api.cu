@@ -348,11 +348,16 @@ void run_sweep(dos_ctx *ctx, const dos_csr *Adesc, SweepRequest &r, cudaStream_t
             a.vec_offset = r.opts.vec_offset + off;
             launch_init_vectors(a, s);
             int k0 = 0;
-            if (profiling) DOS_CUDA_TRY(cudaEventRecord(ctx->prof_events[2 * p], s));
+            // "External" so that, under stream capture, the record becomes an event
+            // node of the graph rather than a capture-internal dependency marker.
+            if (profiling)
+                DOS_CUDA_TRY(cudaEventRecordWithFlags(ctx->prof_events[2 * p], s,
+                                                      cudaEventRecordExternal));
             for (int k = 0; k < S; ++k) {
                 launch_step(a, k, k % slots, s);
                 if (profiling && k == S - 1)
-                    DOS_CUDA_TRY(cudaEventRecord(ctx->prof_events[2 * p + 1], s));
+                    DOS_CUDA_TRY(cudaEventRecordWithFlags(ctx->prof_events[2 * p + 1], s,
+                                                          cudaEventRecordExternal));
                 if ((k + 1) % slots == 0 || k == S - 1) {
                     launch_reduce(partial, plan.n_tiles, pv, width, B, seg.tile_begin, k0,
                                   k + 1 - k0, k0 % slots, slots, S, off, pvt, p > 0, dotsum, s);
@@ -871,12 +876,17 @@ int dos_bounds(dos_ctx *ctx, const dos_csr *Adesc, int method, int steps, uint64
             DOS_CUDA_TRY(cudaMemcpyAsync(be.data(), beta, k * sizeof(double),
                                          cudaMemcpyDeviceToHost, s));
             DOS_CUDA_TRY(cudaStreamSynchronize(s));
-            int kk = k;  // an exact zero beta ends the run (invariant subspace)
-            for (int j = 0; j < k; ++j)
-                if (!(be[j] > 0.0)) {
+            // An invariant subspace ends the run: beta_j <= 1e-12 * the running
+            // estimate max_{i<=j}(|alpha_i| + beta_i + beta_{i-1}) of ||A||.
+            int kk = k;
+            double scale = 0.0;
+            for (int j = 0; j < k; ++j) {
+                scale = std::max(scale, fabs(al[j]) + be[j] + (j ? be[j - 1] : 0.0));
+                if (!(be[j] > 1e-12 * scale)) {
                     kk = j + 1;
                     break;
                 }
+            }
             al.resize(kk);
             be.resize(kk);
             for (int j = 0; j < kk; ++j)

@@ -138,7 +138,7 @@ def test_vec_offset_shards_union(ctx):
     assert np.abs(full[6:] - part).max() < 1e-13
 
 
-@pytest.mark.parametrize("launch", [{"team": 4, "chunks": 4}, {"team": 32, "chunks": 1},
+@pytest.mark.parametrize("launch", [{"team": 16, "chunks": 4}, {"team": 32, "chunks": 1},
                                     {"team": 16, "chunks": 2, "tiles": 7},
                                     {"team": 8, "chunks": 4, "tiles": 1000}])
 def test_launch_shapes_agree(ctx, launch):
@@ -147,6 +147,15 @@ def test_launch_shapes_agree(ctx, launch):
     ref = okpm.kpm_moments(A, lb, ub, 60, 64, seed=5)
     mu = ctx.dos_kpm_moments(dev(A), lb, ub, 60, 64, seed=5, precision="f64", launch=launch)
     assert np.abs(mu - ref).max() < TOL64
+
+
+def test_launch_shape_that_misses_columns_is_rejected(ctx):
+    from paper_1308_5467_gb300 import dos
+    A = anderson_3d(5, 1.0, seed=3)
+    with pytest.raises(dos.DosError) as ei:  # 4 x 4 chunks of 2 doubles < 64 columns
+        ctx.dos_kpm_moments(dev(A), -8.0, 8.0, 10, 64, seed=5, precision="f64",
+                            launch={"team": 4, "chunks": 4})
+    assert ei.value.status == dos.DOS_EINVAL
 
 
 def test_spectrum_escape_is_reported(ctx):
@@ -180,3 +189,25 @@ def test_bad_inputs_are_rejected(ctx):
     with pytest.raises(dos.DosError) as ei:  # FP64 sweep of FP32 values
         ctx.dos_kpm_moments(dev(A, np.float32), -0.1, 8.1, 10, 4, seed=1, precision="f64")
     assert ei.value.status == dos.DOS_EINVAL
+
+
+def test_graph_replay_matches_direct_launches(ctx):
+    """Identical repeated calls are captured in a CUDA graph and replayed; the
+    results equal those of kernel-by-kernel launches bit for bit."""
+    from paper_1308_5467_gb300 import dos
+    A = dev(anderson_3d(11, 5.0, seed=8))
+    runs = [ctx.dos_kpm_moments(A, -9.0, 9.0, 90, 24, seed=6, precision="f32") for _ in range(4)]
+    direct = ctx.dos_kpm_moments(A, -9.0, 9.0, 90, 24, seed=6, precision="f32",
+                                 flags=dos.DOS_OPT_NO_GRAPH)
+    for r in runs:
+        assert np.array_equal(r, direct)
+
+
+def test_profiling_counts_step_launches(ctx):
+    A = dev(laplacian_2d(30))
+    ctx.dos_profile_enable(True)
+    ctx.dos_kpm_moments(A, -0.1, 8.1, 41, 8, seed=1, precision="f64")
+    prof = ctx.dos_profile_read()
+    ctx.dos_profile_enable(False)
+    assert prof["step_launches"] == 21 and prof["sweeps"] == 1
+    assert prof["step_ms"] > 0 and prof["launches"] >= 21

@@ -46,6 +46,16 @@ def test_lanczos_full_run_recovers_extremes():
     assert abs(lb - dvals[0]) < 1e-8 and abs(ub - dvals[-1]) < 1e-8
 
 
+def test_lanczos_stops_at_invariant_subspace():
+    # Three distinct eigenvalues: the Krylov space of any start vector has
+    # dimension 3, so the run ends after 3 steps with the exact extremes.
+    A = diagonal(np.repeat([1.0, 2.0, 4.0], 50))
+    alpha, beta = bounds.lanczos_tridiagonal(A, 20, seed=0)
+    assert len(alpha) == 3 and beta[-1] < 1e-12
+    lb, ub = bounds.lanczos(A, 20, seed=0)
+    assert abs(lb - 1.0) < 1e-12 and abs(ub - 4.0) < 1e-12
+
+
 def test_lanczos_20_steps_bracket_laplacian():
     m = 40
     i = np.arange(1, m + 1)
