@@ -177,6 +177,16 @@ int dos_start_vectors(dos_ctx *ctx, int64_t n, int n_v, uint64_t seed, uint64_t 
 int dos_bounds(dos_ctx *ctx, const dos_csr *A, int method, int steps, uint64_t seed,
                double pad_frac, double *lb, double *ub, void *stream);
 
+/*
+ * Gershgorin bounds of B matrices concatenated as in dos_kpm_moments_batched
+ * (one pass over all rows, one launch): lb[b], ub[b] (host arrays of B) are
+ * min/max over the rows of matrix b of a_ii -+ sum_{j!=i}|a_ij|, widened by
+ * pad_frac * (ub - lb) (a matrix with a single eigenvalue gets +-0.5).
+ * Synchronises `stream`.  Errors: DOS_EINVAL, DOS_ENOMEM, DOS_ECUDA.
+ */
+int dos_bounds_batched(dos_ctx *ctx, const dos_csr *A, int B, const int64_t *seg_rows,
+                       double pad_frac, double *lb, double *ub, void *stream);
+
 /* ---- steps a2-a5: the Chebyshev moment sweep ------------------------------- */
 /*
  * Stochastic Chebyshev moments of B = (A - cI)/d, c = (lb+ub)/2, d = (ub-lb)/2
@@ -255,6 +265,22 @@ int dos_tune(dos_ctx *ctx, const dos_csr *A, int B, const int64_t *seg_rows, int
  */
 int dos_reconstruct(dos_ctx *ctx, const double *mu, int M, int damping, double lb, double ub,
                     const double *t, int N_t, double *phi_hat, double *phi_lambda, void *stream);
+
+/*
+ * Inverse of dos_reconstruct on the Chebyshev grid: given phi_hat at the N_t
+ * nodes t_i = -cos(pi (i + 1/2) / N_t) (host or device), the moments
+ *     mu_k = integral phi_hat(t) T_k(t) dt = (pi/N_t) sum_i sqrt(1 - t_i^2) phi_hat(t_i) T_k(t_i)
+ * for k = 0..M_out, 0 <= M_out < N_t (Gauss-Chebyshev quadrature: exact when
+ * sqrt(1 - t^2) phi_hat(t) is a polynomial of degree <= 2 N_t - 1 - M_out).
+ * With DOS_DAMP_NONE and M_out = N_t - 1, dos_reconstruct of these moments on
+ * the same grid returns phi_hat again: the cosine-transform pair behind the
+ * paper's spectroscopic view of KPM (Section 3.1.2).  Used to score a DOS
+ * given on a grid (e.g. the network of dos_mlp.h) with dos_smoothed_error.
+ * mu: M_out+1 doubles, host or device.
+ * Synchronises `stream` when mu is host memory.
+ */
+int dos_moments_from_grid(dos_ctx *ctx, const double *phi_hat, int N_t, int M_out, double *mu,
+                          void *stream);
 
 /* ---- step a7: accuracy metric ---------------------------------------------- */
 /*

@@ -143,6 +143,18 @@ SegDev upload_segments(dos_ctx *ctx, const std::vector<int32_t> &row0,
 
 int *status_flags(dos_ctx *ctx) { return (int *)ctx->status.get(4 * sizeof(int)); }
 
+// Under stream capture an event record must be flagged "external" to become an
+// event node of the graph (otherwise it only marks a capture-internal
+// dependency); outside capture that flag is rejected, so pick per call.
+void record_timing_event(cudaEvent_t e, cudaStream_t s) {
+    cudaStreamCaptureStatus st = cudaStreamCaptureStatusNone;
+    DOS_CUDA_TRY(cudaStreamIsCapturing(s, &st));
+    if (st == cudaStreamCaptureStatusActive)
+        DOS_CUDA_TRY(cudaEventRecordWithFlags(e, s, cudaEventRecordExternal));
+    else
+        DOS_CUDA_TRY(cudaEventRecord(e, s));
+}
+
 void validate_on_device(dos_ctx *ctx, const DevCSR &A, int B, const int32_t *seg_row0_dev,
                         cudaStream_t s) {
     int *flag = status_flags(ctx) + 1;
@@ -348,16 +360,11 @@ void run_sweep(dos_ctx *ctx, const dos_csr *Adesc, SweepRequest &r, cudaStream_t
             a.vec_offset = r.opts.vec_offset + off;
             launch_init_vectors(a, s);
             int k0 = 0;
-            // "External" so that, under stream capture, the record becomes an event
-            // node of the graph rather than a capture-internal dependency marker.
-            if (profiling)
-                DOS_CUDA_TRY(cudaEventRecordWithFlags(ctx->prof_events[2 * p], s,
-                                                      cudaEventRecordExternal));
+            if (profiling) record_timing_event(ctx->prof_events[2 * p], s);
             for (int k = 0; k < S; ++k) {
                 launch_step(a, k, k % slots, s);
                 if (profiling && k == S - 1)
-                    DOS_CUDA_TRY(cudaEventRecordWithFlags(ctx->prof_events[2 * p + 1], s,
-                                                          cudaEventRecordExternal));
+                    record_timing_event(ctx->prof_events[2 * p + 1], s);
                 if ((k + 1) % slots == 0 || k == S - 1) {
                     launch_reduce(partial, plan.n_tiles, pv, width, B, seg.tile_begin, k0,
                                   k + 1 - k0, k0 % slots, slots, S, off, pvt, p > 0, dotsum, s);
@@ -910,6 +917,46 @@ int dos_bounds(dos_ctx *ctx, const dos_csr *Adesc, int method, int steps, uint64
     });
 }
 
+int dos_bounds_batched(dos_ctx *ctx, const dos_csr *Adesc, int B, const int64_t *seg_rows,
+                       double pad_frac, double *lb, double *ub, void *stream) {
+    return guarded(ctx, [&] {
+        DOS_REQUIRE(lb && ub && seg_rows, "lb / ub / seg_rows is NULL");
+        DOS_REQUIRE(B >= 1 && B <= (1 << 16), "B must be in [1, 65536]");
+        DOS_REQUIRE(isfinite(pad_frac) && pad_frac >= 0.0, "pad_frac must be >= 0");
+        cudaStream_t s = (cudaStream_t)stream;
+        DevCSR A = stage_csr(ctx, Adesc, s);
+        DOS_REQUIRE(seg_rows[0] == 0 && seg_rows[B] == A.n, "seg_rows must start at 0 and end at n");
+        std::vector<int32_t> row0(B + 1), tb(B + 1, 0);
+        for (int b = 0; b <= B; ++b) {
+            if (b < B) DOS_REQUIRE(seg_rows[b + 1] > seg_rows[b], "every matrix needs a row");
+            row0[b] = (int32_t)seg_rows[b];
+        }
+        SegDev seg = upload_segments(ctx, row0, tb, std::vector<double>(B, 0.0),
+                                     std::vector<double>(B, 1.0), s);
+        validate_on_device(ctx, A, B, seg.row0, s);
+        uint8_t *buf = (uint8_t *)ctx->bnd_part.get((size_t)B * 32);
+        unsigned long long *keys = (unsigned long long *)buf;
+        double *out = (double *)(buf + (size_t)B * 16);
+        launch_gershgorin_batched(A.n, A.row_ptr, A.col_idx, A.val, A.dtype, B, seg.row0, keys,
+                                  out, ctx->num_sms, s);
+        std::vector<double> h(2 * (size_t)B);
+        DOS_CUDA_TRY(cudaMemcpyAsync(h.data(), out, h.size() * sizeof(double),
+                                     cudaMemcpyDeviceToHost, s));
+        DOS_CUDA_TRY(cudaStreamSynchronize(s));
+        for (int b = 0; b < B; ++b) {
+            const double lo = h[2 * b], hi = h[2 * b + 1];
+            DOS_REQUIRE(isfinite(lo) && isfinite(hi), "bounds are not finite");
+            const double w = hi - lo;
+            lb[b] = lo - pad_frac * w;
+            ub[b] = hi + pad_frac * w;
+            if (!(ub[b] > lb[b])) {
+                lb[b] = lo - 0.5;
+                ub[b] = hi + 0.5;
+            }
+        }
+    });
+}
+
 int dos_reconstruct(dos_ctx *ctx, const double *mu, int M, int damping, double lb, double ub,
                     const double *t, int N_t, double *phi_hat, double *phi_lambda, void *stream) {
     return guarded(ctx, [&] {
@@ -932,6 +979,22 @@ int dos_reconstruct(dos_ctx *ctx, const double *mu, int M, int damping, double l
         if (phi_lambda) copy_out(phi_lambda, dphl, N_t * sizeof(double), s);
         if (!is_device_ptr(phi_hat) || (phi_lambda && !is_device_ptr(phi_lambda)))
             DOS_CUDA_TRY(cudaStreamSynchronize(s));
+    });
+}
+
+int dos_moments_from_grid(dos_ctx *ctx, const double *phi_hat, int N_t, int M_out, double *mu,
+                          void *stream) {
+    return guarded(ctx, [&] {
+        DOS_REQUIRE(phi_hat && mu, "phi_hat / mu is NULL");
+        DOS_REQUIRE(N_t >= 1 && N_t <= (1 << 24), "N_t must be in [1, 2^24]");
+        DOS_REQUIRE(M_out >= 0 && M_out < N_t, "M_out must be in [0, N_t)");
+        cudaStream_t s = (cudaStream_t)stream;
+        double *buf = (double *)ctx->rec_in.get(((size_t)N_t + M_out + 1) * sizeof(double));
+        double *dphi = buf, *dmu = buf + N_t;
+        DOS_CUDA_TRY(cudaMemcpyAsync(dphi, phi_hat, N_t * sizeof(double), cudaMemcpyDefault, s));
+        launch_grid_moments(dphi, N_t, M_out, dmu, s);
+        copy_out(mu, dmu, (M_out + 1) * sizeof(double), s);
+        if (!is_device_ptr(mu)) DOS_CUDA_TRY(cudaStreamSynchronize(s));
     });
 }
 

@@ -161,7 +161,71 @@ __global__ void lanczos_next_kernel(int64_t n, const double *__restrict__ beta,
     }
 }
 
+// Order-preserving map of a double to an unsigned 64-bit key (negative numbers
+// have all bits flipped, non-negative ones the sign bit set), so integer
+// atomicMin/atomicMax give the exact floating-point min/max in any order.
+__device__ __forceinline__ unsigned long long order_key(double x) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    return (b >> 63) ? ~b : (b | 0x8000000000000000ULL);
+}
+
+template <typename T>
+__global__ void gershgorin_batched_kernel(int64_t n_rows, const int32_t *__restrict__ row_ptr,
+                                          const int32_t *__restrict__ col_idx, const void *val,
+                                          int B, const int32_t *__restrict__ seg_row0,
+                                          unsigned long long *keys) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n_rows;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        int lo = 0, hi = B;
+        while (hi - lo > 1) {
+            const int mid = (lo + hi) >> 1;
+            if (seg_row0[mid] <= i) lo = mid; else hi = mid;
+        }
+        const int64_t local = i - seg_row0[lo];
+        double center = 0.0, radius = 0.0;
+        for (int e = row_ptr[i]; e < row_ptr[i + 1]; ++e) {
+            const double a = load_val<T>(val, e);
+            if (col_idx[e] == local) center += a; else radius += fabs(a);
+        }
+        atomicMin(keys + 2 * lo, order_key(center - radius));
+        atomicMax(keys + 2 * lo + 1, order_key(center + radius));
+    }
+}
+
+__global__ void keys_to_double_kernel(const unsigned long long *keys, int count, double *out) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < count; i += gridDim.x * blockDim.x) {
+        const unsigned long long k = keys[i];
+        const unsigned long long b = (k >> 63) ? (k & 0x7fffffffffffffffULL) : ~k;
+        out[i] = __longlong_as_double((long long)b);
+    }
+}
+
+__global__ void keys_init_kernel(unsigned long long *keys, int B) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < B; i += gridDim.x * blockDim.x) {
+        keys[2 * i] = ~0ULL;     // min accumulator
+        keys[2 * i + 1] = 0ULL;  // max accumulator
+    }
+}
+
 }  // namespace
+
+void launch_gershgorin_batched(int64_t n_rows, const int32_t *row_ptr, const int32_t *col_idx,
+                               const void *val, int dtype, int B, const int32_t *seg_row0,
+                               unsigned long long *keys, double *out, int num_sms,
+                               cudaStream_t s) {
+    keys_init_kernel<<<(B + 255) / 256, 256, 0, s>>>(keys, B);
+    DOS_LAUNCHED();
+    const int grid = reduce_blocks(num_sms, n_rows);
+    if (dtype == DOS_F64)
+        gershgorin_batched_kernel<double><<<grid, kThreads, 0, s>>>(n_rows, row_ptr, col_idx, val,
+                                                                    B, seg_row0, keys);
+    else
+        gershgorin_batched_kernel<float><<<grid, kThreads, 0, s>>>(n_rows, row_ptr, col_idx, val,
+                                                                   B, seg_row0, keys);
+    DOS_LAUNCHED();
+    keys_to_double_kernel<<<(2 * B + 255) / 256, 256, 0, s>>>(keys, 2 * B, out);
+    DOS_LAUNCHED();
+}
 
 int gershgorin_blocks(int num_sms) { return num_sms * 4; }
 int reduce_blocks(int num_sms, int64_t n) {

@@ -197,6 +197,11 @@ void launch_finalize(const double *dotsum, const double *dotsum0, const int32_t 
 void launch_gershgorin(int64_t n, const int32_t *row_ptr, const int32_t *col_idx,
                        const void *val, int dtype, double *part, int n_blocks, cudaStream_t s);
 void launch_minmax_final(const double *part, int n_blocks, double *out, cudaStream_t s);
+// Per-segment Gershgorin min/max: out[2b] = lower, out[2b+1] = upper; keys: 2B scratch.
+void launch_gershgorin_batched(int64_t n_rows, const int32_t *row_ptr, const int32_t *col_idx,
+                               const void *val, int dtype, int B, const int32_t *seg_row0,
+                               unsigned long long *keys, double *out, int num_sms,
+                               cudaStream_t s);
 int gershgorin_blocks(int num_sms);
 void launch_lanczos_start(int64_t n, uint64_t seed, double *q, cudaStream_t s);
 // w = A q - beta_prev * q_prev; partial dots q.w per block
@@ -227,5 +232,6 @@ void launch_blur_eigs(const double *eig, int64_t n_eig, double sigma, double x0,
                       int N_x, double *out, cudaStream_t s);
 void launch_error_norms(const double *a, const double *b, int N_x, double h, double *out,
                         cudaStream_t s);
+void launch_grid_moments(const double *phi, int N, int M, double *mu, cudaStream_t s);
 
 }  // namespace dos

@@ -120,6 +120,25 @@ __global__ void error_norms_kernel(const double *__restrict__ a, const double *_
     }
 }
 
+// mu_k = (pi/N) sum_i sqrt(1 - t_i^2) phi(t_i) T_k(t_i), t_i = -cos(pi (i+1/2)/N):
+// one block per k, T_k(t_i) = cos(k theta_i) with theta_i the node angle
+// pi - pi (i + 1/2)/N, fixed-order block sum.
+__global__ void grid_moments_kernel(const double *__restrict__ phi, int N, int M,
+                                    double *__restrict__ mu) {
+    for (int k = blockIdx.x; k <= M; k += gridDim.x) {
+        double s = 0.0;
+        for (int i = threadIdx.x; i < N; i += blockDim.x) {
+            const double x = (i + 0.5) / (double)N;  // t_i = -cos(pi x) = cos(pi (1 - x))
+            const double w = sinpi(x);               // sqrt(1 - t_i^2)
+            // T_k(t_i) = cos(k pi (1 - x)); reduce k (1 - x) mod 2 exactly enough
+            const double arg = fmod((double)k * (1.0 - x), 2.0);
+            s += w * phi[i] * cospi(arg);
+        }
+        s = block_sum_d(s);
+        if (threadIdx.x == 0) mu[k] = M_PI * s / N;
+    }
+}
+
 int grid_cap(int64_t work, int block, int cap) {
     int64_t g = (work + block - 1) / block;
     return (int)(g < 1 ? 1 : (g > cap ? cap : g));
@@ -156,6 +175,11 @@ void launch_blur_eigs(const double *eig, int64_t n_eig, double sigma, double x0,
                       int N_x, double *out, cudaStream_t s) {
     blur_eigs_kernel<<<N_x < 65535 ? N_x : 65535, 256, 0, s>>>(eig, n_eig, sigma, x0, h, N_x,
                                                                 out);
+    DOS_LAUNCHED();
+}
+
+void launch_grid_moments(const double *phi, int N, int M, double *mu, cudaStream_t s) {
+    grid_moments_kernel<<<M + 1 < 4096 ? M + 1 : 4096, 256, 0, s>>>(phi, N, M, mu);
     DOS_LAUNCHED();
 }
 

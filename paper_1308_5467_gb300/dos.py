@@ -65,6 +65,7 @@ _SIGS = {
     "dos_profile_read": (_i, [_vp, _dp, C.POINTER(C.c_int64), C.POINTER(C.c_int64),
                               C.POINTER(C.c_int64)]),
     "dos_bounds": (_i, [_vp, C.POINTER(dos_csr), _i, _i, _u64, _d, _dp, _dp, _vp]),
+    "dos_bounds_batched": (_i, [_vp, C.POINTER(dos_csr), _i, _vp, _d, _vp, _vp, _vp]),
     "dos_kpm_moments": (_i, [_vp, C.POINTER(dos_csr), _d, _d, _i, _i, _u64, _i, _vp, _vp, _vp]),
     "dos_kpm_moments_ex": (_i, [_vp, C.POINTER(dos_csr), _d, _d, _i, _i, _u64, _i, _vp, _vp,
                                 C.POINTER(dos_kpm_opts), _vp]),
@@ -74,7 +75,18 @@ _SIGS = {
     "dos_reconstruct": (_i, [_vp, _vp, _i, _i, _d, _d, _vp, _i, _vp, _vp, _vp]),
     "dos_smoothed_error": (_i, [_vp, _vp, _i, _i, _d, _d, _vp, _i64, _vp, _i, _i, _d, _i, _dp,
                                 _dp, _vp]),
+    "dos_moments_from_grid": (_i, [_vp, _vp, _i, _i, _vp, _vp]),
 }
+_SIGS.update({
+    "dos_mlp_create": (_i, [_vp, _i, _i, _i, _u64, C.POINTER(_vp)]),
+    "dos_mlp_destroy": (_i, [_vp]),
+    "dos_mlp_num_params": (_i, [_vp, C.POINTER(C.c_int64)]),
+    "dos_mlp_set_params": (_i, [_vp, _vp, _vp]),
+    "dos_mlp_get_params": (_i, [_vp, _vp, _vp]),
+    "dos_mlp_forward": (_i, [_vp, _vp, _i, _vp, _vp]),
+    "dos_mlp_loss_grad": (_i, [_vp, _vp, _vp, _i, C.POINTER(C.c_float), _vp, _vp]),
+    "dos_mlp_train_step": (_i, [_vp, _vp, _vp, _i, C.c_float, C.POINTER(C.c_float), _vp]),
+})
 for _name, (_res, _args) in _SIGS.items():
     _f = getattr(_lib, _name)
     _f.restype = _res
@@ -217,6 +229,17 @@ class Context:
                                     _stream_of(A.row_ptr)))
         return lb.value, ub.value
 
+    def dos_bounds_batched(self, A: CSRArrays, seg_rows, pad_frac: float = 0.01):
+        """Gershgorin (lb, ub) arrays of the B concatenated matrices."""
+        seg = np.ascontiguousarray(seg_rows, dtype=np.int64)
+        B = seg.shape[0] - 1
+        lb = np.empty(B)
+        ub = np.empty(B)
+        self._check(_lib.dos_bounds_batched(self._h, C.byref(A.desc), B, seg.ctypes.data,
+                                            float(pad_frac), lb.ctypes.data, ub.ctypes.data,
+                                            _stream_of(A.row_ptr)))
+        return lb, ub
+
     def _opts(self, flags=0, vec_offset=0, batch_index=0, launch=None):
         o = dos_kpm_opts()
         o.flags = int(flags)
@@ -288,6 +311,15 @@ class Context:
                                          int(N_t), po, pl, _stream_of(mu, out)))
         return (out, outl) if want_lambda or phi_lambda is not None else out
 
+    def dos_moments_from_grid(self, phi_hat, M_out: int, mu=None):
+        """Moments mu_0..mu_M_out of a DOS given at the Chebyshev nodes."""
+        out = np.empty(M_out + 1, dtype=np.float64) if mu is None else mu
+        pp, _, k0 = _ptr(phi_hat)
+        po, _, k1 = _ptr(out)
+        self._check(_lib.dos_moments_from_grid(self._h, pp, int(phi_hat.shape[0]), int(M_out),
+                                               po, _stream_of(phi_hat, out)))
+        return out
+
     def dos_smoothed_error(self, mu, M: int, damping, lb: float, ub: float, sigma: float,
                            eig=None, ref_mu=None, ref_damping="jackson", N_x: int = 4000):
         damp = DAMPINGS[damping] if isinstance(damping, str) else int(damping)
@@ -302,6 +334,75 @@ class Context:
                                             n_eig, pr, M_ref, rdamp, float(sigma), int(N_x),
                                             C.byref(e1), C.byref(einf), _stream_of(mu)))
         return e1.value, einf.value
+
+
+class MLP:
+    """dos_mlp (include/dos_mlp.h): moments -> DOS network trained by the library."""
+
+    def __init__(self, ctx: Context, n_in: int = 64, n_hidden: int = 512, n_out: int = 256,
+                 seed: int = 0):
+        h = C.c_void_p()
+        self.ctx = ctx
+        ctx._check(_lib.dos_mlp_create(ctx._h, int(n_in), int(n_hidden), int(n_out), int(seed),
+                                       C.byref(h)))
+        self._h = h
+        self.n_in, self.n_hidden, self.n_out = int(n_in), int(n_hidden), int(n_out)
+        cnt = C.c_int64()
+        ctx._check(_lib.dos_mlp_num_params(h, C.byref(cnt)))
+        self.n_params = cnt.value
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _lib.dos_mlp_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def dos_mlp_set_params(self, params):
+        p, _, k = _ptr(np.ascontiguousarray(params, dtype=np.float32)
+                       if not _is_torch(params) else params)
+        self.ctx._check(_lib.dos_mlp_set_params(self._h, p, _stream_of(params)))
+
+    def dos_mlp_get_params(self):
+        out = np.empty(self.n_params, dtype=np.float32)
+        self.ctx._check(_lib.dos_mlp_get_params(self._h, out.ctypes.data, C.c_void_p(0)))
+        return out
+
+    def dos_mlp_forward(self, x, out=None):
+        xa = x if _is_torch(x) else np.ascontiguousarray(x, dtype=np.float32)
+        B = int(xa.shape[0])
+        y = np.empty((B, self.n_out), dtype=np.float32) if out is None else out
+        px, _, k0 = _ptr(xa)
+        py, _, k1 = _ptr(y)
+        self.ctx._check(_lib.dos_mlp_forward(self._h, px, B, py, _stream_of(xa, y)))
+        return y
+
+    def dos_mlp_loss_grad(self, x, target, want_grads=True):
+        xa = x if _is_torch(x) else np.ascontiguousarray(x, dtype=np.float32)
+        ta = target if _is_torch(target) else np.ascontiguousarray(target, dtype=np.float32)
+        g = np.empty(self.n_params, dtype=np.float32) if want_grads else None
+        loss = C.c_float()
+        px, _, k0 = _ptr(xa)
+        pt, _, k1 = _ptr(ta)
+        pg, _, k2 = _ptr(g)
+        self.ctx._check(_lib.dos_mlp_loss_grad(self._h, px, pt, int(xa.shape[0]), C.byref(loss),
+                                               pg, _stream_of(xa, ta)))
+        return loss.value, g
+
+    def dos_mlp_train_step(self, x, target, lr: float, want_loss: bool = True):
+        xa = x if _is_torch(x) else np.ascontiguousarray(x, dtype=np.float32)
+        ta = target if _is_torch(target) else np.ascontiguousarray(target, dtype=np.float32)
+        px, _, k0 = _ptr(xa)
+        pt, _, k1 = _ptr(ta)
+        loss = C.c_float()
+        self.ctx._check(_lib.dos_mlp_train_step(self._h, px, pt, int(xa.shape[0]), float(lr),
+                                                C.byref(loss) if want_loss else None,
+                                                _stream_of(xa, ta)))
+        return loss.value if want_loss else None
 
 
 def status_string(status: int) -> str:
