@@ -238,6 +238,37 @@ int dos_kpm_moments_batched(dos_ctx *ctx, const dos_csr *A, int B, const int64_t
                             const dos_kpm_opts *opts, void *stream);
 
 /*
+ * dos_kpm_moments without any memory allocation.  The paper has no
+ * counterpart: this exists for callers that cannot call cudaMalloc while they
+ * run -- code executing while a CUDA graph is being captured around it, or
+ * applications whose device memory is owned by their own pool allocator or
+ * fixed by a budget.  It computes the same moments mu_0..mu_M as
+ * dos_kpm_moments (single matrix, start-vector counter b = 0, vector offset
+ * 0) but keeps all intermediates in one fixed 64 MiB device array that is part
+ * of the library image (every GPU that loads the library holds it until the
+ * process exits), so the caller passes only inputs and outputs and no
+ * context is needed.  It works on the calling thread's current device.
+ *   A: all three arrays in DEVICE memory; values FP64 for DOS_PREC_F64, FP32
+ *      for DOS_PREC_F32_ACC64 (no conversion copy is made).
+ *   mu: M+1 doubles in device memory.
+ *   Limits: n_v <= 256, M <= 20000, and 2 * n * ld * element_size <= 63 MiB
+ *      with ld = n_v rounded up to 2 (FP64) or 4 (FP32) -- e.g. n <= 129024
+ *      rows at n_v = 64 in FP32.  Larger problems return DOS_ENOMEM before any
+ *      work is queued.
+ *   The first call on a device looks up the array's device address (a host
+ *   symbol is only a stand-in for it); make that first call before any stream
+ *   capture.  Every call uses the same array and leaves its contents behind
+ *   (the kernels re-initialise what they read); calls that overlap on the GPU
+ *   -- from several host threads or streams -- race on it and must be
+ *   serialised by the caller.  Synchronises `stream` (to check the CSR
+ *   structure and the spectrum).
+ * Errors: DOS_EINVAL (bad argument or CSR, host pointers), DOS_ENOMEM (sizes
+ * beyond the limits), DOS_ECUDA, DOS_ESPECTRUM.  No message is recorded.
+ */
+int dos_kpm_moments_noalloc(const dos_csr *A, double lb, double ub, int M, int n_v,
+                            uint64_t seed, int precision, double *mu, void *stream);
+
+/*
  * Autotuner: time each candidate launch shape of the fused sweep kernel for a
  * few steps on this matrix (and segment layout, B >= 1; seg_rows as in
  * dos_kpm_moments_batched, NULL when B == 1) and cache the fastest in the
