@@ -1022,13 +1022,14 @@ int dos_smoothed_error(dos_ctx *ctx, const double *mu, int M, int damping, doubl
         const int N_q = (int)nq64;
         const double x0 = lb - 6.0 * sigma;
         const double h = (ub - lb + 12.0 * sigma) / (N_x - 1);
-        // scratch: mu | ref_mu | poly (M'+1 + N_q) | approx (N_x) | ref (N_x) | out (2) | eig
+        // scratch: mu | ref_mu | poly (M'+1 + 2 N_q) | approx (N_x) | ref (N_x) | out (2) | eig
         const size_t n_ref = eig ? 0 : (size_t)M_ref + 1;
         const size_t neig = eig ? (size_t)n_eig : 0;
-        const size_t nd = (size_t)(M + 1) + n_ref + (size_t)(Meff + 1) + N_q + 2 * (size_t)N_x + 2 + neig;
+        const size_t nd = (size_t)(M + 1) + n_ref + (size_t)(Meff + 1) + 2 * (size_t)N_q +
+                          2 * (size_t)N_x + 2 + neig;
         double *buf = (double *)ctx->err_buf.get(nd * sizeof(double));
         double *dmu = buf, *dref = dmu + (M + 1), *poly = dref + n_ref;
-        double *approx = poly + (Meff + 1) + N_q, *ref = approx + N_x, *out = ref + N_x;
+        double *approx = poly + (Meff + 1) + 2 * (size_t)N_q, *ref = approx + N_x, *out = ref + N_x;
         double *deig = out + 2;
         DOS_CUDA_TRY(cudaMemcpyAsync(dmu, mu, (M + 1) * sizeof(double), cudaMemcpyDefault, s));
         launch_blur_kpm(dmu, M, damping, lb, ub, sigma, N_q, x0, h, N_x, poly, approx, s);

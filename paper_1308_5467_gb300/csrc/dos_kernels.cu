@@ -51,9 +51,14 @@ __global__ void reconstruct_kernel(const double *__restrict__ a, int M, double d
     }
 }
 
-__global__ void nodes_kernel(const double *__restrict__ a, int M, int N_q, double *__restrict__ P) {
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N_q; i += gridDim.x * blockDim.x)
-        P[i] = clenshaw(a, M, cospi((i + 0.5) / (double)N_q));
+// P(t_i) and the node's position c + d t_i in eigenvalue units.
+__global__ void nodes_kernel(const double *__restrict__ a, int M, int N_q, double c, double d,
+                             double *__restrict__ P, double *__restrict__ Y) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N_q; i += gridDim.x * blockDim.x) {
+        const double t = cospi((i + 0.5) / (double)N_q);
+        P[i] = clenshaw(a, M, t);
+        Y[i] = c + d * t;
+    }
 }
 
 __device__ __forceinline__ double gauss(double u, double inv_sigma, double norm) {
@@ -74,15 +79,17 @@ __device__ __forceinline__ double block_sum_d(double s) {
     return tot;
 }
 
-__global__ void blur_kpm_kernel(const double *__restrict__ P, int N_q, double c, double d,
+__global__ void blur_kpm_kernel(const double *__restrict__ P, const double *__restrict__ Y, int N_q,
                                 double sigma, double x0, double h, int N_x, double *out) {
     const double inv_s = 1.0 / sigma, norm = 1.0 / sqrt(2.0 * M_PI * sigma * sigma);
+    // exp(-z^2/2) underflows to exactly 0 in FP64 beyond |z| = 38.6: skip those nodes
+    const double cut = 38.7 * sigma;
     for (int m = blockIdx.x; m < N_x; m += gridDim.x) {
         const double x = x0 + m * h;
         double s = 0.0;
         for (int i = threadIdx.x; i < N_q; i += blockDim.x) {
-            const double ti = cospi((i + 0.5) / (double)N_q);
-            s += P[i] * gauss(x - c - d * ti, inv_s, norm);
+            const double u = x - Y[i];
+            if (fabs(u) < cut) s += P[i] * gauss(u, inv_s, norm);
         }
         s = block_sum_d(s);
         if (threadIdx.x == 0) out[m] = s / N_q;
@@ -156,18 +163,17 @@ void launch_reconstruct(const double *mu, int M, int damping, double lb, double 
     DOS_LAUNCHED();
 }
 
-// poly_scratch: (M+1) coefficients followed by N_q node values.
+// poly_scratch: (M+1) coefficients, N_q node values, N_q node positions.
 void launch_blur_kpm(const double *mu, int M, int damping, double lb, double ub, double sigma,
                      int N_q, double x0, double h, int N_x, double *poly_scratch, double *out,
                      cudaStream_t s) {
-    double *a = poly_scratch, *P = poly_scratch + (M + 1);
+    double *a = poly_scratch, *P = poly_scratch + (M + 1), *Y = P + N_q;
     coef_kernel<<<grid_cap(M + 1, 256, 1024), 256, 0, s>>>(mu, M, damping, a);
     DOS_LAUNCHED();
-    nodes_kernel<<<grid_cap(N_q, 256, 4096), 256, 0, s>>>(a, M, N_q, P);
+    nodes_kernel<<<grid_cap(N_q, 256, 4096), 256, 0, s>>>(a, M, N_q, 0.5 * (lb + ub),
+                                                          0.5 * (ub - lb), P, Y);
     DOS_LAUNCHED();
-    blur_kpm_kernel<<<N_x < 65535 ? N_x : 65535, 256, 0, s>>>(P, N_q, 0.5 * (lb + ub),
-                                                               0.5 * (ub - lb), sigma, x0, h,
-                                                               N_x, out);
+    blur_kpm_kernel<<<N_x < 65535 ? N_x : 65535, 256, 0, s>>>(P, Y, N_q, sigma, x0, h, N_x, out);
     DOS_LAUNCHED();
 }
 

@@ -61,13 +61,23 @@ __device__ __forceinline__ void ff_add_prod(FF &a, float x, float y) {
     a.hi = s;
     a.lo = __fadd_rn(a.lo, __fadd_rn(e, pe));
 }
+// Add a float to the pair with the same two-sum (no product split).
+__device__ __forceinline__ void ff_add(FF &a, float v) {
+    const float s = __fadd_rn(a.hi, v);
+    const float bb = __fsub_rn(s, a.hi);
+    const float e = __fadd_rn(__fsub_rn(a.hi, __fsub_rn(s, bb)), __fsub_rn(v, bb));
+    a.hi = s;
+    a.lo = __fadd_rn(a.lo, e);
+}
 __device__ __forceinline__ double acc_value(const FF &a) { return (double)a.hi + (double)a.lo; }
 __device__ __forceinline__ void acc_zero(FF &a) { a.hi = 0.f; a.lo = 0.f; }
 __device__ __forceinline__ void acc_add_prod(FF &a, float x, float y) { ff_add_prod(a, x, y); }
+__device__ __forceinline__ void acc_add(FF &a, float v) { ff_add(a, v); }
 
 __device__ __forceinline__ double acc_value(const double &a) { return a; }
 __device__ __forceinline__ void acc_zero(double &a) { a = 0.0; }
 __device__ __forceinline__ void acc_add_prod(double &a, double x, double y) { a = fma(x, y, a); }
+__device__ __forceinline__ void acc_add(double &a, double v) { a += v; }
 
 template <typename T> struct Traits;
 template <> struct Traits<float> {
@@ -208,11 +218,39 @@ __device__ __forceinline__ void block_reduce_store(const Acc (&acc)[CPT][VPT], d
     __syncthreads();
 }
 
-template <typename T, int G, int CPT>
-__global__ void __launch_bounds__(kBlock) step_kernel(const StepParams<T> p) {
+// One block per row tile; a team of G threads shares a matrix row, thread g of
+// the team owning the 16-byte chunks g, g+G, ..., g+(CPT-1)G of the rows of X.
+// Per row the independent loads are issued before anything waits on them: the
+// row's own X_k[i] and X_{k-1}[i] chunks and the next row's extents first, then
+// the gathers X_k[j] of up to 8 nonzeros at a time; so a row costs about one
+// memory latency instead of a chain of four.
+// Deterministic block sum of one value per thread into *out (red: >= 32 doubles).
+template <typename Acc>
+__device__ __forceinline__ void block_reduce_scalar(const Acc &acc, double *out, double *red) {
+    double v = acc_value(acc);
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0) red[warp] = v;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double s = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w];
+        *out = s;
+    }
+    __syncthreads();
+}
+
+// PV: keep one accumulator per vector (per-vector moments requested); otherwise
+// each thread first sums its row's products over its own vectors in the
+// working precision (at most 4*CPT terms, an error at the level of the FP32
+// rounding of the vectors themselves) and accumulates those row sums.
+template <typename T, int G, int CPT, bool PV>
+__global__ void __launch_bounds__(kBlock, 3) step_kernel(const StepParams<T> p) {
     constexpr int VPT = Traits<T>::VPT;
     using Acc = typename Traits<T>::Acc;
     constexpr int TPW = 32 / G;  // teams per warp
+    constexpr int U = 8;         // nonzeros per gather batch
     extern __shared__ double red[];
 
     const int4 tl = p.tiles[blockIdx.x];
@@ -226,13 +264,18 @@ __global__ void __launch_bounds__(kBlock) step_kernel(const StepParams<T> p) {
     const int ld = p.ld;
     const T *__restrict__ xseg = p.xc + (size_t)p.seg_row0[seg] * ld;
     const T *__restrict__ xc = p.xc;
+    const int32_t *__restrict__ row_ptr = p.row_ptr;
+    const int32_t *__restrict__ col_idx = p.col_idx;
+    const T *__restrict__ val = p.val;
     T *xn = p.xn;
 
-    Acc accR[CPT][VPT], accS[CPT][VPT], acc0[CPT][VPT];
+    const bool first = p.first != 0;
+    constexpr int NA = PV ? CPT : 1, NJ = PV ? VPT : 1;
+    Acc accR[NA][NJ], accS[NA][NJ], acc0[NA][NJ];
 #pragma unroll
-    for (int cc = 0; cc < CPT; ++cc)
+    for (int cc = 0; cc < NA; ++cc)
 #pragma unroll
-        for (int j = 0; j < VPT; ++j) {
+        for (int j = 0; j < NJ; ++j) {
             acc_zero(accR[cc][j]);
             acc_zero(accS[cc][j]);
             acc_zero(acc0[cc][j]);
@@ -242,24 +285,45 @@ __global__ void __launch_bounds__(kBlock) step_kernel(const StepParams<T> p) {
 #pragma unroll
     for (int cc = 0; cc < CPT; ++cc) valid[cc] = (g + cc * G) < p.n_chunks;
 
-    for (int row = rb + team; row < re; row += n_teams) {
-        const int e0 = __ldg(p.row_ptr + row), e1 = __ldg(p.row_ptr + row + 1);
+    int row = rb + team;
+    int e0 = 0, e1 = 0;
+    if (row < re) {
+        e0 = __ldg(row_ptr + row);
+        e1 = __ldg(row_ptr + row + 1);
+    }
+    while (row < re) {
+        const size_t roff = (size_t)row * ld;
+        T xk[CPT][VPT], xo[CPT][VPT];
+#pragma unroll
+        for (int cc = 0; cc < CPT; ++cc) {
+            if (valid[cc]) {
+                const int off = (g + cc * G) * VPT;
+                load16(xc + roff + off, xk[cc]);
+                if (!first) load16(xn + roff + off, xo[cc]);
+            }
+        }
+        const int nrow = row + n_teams;
+        int ne0 = 0, ne1 = 0;
+        if (nrow < re) {
+            ne0 = __ldg(row_ptr + nrow);
+            ne1 = __ldg(row_ptr + nrow + 1);
+        }
         T y[CPT][VPT];
 #pragma unroll
         for (int cc = 0; cc < CPT; ++cc)
 #pragma unroll
             for (int j = 0; j < VPT; ++j) y[cc][j] = T(0);
-        for (int e = e0; e < e1; e += 4) {
-            int col[4];
-            T a[4];
+        for (int e = e0; e < e1; e += U) {
+            int col[U];
+            T a[U];
 #pragma unroll
-            for (int u = 0; u < 4; ++u) {
+            for (int u = 0; u < U; ++u) {
                 const bool ok = e + u < e1;
-                col[u] = ok ? __ldg(p.col_idx + e + u) : 0;
-                a[u] = ok ? __ldg(p.val + e + u) : T(0);
+                col[u] = ok ? __ldg(col_idx + e + u) : 0;
+                a[u] = ok ? __ldg(val + e + u) : T(0);
             }
 #pragma unroll
-            for (int u = 0; u < 4; ++u) {
+            for (int u = 0; u < U; ++u) {
                 if (e + u < e1) {
                     const T *src = xseg + (size_t)col[u] * ld;
 #pragma unroll
@@ -274,38 +338,57 @@ __global__ void __launch_bounds__(kBlock) step_kernel(const StepParams<T> p) {
                 }
             }
         }
-        const size_t roff = (size_t)row * ld;
+        T rr = T(0), ss = T(0), zz = T(0);
 #pragma unroll
         for (int cc = 0; cc < CPT; ++cc) {
             if (!valid[cc]) continue;
             const int off = (g + cc * G) * VPT;
-            T xk[VPT], xo[VPT], xnew[VPT];
-            load16(xc + roff + off, xk);
-            if (p.first) {
+            T xnew[VPT];
+            if (first) {
 #pragma unroll
-                for (int j = 0; j < VPT; ++j) xnew[j] = fma(-c, xk[j], y[cc][j]) * inv_d;
+                for (int j = 0; j < VPT; ++j) xnew[j] = fma(-c, xk[cc][j], y[cc][j]) * inv_d;
             } else {
-                load16(xn + roff + off, xo);
 #pragma unroll
                 for (int j = 0; j < VPT; ++j)
-                    xnew[j] = fma(T(2), fma(-c, xk[j], y[cc][j]) * inv_d, -xo[j]);
+                    xnew[j] = fma(T(2), fma(-c, xk[cc][j], y[cc][j]) * inv_d, -xo[cc][j]);
             }
             store16(xn + roff + off, xnew);
 #pragma unroll
             for (int j = 0; j < VPT; ++j) {
-                acc_add_prod(accR[cc][j], xnew[j], xk[j]);
-                acc_add_prod(accS[cc][j], xnew[j], xnew[j]);
-                if (p.first) acc_add_prod(acc0[cc][j], xk[j], xk[j]);
+                if constexpr (PV) {
+                    acc_add_prod(accR[cc][j], xnew[j], xk[cc][j]);
+                    acc_add_prod(accS[cc][j], xnew[j], xnew[j]);
+                    if (first) acc_add_prod(acc0[cc][j], xk[cc][j], xk[cc][j]);
+                } else {
+                    rr = fma(xnew[j], xk[cc][j], rr);
+                    ss = fma(xnew[j], xnew[j], ss);
+                    zz = fma(xk[cc][j], xk[cc][j], zz);
+                }
             }
         }
+        if constexpr (!PV) {
+            acc_add(accR[0][0], rr);
+            acc_add(accS[0][0], ss);
+            if (first) acc_add(acc0[0][0], zz);
+        }
+        row = nrow;
+        e0 = ne0;
+        e1 = ne1;
     }
 
-    double *out = p.part + (size_t)blockIdx.x * 2 * p.pv;
-    block_reduce_store<Acc, G, CPT, VPT>(accR, out, ld, p.n_chunks, p.pv, red);
-    block_reduce_store<Acc, G, CPT, VPT>(accS, out + p.pv, ld, p.n_chunks, p.pv, red);
-    if (p.first)
-        block_reduce_store<Acc, G, CPT, VPT>(acc0, p.part0 + (size_t)blockIdx.x * p.pv, ld,
-                                             p.n_chunks, p.pv, red);
+    if constexpr (PV) {
+        double *out = p.part + (size_t)blockIdx.x * 2 * p.pv;
+        block_reduce_store<Acc, G, CPT, VPT>(accR, out, ld, p.n_chunks, p.pv, red);
+        block_reduce_store<Acc, G, CPT, VPT>(accS, out + p.pv, ld, p.n_chunks, p.pv, red);
+        if (first)
+            block_reduce_store<Acc, G, CPT, VPT>(acc0, p.part0 + (size_t)blockIdx.x * p.pv, ld,
+                                                 p.n_chunks, p.pv, red);
+    } else {
+        double *out = p.part + (size_t)blockIdx.x * 2;
+        block_reduce_scalar(accR[0][0], out, red);
+        block_reduce_scalar(accS[0][0], out + 1, red);
+        if (first) block_reduce_scalar(acc0[0][0], p.part0 + blockIdx.x, red);
+    }
 }
 
 // ---- kernel table --------------------------------------------------------------
@@ -313,9 +396,9 @@ template <typename T>
 using StepFn = void (*)(const StepParams<T>);
 
 template <typename T>
-StepFn<T> pick(int G, int CPT) {
+StepFn<T> pick(int G, int CPT, bool per_vec) {
 #define DOS_CASE(GG, CC) \
-    if (G == GG && CPT == CC) return step_kernel<T, GG, CC>;
+    if (G == GG && CPT == CC) return per_vec ? step_kernel<T, GG, CC, true> : step_kernel<T, GG, CC, false>;
 #define DOS_CASES(GG) DOS_CASE(GG, 1) DOS_CASE(GG, 2) DOS_CASE(GG, 4)
     DOS_CASES(1) DOS_CASES(2) DOS_CASES(4) DOS_CASES(8) DOS_CASES(16) DOS_CASES(32)
 #undef DOS_CASES
@@ -554,12 +637,12 @@ bool shape_supported(int precision, const Shape &sh, int ld) {
 int max_active_blocks(int precision, const Shape &sh) {
     int nb = 0;
     if (precision == DOS_PREC_F64) {
-        auto fn = pick<double>(sh.team, sh.chunks);
+        auto fn = pick<double>(sh.team, sh.chunks, false);
         if (!fn) return 0;
         DOS_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, sh.block,
                                                                     step_smem(sh.block, 256)));
     } else {
-        auto fn = pick<float>(sh.team, sh.chunks);
+        auto fn = pick<float>(sh.team, sh.chunks, false);
         if (!fn) return 0;
         DOS_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, sh.block,
                                                                     step_smem(sh.block, 256)));
@@ -625,7 +708,7 @@ static void launch_step_t(const SweepArgs &a, int k, int slot, cudaStream_t s) {
     p.seg_inv_d = a.seg_inv_d;
     p.part = a.partial + (size_t)slot * a.n_tiles * 2 * p.pv;
     p.part0 = a.partial0;
-    auto fn = pick<T>(a.shape.team, a.shape.chunks);
+    auto fn = pick<T>(a.shape.team, a.shape.chunks, a.per_vec != 0);
     if (!fn) throw Error{DOS_EINVAL, "unsupported launch shape"};
     fn<<<a.n_tiles, a.shape.block, step_smem(a.shape.block, a.ld), s>>>(p);
     DOS_LAUNCHED();

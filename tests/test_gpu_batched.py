@@ -110,4 +110,5 @@ def test_autotuned_shape_gives_same_moments(ctx, batch512):
     best, ms = ctx.dos_tune(A, 32, "f32", seg_rows=seg)
     assert best["team"] >= 1 and best["tiles"] >= 512 and ms > 0
     tuned = ctx.dos_kpm_moments_batched(A, seg, lb, ub, 40, 32, seed=4, precision="f32")
-    assert np.abs(tuned - default).max() < 1e-9
+    # another launch shape groups the FP32 row sums differently: within the FP32 bound
+    assert np.all(np.abs(tuned - default) <= 2e-7 * (np.arange(41) + 1) + 1e-6)
