@@ -345,6 +345,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-f64-form", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--launch", default=None,
+                    help="fixed launch shape team,chunks,staged(1|2) instead of the autotuner "
+                         "(used when profiling one known kernel instance)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -377,8 +380,15 @@ def main():
     lb, ub = ctx.dos_bounds(Ad, "gershgorin", pad_frac=0.01)
     sigma = 0.02 * (ub - lb)
     # launch shape of the fused step chosen by the library's autotuner (cached in ctx)
-    tuned_shape, tuned_ms = ctx.dos_tune(Ad, n_v, prec)
-    tuned64 = ctx.dos_tune(Ad64, n_v, "f64")[0] if (prec == "f32" and not args.no_f64_form) else None
+    fixed = None
+    if args.launch:
+        t_, c_, s_ = (int(v) for v in args.launch.split(","))
+        fixed = {"team": t_, "chunks": c_, "staged": s_}
+        tuned_shape, tuned64 = fixed, None
+    else:
+        tuned_shape, tuned_ms = ctx.dos_tune(Ad, n_v, prec)
+        tuned64 = (ctx.dos_tune(Ad64, n_v, "f64")[0]
+                   if (prec == "f32" and not args.no_f64_form) else None)
     # reference DOS for the smoothed error: FP64 sweep with 1024 independent vectors
     ref_mu = ctx.dos_kpm_moments(Ad64, lb, ub, M, 1024, seed=seed + 1000, precision="f64",
                                  vec_offset=0)
@@ -386,7 +396,8 @@ def main():
     def step(Acsr, precision, host=False):
         lo, hi = ctx.dos_bounds(Acsr, "gershgorin", pad_frac=0.01)
         mu = ctx.dos_kpm_moments(Acsr, lo, hi, M, n_v, seed=seed, precision=precision,
-                                 vec_offset=vec_offset)
+                                 vec_offset=vec_offset,
+                                 launch=fixed if precision == prec else None)
         phi = ctx.dos_reconstruct(mu, M, "jackson", lo, hi, N_t=1000)
         e1, einf = ctx.dos_smoothed_error(mu, M, "jackson", lo, hi, sigma, ref_mu=ref_mu)
         return mu, phi, e1, einf

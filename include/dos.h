@@ -78,6 +78,9 @@ extern "C" {
                                        replaying a cached CUDA graph */
 #define DOS_OPT_AUTOTUNE 8u         /* time the candidate launch shapes on this matrix
                                        once and cache the fastest (see dos_tune) */
+#define DOS_OPT_TEST_STALL_WAIT 16u /* failure-detection tests only: the staged kernel
+                                       expects 16 bytes more than it copies, so its first
+                                       wait can never complete and must run out */
 
 typedef struct dos_ctx dos_ctx;
 
@@ -100,6 +103,9 @@ typedef struct {
     int32_t chunks;          /* 16-byte vector chunks per thread (1, 2, 4 or 8) */
     int32_t block;           /* threads per block (64..1024, multiple of 32) */
     int32_t tiles;           /* row tiles = blocks per sweep step */
+    int32_t staged;          /* 1: rows of X_k / X_{k-1} loaded by the threads;
+                                2: row panels of X_k and X_{k-1} staged in shared memory
+                                by bulk asynchronous (TMA) copies */
 } dos_launch;
 
 /* Optional arguments of the _ex / _batched entry points (NULL = defaults). */
@@ -111,6 +117,9 @@ typedef struct {
     uint64_t batch_index;    /* matrix index b used by the start-vector counter
                                 (single-matrix calls; default 0) */
     dos_launch launch;       /* launch shape override (zeros = autotuned/default) */
+    int64_t wait_limit_cycles; /* limit of each device-side wait of the staged kernel, in
+                                SM clock cycles (0 = about one second); a wait that runs
+                                out makes the call return DOS_ETIMEOUT */
 } dos_kpm_opts;
 
 /* ---- context --------------------------------------------------------------- */

@@ -4,6 +4,8 @@
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
+#include <stdio.h>
+#include <stdlib.h>
 #include <string.h>
 
 #include <algorithm>
@@ -184,16 +186,26 @@ Shape tune_shape(dos_ctx *ctx, const dos_csr *A, int B, const int64_t *seg_rows,
 Shape choose_shape(dos_ctx *ctx, const SweepRequest &r, const dos_csr *Adesc, int ld,
                    int64_t n_rows, int64_t nnz, cudaStream_t s) {
     const dos_launch &o = r.opts.launch;
-    if (o.team || o.chunks || o.block || o.tiles) {
+    if (o.team || o.chunks || o.block || o.tiles || o.staged) {
         Shape d = default_shape(r.precision, ld, ctx->num_sms, n_rows);
         Shape sh;
         sh.team = o.team ? o.team : d.team;
         sh.chunks = o.chunks ? o.chunks : d.chunks;
         sh.block = o.block ? o.block : d.block;
-        sh.tiles = o.tiles ? o.tiles : d.tiles;
+        sh.staged = o.staged ? (o.staged == 2) : d.staged;
+        sh.tiles = 1;
+        DOS_REQUIRE(o.staged >= 0 && o.staged <= 2, "launch.staged must be 0, 1 or 2");
         DOS_REQUIRE(shape_supported(r.precision, sh, ld),
                     "launch override does not cover the vector block (team*chunks*16B >= row) "
-                    "or uses an unsupported team/chunks/block");
+                    "or uses an unsupported team/chunks/block/staged combination");
+        if (o.tiles) {
+            sh.tiles = o.tiles;
+        } else {
+            const int occ = std::max(1, max_active_blocks(r.precision, sh, ld));
+            const int teams = (sh.block / 32) * (32 / sh.team);
+            sh.tiles = (int)std::max<int64_t>(
+                1, std::min<int64_t>((int64_t)ctx->num_sms * occ, (n_rows + teams - 1) / teams));
+        }
         return sh;
     }
     auto it = ctx->tuned.find(std::make_tuple(n_rows, nnz, r.B, std::min(r.n_v, kPanelMax),
@@ -339,6 +351,9 @@ void run_sweep(dos_ctx *ctx, const dos_csr *Adesc, SweepRequest &r, cudaStream_t
     a.seed = r.seed;
     a.batch_index = r.opts.batch_index;
     a.shape = sh;
+    a.status = status;
+    a.spin_cycles = r.opts.wait_limit_cycles;
+    a.stall_test = (r.opts.flags & DOS_OPT_TEST_STALL_WAIT) ? 1 : 0;
 
     const double tol = r.precision == DOS_PREC_F64 ? 1e-8 : 1e-3;
     const bool profiling = ctx->profiling;
@@ -455,6 +470,9 @@ void run_sweep(dos_ctx *ctx, const dos_csr *Adesc, SweepRequest &r, cudaStream_t
             }
             ctx->prof_sweeps += 1;
         }
+        if (h & 4)
+            throw Error{DOS_ETIMEOUT,
+                        "a bounded device-side wait of the staged sweep kernel ran out"};
         if (!(r.opts.flags & DOS_OPT_NO_SPECTRUM_CHECK) && (h & 2))
             throw Error{DOS_ESPECTRUM,
                         "a moment exceeds mu_0 in magnitude or is not finite: the bounds do not "
@@ -496,14 +514,18 @@ Shape tune_shape(dos_ctx *ctx, const dos_csr *A, int B, const int64_t *seg_rows,
     double best_t = INFINITY;
     bool first = true;
     for (int G = 1; G <= 32; G <<= 1) {
-        for (int C : {1, 2, 4}) {
+        for (int C : {1, 2, 4})
+        for (int staged : {0, 1}) {
             const int cover = G * C;
             if (cover < chunks || (cover > 1 && cover / 2 >= chunks)) continue;
             Shape sh;
             sh.team = G;
             sh.chunks = C;
             sh.block = 256;
-            const int occ = max_active_blocks(precision, sh);
+            sh.staged = staged;
+            sh.tiles = 1;
+            if (!shape_supported(precision, sh, ld)) continue;
+            const int occ = max_active_blocks(precision, sh, ld);
             if (occ <= 0) continue;
             const int teams = (256 / 32) * (32 / G);
             const int64_t max_tiles = std::max<int64_t>(B, (A->n + teams - 1) / teams);
@@ -530,6 +552,7 @@ Shape tune_shape(dos_ctx *ctx, const dos_csr *A, int B, const int64_t *seg_rows,
                         r.opts.launch.chunks = sh.chunks;
                         r.opts.launch.block = sh.block;
                         r.opts.launch.tiles = sh.tiles;
+                        r.opts.launch.staged = sh.staged ? 2 : 1;
                         DOS_CUDA_TRY(cudaEventRecord(e0, s));
                         run_sweep(ctx, A, r, s);
                         DOS_CUDA_TRY(cudaEventRecord(e1, s));
@@ -539,6 +562,9 @@ Shape tune_shape(dos_ctx *ctx, const dos_csr *A, int B, const int64_t *seg_rows,
                     }
                     per_step = std::min(per_step, (double)(ms[1] - ms[0]) / 16.0);
                 }
+                if (getenv("DOS_TUNE_VERBOSE"))
+                    fprintf(stderr, "dos_tune: team %d chunks %d staged %d tiles %d: %.4f ms/step\n",
+                            sh.team, sh.chunks, sh.staged, sh.tiles, per_step);
                 if (per_step < best_t) {
                     best_t = per_step;
                     best = sh;
@@ -830,6 +856,7 @@ int dos_tune(dos_ctx *ctx, const dos_csr *A, int B, const int64_t *seg_rows, int
             best->chunks = sh.chunks;
             best->block = sh.block;
             best->tiles = sh.tiles;
+            best->staged = sh.staged ? 2 : 1;
         }
     });
 }

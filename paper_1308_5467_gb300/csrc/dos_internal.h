@@ -82,6 +82,7 @@ struct PinnedBuffer {
 // Launch shape of the fused step kernel.
 struct Shape {
     int team = 0, chunks = 0, block = 0, tiles = 0;
+    int staged = 0;  // 1: TMA-staged row panels (step_staged_kernel)
 };
 
 // Cached CUDA graph for one sweep configuration.
@@ -167,12 +168,15 @@ struct SweepArgs {
     int64_t vec_offset;
     uint64_t batch_index;     // counter field b for segment 0 (segment s uses b + s)
     Shape shape;
+    int *status = nullptr;    // device flags: bit 1 spectrum, bit 2 wait timeout
+    long long spin_cycles = 0;  // bounded-wait limit (0: about one second)
+    int stall_test = 0;       // tests only: make the staged kernel's first wait run out
 };
 
 // Occupancy-derived default shape for (precision, ld).
 Shape default_shape(int precision, int ld, int num_sms, int64_t n_rows);
 bool shape_supported(int precision, const Shape &sh, int ld);
-int max_active_blocks(int precision, const Shape &sh);
+int max_active_blocks(int precision, const Shape &sh, int ld);
 
 void launch_init_vectors(const SweepArgs &a, cudaStream_t s);
 // Step k (0-based): reads x_cur = blocks[k%2], writes blocks[(k+1)%2]; partial slice `slot`.

@@ -21,6 +21,10 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <map>
+#include <mutex>
+#include <tuple>
+
 #include "dos_internal.h"
 
 namespace dos {
@@ -161,6 +165,11 @@ struct StepParams {
     const double *seg_c, *seg_inv_d;
     double *part;   // [n_tiles][2][pv]
     double *part0;  // [n_tiles][pv]
+    int *status;    // bit 2 (value 4): a bounded device-side wait ran out
+    int panel_rows; // staged kernel: rows per shared-memory panel
+    long long spin_cycles;  // staged kernel: wait limit in SM clock cycles
+    int stall_test; // staged kernel, tests only: over-count the expected bytes so a
+                    // wait never completes and must run out
 };
 
 // Deterministic block reduction of one accumulator set into out[0..pv).
@@ -391,9 +400,272 @@ __global__ void __launch_bounds__(kBlock, 3) step_kernel(const StepParams<T> p) 
     }
 }
 
+// ---- TMA-staged variant -----------------------------------------------------------
+// The tile is walked in panels of R consecutive rows.  One elected thread
+// copies the panel's slabs X_k[r0:r0+R, :] and X_{k-1}[r0:r0+R, :] (contiguous,
+// 16-byte aligned) into shared memory with bulk asynchronous copies
+// (cp.async.bulk, the Tensor Memory Accelerator's 1-D form) that complete on an
+// mbarrier, two stages deep, so the next panel streams in while this one is
+// computed and the streaming loads hold no registers.  The gathers X_k[j] of
+// the SpMM still go through L1/L2.  Every wait is bounded: past
+// `spin_cycles` the block agrees (syncthreads_or) to stop, sets status bit 4
+// and returns after waiting, again bounded, for its copies in flight.
+__device__ __forceinline__ uint32_t smem_addr(const void *p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count)
+                 : "memory");
+}
+__device__ __forceinline__ void mbar_init_fence() {
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)),
+                 "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void bulk_copy_g2s(void *dst, const void *src, uint32_t bytes,
+                                              uint64_t *bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
+            "r"(smem_addr(dst)),
+        "l"(src), "r"(bytes), "r"(smem_addr(bar))
+        : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
+    uint32_t done;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(done)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    return done != 0;
+}
+// Bounded wait for phase `parity` of `bar`; false if `limit` cycles passed first.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity,
+                                                  long long limit) {
+    const long long t0 = clock64();
+    while (!mbar_try_wait(bar, parity)) {
+        if (clock64() - t0 > limit) return false;
+    }
+    return true;
+}
+
+template <typename T, int G, int CPT, bool PV>
+__global__ void __launch_bounds__(kBlock, 2) step_staged_kernel(const StepParams<T> p) {
+    constexpr int VPT = Traits<T>::VPT;
+    using Acc = typename Traits<T>::Acc;
+    constexpr int TPW = 32 / G;
+    constexpr int U = 8;
+    extern __shared__ __align__(128) unsigned char smem[];
+    const int ld = p.ld;
+    const int R = p.panel_rows;
+    uint64_t *bar = reinterpret_cast<uint64_t *>(smem);          // 2 barriers
+    T *slab = reinterpret_cast<T *>(smem + 128);                  // [2 stages][cur, prev][R*ld]
+    double *red = reinterpret_cast<double *>(smem + 128 + 4 * (size_t)R * ld * sizeof(T));
+
+    const int4 tl = p.tiles[blockIdx.x];
+    const int rb = tl.x, re = tl.y, seg = tl.z;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int g = lane % G;
+    const int n_teams = (blockDim.x >> 5) * TPW;
+    const int team = warp * TPW + lane / G;
+    const T c = (T)p.seg_c[seg];
+    const T inv_d = (T)p.seg_inv_d[seg];
+    const T *__restrict__ xseg = p.xc + (size_t)p.seg_row0[seg] * ld;
+    const int32_t *__restrict__ row_ptr = p.row_ptr;
+    const int32_t *__restrict__ col_idx = p.col_idx;
+    const T *__restrict__ val = p.val;
+    T *xn = p.xn;
+    const bool first = p.first != 0;
+    const int n_panels = (re - rb + R - 1) / R;
+
+    constexpr int NA = PV ? CPT : 1, NJ = PV ? VPT : 1;
+    Acc accR[NA][NJ], accS[NA][NJ], acc0[NA][NJ];
+#pragma unroll
+    for (int cc = 0; cc < NA; ++cc)
+#pragma unroll
+        for (int j = 0; j < NJ; ++j) {
+            acc_zero(accR[cc][j]);
+            acc_zero(accS[cc][j]);
+            acc_zero(acc0[cc][j]);
+        }
+    bool valid[CPT];
+#pragma unroll
+    for (int cc = 0; cc < CPT; ++cc) valid[cc] = (g + cc * G) < p.n_chunks;
+
+    if (threadIdx.x == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+        mbar_init_fence();
+    }
+    __syncthreads();
+    auto issue = [&](int panel, int stage) {
+        const int r0 = rb + panel * R;
+        const int rows = min(R, re - r0);
+        const uint32_t bytes = (uint32_t)((size_t)rows * ld * sizeof(T));
+        T *dst = slab + (size_t)stage * 2 * R * ld;
+        mbar_expect_tx(&bar[stage], (first ? bytes : 2 * bytes) + (p.stall_test ? 16u : 0u));
+        bulk_copy_g2s(dst, p.xc + (size_t)r0 * ld, bytes, &bar[stage]);
+        if (!first) bulk_copy_g2s(dst + (size_t)R * ld, xn + (size_t)r0 * ld, bytes, &bar[stage]);
+    };
+    if (threadIdx.x == 0 && n_panels > 0) issue(0, 0);
+    int issued = n_panels > 0 ? 1 : 0, consumed = 0;
+    bool timed_out = false;
+    for (int pi = 0; pi < n_panels; ++pi) {
+        const int stage = pi & 1;
+        if (threadIdx.x == 0 && pi + 1 < n_panels) issue(pi + 1, stage ^ 1);
+        if (pi + 1 < n_panels) ++issued;
+        const bool ok = mbar_wait_bounded(&bar[stage], (pi >> 1) & 1, p.spin_cycles);
+        if (__syncthreads_or(!ok)) {
+            timed_out = true;
+            break;
+        }
+        ++consumed;
+        const T *scur = slab + (size_t)stage * 2 * R * ld;
+        const T *sprev = scur + (size_t)R * ld;
+        const int r0 = rb + pi * R;
+        const int rows = min(R, re - r0);
+        int j = team;
+        int e0 = 0, e1 = 0;
+        if (j < rows) {
+            e0 = __ldg(row_ptr + r0 + j);
+            e1 = __ldg(row_ptr + r0 + j + 1);
+        }
+        while (j < rows) {
+            const int row = r0 + j;
+            const int nj = j + n_teams;
+            int ne0 = 0, ne1 = 0;
+            if (nj < rows) {
+                ne0 = __ldg(row_ptr + r0 + nj);
+                ne1 = __ldg(row_ptr + r0 + nj + 1);
+            }
+            T y[CPT][VPT];
+#pragma unroll
+            for (int cc = 0; cc < CPT; ++cc)
+#pragma unroll
+                for (int q = 0; q < VPT; ++q) y[cc][q] = T(0);
+            for (int e = e0; e < e1; e += U) {
+                int col[U];
+                T a[U];
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    const bool okk = e + u < e1;
+                    col[u] = okk ? __ldg(col_idx + e + u) : 0;
+                    a[u] = okk ? __ldg(val + e + u) : T(0);
+                }
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    if (e + u < e1) {
+                        const T *src = xseg + (size_t)col[u] * ld;
+#pragma unroll
+                        for (int cc = 0; cc < CPT; ++cc) {
+                            if (valid[cc]) {
+                                T xv[VPT];
+                                load16(src + (g + cc * G) * VPT, xv);
+#pragma unroll
+                                for (int q = 0; q < VPT; ++q) y[cc][q] = fma(a[u], xv[q], y[cc][q]);
+                            }
+                        }
+                    }
+                }
+            }
+            T rr = T(0), ss = T(0), zz = T(0);
+#pragma unroll
+            for (int cc = 0; cc < CPT; ++cc) {
+                if (!valid[cc]) continue;
+                const int off = (g + cc * G) * VPT;
+                T xk[VPT], xo[VPT], xnew[VPT];
+                load16(scur + (size_t)j * ld + off, xk);
+                if (first) {
+#pragma unroll
+                    for (int q = 0; q < VPT; ++q) xnew[q] = fma(-c, xk[q], y[cc][q]) * inv_d;
+                } else {
+                    load16(sprev + (size_t)j * ld + off, xo);
+#pragma unroll
+                    for (int q = 0; q < VPT; ++q)
+                        xnew[q] = fma(T(2), fma(-c, xk[q], y[cc][q]) * inv_d, -xo[q]);
+                }
+                store16(xn + (size_t)row * ld + off, xnew);
+#pragma unroll
+                for (int q = 0; q < VPT; ++q) {
+                    if constexpr (PV) {
+                        acc_add_prod(accR[cc][q], xnew[q], xk[q]);
+                        acc_add_prod(accS[cc][q], xnew[q], xnew[q]);
+                        if (first) acc_add_prod(acc0[cc][q], xk[q], xk[q]);
+                    } else {
+                        rr = fma(xnew[q], xk[q], rr);
+                        ss = fma(xnew[q], xnew[q], ss);
+                        zz = fma(xk[q], xk[q], zz);
+                    }
+                }
+            }
+            if constexpr (!PV) {
+                acc_add(accR[0][0], rr);
+                acc_add(accS[0][0], ss);
+                if (first) acc_add(acc0[0][0], zz);
+            }
+            j = nj;
+            e0 = ne0;
+            e1 = ne1;
+        }
+        __syncthreads();  // this stage is refilled in the next iteration
+    }
+    if (timed_out) {
+        // drain: wait (bounded) for the copies this block issued and never consumed
+        if (threadIdx.x == 0) {
+            atomicOr(p.status, 4);
+            for (int k = consumed; k < issued; ++k)
+                mbar_wait_bounded(&bar[k & 1], (k >> 1) & 1, p.spin_cycles);
+        }
+        __syncthreads();
+        return;
+    }
+    if constexpr (PV) {
+        double *out = p.part + (size_t)blockIdx.x * 2 * p.pv;
+        block_reduce_store<Acc, G, CPT, VPT>(accR, out, ld, p.n_chunks, p.pv, red);
+        block_reduce_store<Acc, G, CPT, VPT>(accS, out + p.pv, ld, p.n_chunks, p.pv, red);
+        if (first)
+            block_reduce_store<Acc, G, CPT, VPT>(acc0, p.part0 + (size_t)blockIdx.x * p.pv, ld,
+                                                 p.n_chunks, p.pv, red);
+    } else {
+        double *out = p.part + (size_t)blockIdx.x * 2;
+        block_reduce_scalar(accR[0][0], out, red);
+        block_reduce_scalar(accS[0][0], out + 1, red);
+        if (first) block_reduce_scalar(acc0[0][0], p.part0 + blockIdx.x, red);
+    }
+}
+
 // ---- kernel table --------------------------------------------------------------
 template <typename T>
 using StepFn = void (*)(const StepParams<T>);
+
+template <typename T>
+StepFn<T> pick_staged(int G, int CPT, bool per_vec) {
+#define DOS_CASE(GG, CC)                                                                     \
+    if (G == GG && CPT == CC)                                                                \
+        return per_vec ? step_staged_kernel<T, GG, CC, true> : step_staged_kernel<T, GG, CC, false>;
+    DOS_CASE(4, 1) DOS_CASE(8, 1) DOS_CASE(16, 1) DOS_CASE(32, 1)
+    DOS_CASE(8, 2) DOS_CASE(16, 2) DOS_CASE(32, 2) DOS_CASE(32, 4)
+#undef DOS_CASE
+    return nullptr;
+}
+
+// Rows per panel of the staged kernel: a multiple of the team count with the four
+// slabs within ~64 KB, at most 4 rows per team.
+int staged_panel_rows(int block, int team, int ld, int esz) {
+    const int n_teams = (block / 32) * (32 / team);
+    int rpt = 4;
+    while (rpt > 1 && (size_t)4 * n_teams * rpt * ld * esz > (size_t)64 * 1024) --rpt;
+    return n_teams * rpt;
+}
+size_t staged_smem(int block, int team, int ld, int esz) {
+    const int R = staged_panel_rows(block, team, ld, esz);
+    return 128 + (size_t)4 * R * ld * esz + (size_t)(block / 32) * ld * sizeof(double);
+}
 
 template <typename T>
 StepFn<T> pick(int G, int CPT, bool per_vec) {
@@ -631,23 +903,48 @@ bool shape_supported(int precision, const Shape &sh, int ld) {
     if (sh.team < 1 || sh.team > 32 || (sh.team & (sh.team - 1))) return false;
     if (sh.chunks != 1 && sh.chunks != 2 && sh.chunks != 4) return false;
     if (sh.tiles < 1) return false;
+    if (sh.staged && !(precision == DOS_PREC_F64 ? (void *)pick_staged<double>(sh.team, sh.chunks, false)
+                                                 : (void *)pick_staged<float>(sh.team, sh.chunks, false)))
+        return false;
     return sh.team * sh.chunks * vpt >= ld;
 }
 
-int max_active_blocks(int precision, const Shape &sh) {
+// Opt in to more than 48 KB of dynamic shared memory (per kernel, per device;
+// remembered so the driver is asked once per size).
+template <typename T>
+static void allow_smem(StepFn<T> fn, size_t bytes) {
+    static std::mutex mu;
+    static std::map<std::tuple<const void *, int>, size_t> granted;
+    int dev = 0;
+    DOS_CUDA_TRY(cudaGetDevice(&dev));
+    std::lock_guard<std::mutex> lock(mu);
+    size_t &g = granted[std::make_tuple((const void *)fn, dev)];
+    if (g >= bytes) return;
+    DOS_CUDA_TRY(cudaFuncSetAttribute((const void *)fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)bytes));
+    g = bytes;
+}
+
+template <typename T>
+static int occupancy_t(const Shape &sh, int ld) {
     int nb = 0;
-    if (precision == DOS_PREC_F64) {
-        auto fn = pick<double>(sh.team, sh.chunks, false);
+    if (sh.staged) {
+        auto fn = pick_staged<T>(sh.team, sh.chunks, false);
         if (!fn) return 0;
-        DOS_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, sh.block,
-                                                                    step_smem(sh.block, 256)));
+        const size_t sm = staged_smem(sh.block, sh.team, ld, sizeof(T));
+        allow_smem<T>(fn, sm);
+        DOS_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, sh.block, sm));
     } else {
-        auto fn = pick<float>(sh.team, sh.chunks, false);
+        auto fn = pick<T>(sh.team, sh.chunks, false);
         if (!fn) return 0;
         DOS_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, sh.block,
-                                                                    step_smem(sh.block, 256)));
+                                                                    step_smem(sh.block, ld)));
     }
     return nb;
+}
+
+int max_active_blocks(int precision, const Shape &sh, int ld) {
+    return precision == DOS_PREC_F64 ? occupancy_t<double>(sh, ld) : occupancy_t<float>(sh, ld);
 }
 
 Shape default_shape(int precision, int ld, int num_sms, int64_t n_rows) {
@@ -664,7 +961,7 @@ Shape default_shape(int precision, int ld, int num_sms, int64_t n_rows) {
         sh.team = 32;
         sh.chunks = chunks <= 64 ? 2 : 4;
     }
-    const int occ = max_active_blocks(precision, sh);
+    const int occ = max_active_blocks(precision, sh, ld);
     const int teams = (kBlock / 32) * (32 / sh.team);
     int64_t tiles = (int64_t)num_sms * (occ > 0 ? occ : 1);
     const int64_t max_tiles = (n_rows + teams - 1) / teams;
@@ -708,9 +1005,22 @@ static void launch_step_t(const SweepArgs &a, int k, int slot, cudaStream_t s) {
     p.seg_inv_d = a.seg_inv_d;
     p.part = a.partial + (size_t)slot * a.n_tiles * 2 * p.pv;
     p.part0 = a.partial0;
-    auto fn = pick<T>(a.shape.team, a.shape.chunks, a.per_vec != 0);
-    if (!fn) throw Error{DOS_EINVAL, "unsupported launch shape"};
-    fn<<<a.n_tiles, a.shape.block, step_smem(a.shape.block, a.ld), s>>>(p);
+    p.status = a.status;
+    p.spin_cycles = a.spin_cycles > 0 ? a.spin_cycles : 2000000000LL;  // ~1 s
+    p.stall_test = a.stall_test;
+    if (a.shape.staged) {
+        auto fn = pick_staged<T>(a.shape.team, a.shape.chunks, a.per_vec != 0);
+        if (!fn) throw Error{DOS_EINVAL, "unsupported staged launch shape"};
+        p.panel_rows = staged_panel_rows(a.shape.block, a.shape.team, a.ld, sizeof(T));
+        const size_t sm = staged_smem(a.shape.block, a.shape.team, a.ld, sizeof(T));
+        allow_smem<T>(fn, sm);
+        fn<<<a.n_tiles, a.shape.block, sm, s>>>(p);
+    } else {
+        auto fn = pick<T>(a.shape.team, a.shape.chunks, a.per_vec != 0);
+        if (!fn) throw Error{DOS_EINVAL, "unsupported launch shape"};
+        p.panel_rows = 0;
+        fn<<<a.n_tiles, a.shape.block, step_smem(a.shape.block, a.ld), s>>>(p);
+    }
     DOS_LAUNCHED();
 }
 

@@ -145,6 +145,7 @@ extern "C" int dos_kpm_moments_noalloc(const dos_csr *A, double lb, double ub, i
         a.vec_offset = 0;
         a.batch_index = 0;
         a.shape = sh;
+        a.status = status;
         launch_init_vectors(a, s);
         int k0 = 0;
         for (int k = 0; k < S; ++k) {

@@ -30,6 +30,7 @@ DOS_PREC_F64, DOS_PREC_F32_ACC64 = 0, 1
 DOS_BOUNDS_GERSHGORIN, DOS_BOUNDS_LANCZOS = 0, 1
 DOS_DAMP_NONE, DOS_DAMP_JACKSON = 0, 1
 DOS_OPT_NO_VALIDATE, DOS_OPT_NO_SPECTRUM_CHECK, DOS_OPT_NO_GRAPH, DOS_OPT_AUTOTUNE = 1, 2, 4, 8
+DOS_OPT_TEST_STALL_WAIT = 16
 
 PRECISIONS = {"f64": DOS_PREC_F64, "f32": DOS_PREC_F32_ACC64}
 DAMPINGS = {"none": DOS_DAMP_NONE, "jackson": DOS_DAMP_JACKSON}
@@ -44,12 +45,12 @@ class dos_csr(C.Structure):
 
 class dos_launch(C.Structure):
     _fields_ = [("team", C.c_int32), ("chunks", C.c_int32), ("block", C.c_int32),
-                ("tiles", C.c_int32)]
+                ("tiles", C.c_int32), ("staged", C.c_int32)]
 
 
 class dos_kpm_opts(C.Structure):
     _fields_ = [("flags", C.c_uint32), ("vec_offset", C.c_int64), ("batch_index", C.c_uint64),
-                ("launch", dos_launch)]
+                ("launch", dos_launch), ("wait_limit_cycles", C.c_int64)]
 
 
 _vp, _i, _i64, _u64, _d = C.c_void_p, C.c_int, C.c_int64, C.c_uint64, C.c_double
@@ -240,24 +241,26 @@ class Context:
                                             _stream_of(A.row_ptr)))
         return lb, ub
 
-    def _opts(self, flags=0, vec_offset=0, batch_index=0, launch=None):
+    def _opts(self, flags=0, vec_offset=0, batch_index=0, launch=None, wait_limit_cycles=0):
         o = dos_kpm_opts()
         o.flags = int(flags)
         o.vec_offset = int(vec_offset)
         o.batch_index = int(batch_index)
+        o.wait_limit_cycles = int(wait_limit_cycles)
         if launch:
-            o.launch = dos_launch(*[int(launch.get(k, 0)) for k in ("team", "chunks", "block", "tiles")])
+            o.launch = dos_launch(*[int(launch.get(k, 0))
+                                    for k in ("team", "chunks", "block", "tiles", "staged")])
         return o
 
     def dos_kpm_moments(self, A: CSRArrays, lb: float, ub: float, M: int, n_v: int, seed: int,
                         precision="f64", mu=None, mu_per_vec=None, flags=0, vec_offset=0,
-                        batch_index=0, launch=None):
+                        batch_index=0, launch=None, wait_limit_cycles=0):
         """Moments mu_0..mu_M (numpy float64 unless `mu` is given)."""
         prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
         out = np.empty(M + 1, dtype=np.float64) if mu is None else mu
         pmu, _, k0 = _ptr(out)
         ppv, _, k1 = _ptr(mu_per_vec)
-        opts = self._opts(flags, vec_offset, batch_index, launch)
+        opts = self._opts(flags, vec_offset, batch_index, launch, wait_limit_cycles)
         self._check(_lib.dos_kpm_moments_ex(self._h, C.byref(A.desc), float(lb), float(ub),
                                             int(M), int(n_v), int(seed), prec, pmu, ppv,
                                             C.byref(opts), _stream_of(A.row_ptr, out)))
@@ -291,7 +294,7 @@ class Context:
                                   None if seg is None else seg.ctypes.data, int(n_v), prec,
                                   C.byref(best), C.byref(ms), _stream_of(A.row_ptr)))
         return {"team": best.team, "chunks": best.chunks, "block": best.block,
-                "tiles": best.tiles}, ms.value
+                "tiles": best.tiles, "staged": best.staged}, ms.value
 
     def dos_reconstruct(self, mu, M: int, damping="jackson", lb: float = -1.0, ub: float = 1.0,
                         t=None, N_t: int = 1000, phi_hat=None, phi_lambda=None,

@@ -149,6 +149,50 @@ def test_launch_shapes_agree(ctx, launch):
     assert np.abs(mu - ref).max() < TOL64
 
 
+@pytest.mark.parametrize("precision", ["f64", "f32"])
+@pytest.mark.parametrize("launch", [{"staged": 2}, {"team": 8, "chunks": 2, "staged": 2},
+                                    {"team": 32, "chunks": 1, "staged": 2, "tiles": 5},
+                                    {"team": 16, "chunks": 1, "staged": 2, "tiles": 333}])
+def test_staged_panels_parity(ctx, precision, launch):
+    """Row panels staged in shared memory by bulk asynchronous copies: ragged
+    last panels, one tile of many panels, many tiles of one panel, ragged n_v."""
+    A = anderson_3d(13, 6.0, seed=4)
+    lb, ub = -9.6, 9.6
+    dtype = np.float64 if precision == "f64" else np.float32
+    Aw = A.astype(dtype)
+    for n_v in (64, 20):
+        if launch.get("team", 16) * launch.get("chunks", 1) * (2 if precision == "f64" else 4) < n_v:
+            continue
+        pv = np.empty((n_v, 71))
+        mu = ctx.dos_kpm_moments(dev(Aw), lb, ub, 70, n_v, seed=5, precision=precision,
+                                 launch=launch, mu_per_vec=pv)
+        mu_tot = ctx.dos_kpm_moments(dev(Aw), lb, ub, 70, n_v, seed=5, precision=precision,
+                                     launch=launch)
+        ref = okpm.kpm_moments_per_vector(Aw, lb, ub, 70, n_v, seed=5)
+        tol = TOL64 if precision == "f64" else tol32(70)
+        assert np.all(np.abs(pv - ref) <= tol)
+        assert np.all(np.abs(mu - ref.mean(axis=0)) <= tol)
+        assert np.all(np.abs(mu_tot - ref.mean(axis=0)) <= tol)
+
+
+def test_bounded_wait_timeout_is_reported_and_context_survives(ctx):
+    """Failure detection: the staged kernel's wait is made to run out (it
+    expects bytes that never arrive); the call returns DOS_ETIMEOUT after the
+    short limit and the next call on the same context works."""
+    from paper_1308_5467_gb300 import dos
+    A = dev(anderson_3d(10, 3.0, seed=2))
+    with pytest.raises(dos.DosError) as ei:
+        ctx.dos_kpm_moments(A, -8.0, 8.0, 10, 16, seed=1, precision="f32",
+                            launch={"staged": 2}, flags=dos.DOS_OPT_TEST_STALL_WAIT,
+                            wait_limit_cycles=2_000_000)
+    assert ei.value.status == dos.DOS_ETIMEOUT
+    ok = ctx.dos_kpm_moments(A, -8.0, 8.0, 10, 16, seed=1, precision="f32",
+                             launch={"staged": 2})
+    ref = okpm.kpm_moments(anderson_3d(10, 3.0, seed=2).astype(np.float32), -8.0, 8.0, 10, 16,
+                           seed=1)
+    assert np.all(np.abs(ok - ref) <= tol32(10))
+
+
 def test_launch_shape_that_misses_columns_is_rejected(ctx):
     from paper_1308_5467_gb300 import dos
     A = anderson_3d(5, 1.0, seed=3)
