@@ -233,6 +233,40 @@ __device__ __forceinline__ void block_reduce_store(const Acc (&acc)[CPT][VPT], d
 // row's own X_k[i] and X_{k-1}[i] chunks and the next row's extents first, then
 // the gathers X_k[j] of up to 8 nonzeros at a time; so a row costs about one
 // memory latency instead of a chain of four.
+// The next U (column, value) pairs of the team's row, starting at entry e
+// (entries at or past e1 come back as column 0, value 0).  Thread g of the team
+// loads entries e + g, e + g + G, ... once, and the team exchanges them by
+// shuffles among its own lanes (mask), instead of every thread loading all U.
+template <typename T, int G, int U>
+__device__ __forceinline__ void team_fetch(const int32_t *__restrict__ col_idx,
+                                           const T *__restrict__ val, int e, int e1, int g,
+                                           int team_base, unsigned mask, int (&col)[U],
+                                           T (&a)[U]) {
+    constexpr int PER = (U + G - 1) / G;
+    int mc[PER];
+    T ma[PER];
+#pragma unroll
+    for (int q = 0; q < PER; ++q) {
+        const int idx = e + g + q * G;
+        const bool ok = (g + q * G < U) && idx < e1;
+        mc[q] = ok ? __ldg(col_idx + idx) : 0;
+        ma[q] = ok ? __ldg(val + idx) : T(0);
+    }
+    if constexpr (G == 1) {
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            col[u] = mc[u];
+            a[u] = ma[u];
+        }
+    } else {
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            col[u] = __shfl_sync(mask, mc[u / G], team_base + (u % G));
+            a[u] = __shfl_sync(mask, ma[u / G], team_base + (u % G));
+        }
+    }
+}
+
 // Deterministic block sum of one value per thread into *out (red: >= 32 doubles).
 template <typename Acc>
 __device__ __forceinline__ void block_reduce_scalar(const Acc &acc, double *out, double *red) {
@@ -259,7 +293,7 @@ __global__ void __launch_bounds__(kBlock, 3) step_kernel(const StepParams<T> p) 
     constexpr int VPT = Traits<T>::VPT;
     using Acc = typename Traits<T>::Acc;
     constexpr int TPW = 32 / G;  // teams per warp
-    constexpr int U = 8;         // nonzeros per gather batch
+    constexpr int U = CPT >= 4 ? 4 : 8;  // nonzeros per gather batch (bounded registers)
     extern __shared__ double red[];
 
     const int4 tl = p.tiles[blockIdx.x];
@@ -268,6 +302,8 @@ __global__ void __launch_bounds__(kBlock, 3) step_kernel(const StepParams<T> p) 
     const int g = lane % G;
     const int n_teams = (blockDim.x >> 5) * TPW;
     const int team = warp * TPW + lane / G;
+    const int team_base = (lane / G) * G;
+    const unsigned team_mask = G == 32 ? 0xffffffffu : (((1u << G) - 1u) << team_base);
     const T c = (T)p.seg_c[seg];
     const T inv_d = (T)p.seg_inv_d[seg];
     const int ld = p.ld;
@@ -325,12 +361,7 @@ __global__ void __launch_bounds__(kBlock, 3) step_kernel(const StepParams<T> p) 
         for (int e = e0; e < e1; e += U) {
             int col[U];
             T a[U];
-#pragma unroll
-            for (int u = 0; u < U; ++u) {
-                const bool ok = e + u < e1;
-                col[u] = ok ? __ldg(col_idx + e + u) : 0;
-                a[u] = ok ? __ldg(val + e + u) : T(0);
-            }
+            team_fetch<T, G, U>(col_idx, val, e, e1, g, team_base, team_mask, col, a);
 #pragma unroll
             for (int u = 0; u < U; ++u) {
                 if (e + u < e1) {
@@ -459,7 +490,7 @@ __global__ void __launch_bounds__(kBlock, 2) step_staged_kernel(const StepParams
     constexpr int VPT = Traits<T>::VPT;
     using Acc = typename Traits<T>::Acc;
     constexpr int TPW = 32 / G;
-    constexpr int U = 8;
+    constexpr int U = CPT >= 4 ? 4 : 8;
     extern __shared__ __align__(128) unsigned char smem[];
     const int ld = p.ld;
     const int R = p.panel_rows;
@@ -473,6 +504,8 @@ __global__ void __launch_bounds__(kBlock, 2) step_staged_kernel(const StepParams
     const int g = lane % G;
     const int n_teams = (blockDim.x >> 5) * TPW;
     const int team = warp * TPW + lane / G;
+    const int team_base = (lane / G) * G;
+    const unsigned team_mask = G == 32 ? 0xffffffffu : (((1u << G) - 1u) << team_base);
     const T c = (T)p.seg_c[seg];
     const T inv_d = (T)p.seg_inv_d[seg];
     const T *__restrict__ xseg = p.xc + (size_t)p.seg_row0[seg] * ld;
@@ -551,12 +584,7 @@ __global__ void __launch_bounds__(kBlock, 2) step_staged_kernel(const StepParams
             for (int e = e0; e < e1; e += U) {
                 int col[U];
                 T a[U];
-#pragma unroll
-                for (int u = 0; u < U; ++u) {
-                    const bool okk = e + u < e1;
-                    col[u] = okk ? __ldg(col_idx + e + u) : 0;
-                    a[u] = okk ? __ldg(val + e + u) : T(0);
-                }
+                team_fetch<T, G, U>(col_idx, val, e, e1, g, team_base, team_mask, col, a);
 #pragma unroll
                 for (int u = 0; u < U; ++u) {
                     if (e + u < e1) {
