@@ -494,10 +494,10 @@ def main():
                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms_per_step": ms_e2e}
 
     if world > 1:
-        t = torch.from_numpy(mu).to(device)
-        dist.all_reduce(t)
-        mu_all = (t / world).cpu().numpy()
-        del mu_all
+        # the ranks swept disjoint blocks of start vectors (offset rank * n_v):
+        # one weighted all-reduce of M+1 doubles gives the moments of all of them
+        from paper_1308_5467_gb300.shard import combine_moments, torch_all_reduce
+        mu = combine_moments(mu, n_v, n_v * world, torch_all_reduce(device=device))
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
