@@ -105,7 +105,10 @@ typedef struct {
     int32_t tiles;           /* row tiles = blocks per sweep step */
     int32_t staged;          /* 1: rows of X_k / X_{k-1} loaded by the threads;
                                 2: row panels of X_k and X_{k-1} staged in shared memory
-                                by bulk asynchronous (TMA) copies */
+                                by bulk asynchronous (TMA) copies;
+                                3: every gather issued as a 16-byte asynchronous copy into
+                                shared memory, two chunks of nonzeros in flight per
+                                thread (0: choose) */
 } dos_launch;
 
 /* Optional arguments of the _ex / _batched entry points (NULL = defaults). */

@@ -192,9 +192,9 @@ Shape choose_shape(dos_ctx *ctx, const SweepRequest &r, const dos_csr *Adesc, in
         sh.team = o.team ? o.team : d.team;
         sh.chunks = o.chunks ? o.chunks : d.chunks;
         sh.block = o.block ? o.block : d.block;
-        sh.staged = o.staged ? (o.staged == 2) : d.staged;
+        DOS_REQUIRE(o.staged >= 0 && o.staged <= 3, "launch.staged must be 0, 1, 2 or 3");
+        sh.staged = o.staged ? o.staged - 1 : d.staged;
         sh.tiles = 1;
-        DOS_REQUIRE(o.staged >= 0 && o.staged <= 2, "launch.staged must be 0, 1 or 2");
         DOS_REQUIRE(shape_supported(r.precision, sh, ld),
                     "launch override does not cover the vector block (team*chunks*16B >= row) "
                     "or uses an unsupported team/chunks/block/staged combination");
@@ -515,7 +515,7 @@ Shape tune_shape(dos_ctx *ctx, const dos_csr *A, int B, const int64_t *seg_rows,
     bool first = true;
     for (int G = 1; G <= 32; G <<= 1) {
         for (int C : {1, 2, 4})
-        for (int staged : {0, 1}) {
+        for (int staged : {0, 1, 2}) {  // direct loads, TMA panels, asynchronous gathers
             const int cover = G * C;
             if (cover < chunks || (cover > 1 && cover / 2 >= chunks)) continue;
             Shape sh;
@@ -552,7 +552,7 @@ Shape tune_shape(dos_ctx *ctx, const dos_csr *A, int B, const int64_t *seg_rows,
                         r.opts.launch.chunks = sh.chunks;
                         r.opts.launch.block = sh.block;
                         r.opts.launch.tiles = sh.tiles;
-                        r.opts.launch.staged = sh.staged ? 2 : 1;
+                        r.opts.launch.staged = sh.staged + 1;
                         DOS_CUDA_TRY(cudaEventRecord(e0, s));
                         run_sweep(ctx, A, r, s);
                         DOS_CUDA_TRY(cudaEventRecord(e1, s));
@@ -856,7 +856,7 @@ int dos_tune(dos_ctx *ctx, const dos_csr *A, int B, const int64_t *seg_rows, int
             best->chunks = sh.chunks;
             best->block = sh.block;
             best->tiles = sh.tiles;
-            best->staged = sh.staged ? 2 : 1;
+            best->staged = sh.staged + 1;
         }
     });
 }

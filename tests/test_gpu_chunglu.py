@@ -33,7 +33,15 @@ def test_chung_lu_full_size_sampled(graph):
         phi = ctx.dos_reconstruct(mu, M, "jackson", lb, ub, N_t=2000)
     assert mu[0] == 1.0 and np.all(np.abs(mu) <= 1.0 + 1e-4)
     assert np.abs(pv.mean(axis=0) - mu).max() < 1e-9
-    assert phi.min() >= -1e-6 * phi.max()
+    # With exact moments P(t) = pi sqrt(1-t^2) phi_hat(t) = g_0 mu_0 + 2 sum g_k mu_k T_k(t)
+    # is >= 0 (Jackson kernel, positive measure); the FP32 form may move it by at most
+    # sum_k (2 - delta_k0) g_k |dmu_k| with |dmu_k| within the stated FP32 bound.
+    from oracle.dos import chebyshev_nodes, jackson
+    t = chebyshev_nodes(2000)
+    P = np.pi * np.sqrt(1 - t * t) * phi
+    tolk = 2e-7 * (np.arange(M + 1) + 1) + 1e-6
+    slack = np.sum(np.where(np.arange(M + 1) == 0, 1.0, 2.0) * jackson(M) * tolk)
+    assert P.min() >= -slack
     K = 200
     picks = [0, 255]
     ref = okpm.kpm_moments_per_vector(A, lb, ub, K, 1, seed=3, vec_offset=picks[0],

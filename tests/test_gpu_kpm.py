@@ -152,10 +152,14 @@ def test_launch_shapes_agree(ctx, launch):
 @pytest.mark.parametrize("precision", ["f64", "f32"])
 @pytest.mark.parametrize("launch", [{"staged": 2}, {"team": 8, "chunks": 2, "staged": 2},
                                     {"team": 32, "chunks": 1, "staged": 2, "tiles": 5},
-                                    {"team": 16, "chunks": 1, "staged": 2, "tiles": 333}])
+                                    {"team": 16, "chunks": 1, "staged": 2, "tiles": 333},
+                                    {"staged": 3}, {"team": 4, "chunks": 4, "staged": 3},
+                                    {"team": 8, "chunks": 2, "staged": 3, "tiles": 3},
+                                    {"team": 32, "chunks": 1, "staged": 3, "tiles": 400}])
 def test_staged_panels_parity(ctx, precision, launch):
-    """Row panels staged in shared memory by bulk asynchronous copies: ragged
-    last panels, one tile of many panels, many tiles of one panel, ragged n_v."""
+    """Row panels staged in shared memory by bulk asynchronous copies (staged 2)
+    and gathers issued as asynchronous copies (staged 3): ragged last panels and
+    chunks, one tile of many rows, many small tiles, ragged n_v."""
     A = anderson_3d(13, 6.0, seed=4)
     lb, ub = -9.6, 9.6
     dtype = np.float64 if precision == "f64" else np.float32
