@@ -346,6 +346,49 @@ int dos_smoothed_error(dos_ctx *ctx, const double *mu, int M, int damping, doubl
                        int ref_damping, double sigma, int N_x, double *err_l1, double *err_inf,
                        void *stream);
 
+/* ---- the Lanczos DOS (Section 3.2.1) -------------------------------------- */
+/*
+ * n_v independent M-step Lanczos runs (Eq. lanfact, plain three-term
+ * recurrence without reorthogonalisation, FP64) from the unit-normalised
+ * Rademacher start vectors l = 0..n_v-1 of `seed` (the vectors of
+ * dos_kpm_moments), advanced together as one block SpMM per step.  For each
+ * run the eigenvalues theta (Ritz values) of its tridiagonal T and the squared
+ * first components of the unit eigenvectors (weights, summing to one) are
+ * computed on the device (implicit QL, Golub-Welsch): the quadrature of
+ * Eq. landist / Eq. tauexpand.  A run that reaches an invariant subspace
+ * (beta_j <= 1e-12 * its running norm estimate) stops after j+1 steps: its
+ * remaining entries are 0 and m_used[l] = j+1.
+ *   A: FP64 values.  1 <= M <= min(n, 4096), 1 <= n_v <= 256.
+ *   theta, weight: n_v*M doubles, [l*M + k], host or device.
+ *   m_used: NULL or n_v ints (host).
+ * Synchronises `stream`.  Errors: DOS_EINVAL, DOS_ENOMEM, DOS_ECUDA.
+ */
+int dos_lanczos_ritz(dos_ctx *ctx, const dos_csr *A, int M, int n_v, uint64_t seed,
+                     double *theta, double *weight, int *m_used, void *stream);
+
+/*
+ * The Lanczos DOS of Eq. landos at N_x points x (host or device):
+ *   phi(x) = (1/n_v) sum_l sum_k weight[l*M+k] g_sigma(x - theta[l*M+k])
+ * (the paper's extra 1/n belongs to unnormalised start vectors; with unit ones
+ * each run's weights sum to one and phi integrates to one).  phi: N_x doubles,
+ * host or device.  Synchronises `stream` when phi is host memory.
+ */
+int dos_lanczos_dos(dos_ctx *ctx, const double *theta, const double *weight, int n_v, int M,
+                    double sigma, const double *x, int N_x, double *phi, void *stream);
+
+/*
+ * dos_smoothed_error for an approximation given as weighted points (e.g. the
+ * Ritz values and weights of dos_lanczos_ritz): the approximate density is
+ * sum_j w_j g_sigma(x - p_j) / sum_j w_j, blurred by nothing further (the
+ * Gaussian is already the blur); the reference, grid and norms are those of
+ * dos_smoothed_error.  pts, wts: n_pts doubles, host or device.  err_l1,
+ * err_inf: host (may be NULL).  Synchronises `stream`.
+ */
+int dos_points_error(dos_ctx *ctx, const double *pts, const double *wts, int64_t n_pts,
+                     double lb, double ub, const double *eig, int64_t n_eig, const double *ref_mu,
+                     int M_ref, int ref_damping, double sigma, int N_x, double *err_l1,
+                     double *err_inf, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -711,7 +711,7 @@ int dos_ctx_destroy(dos_ctx *ctx) {
     for (Buffer *b : {&ctx->csr_rowptr, &ctx->csr_colidx, &ctx->csr_val, &ctx->val_f32, &ctx->xbuf,
                       &ctx->partial, &ctx->dotsum, &ctx->tiles, &ctx->segs, &ctx->status,
                       &ctx->mu_dev, &ctx->mupv_dev, &ctx->bnd_vec, &ctx->bnd_part, &ctx->bnd_out,
-                      &ctx->rec_in, &ctx->rec_out, &ctx->err_buf})
+                      &ctx->rec_in, &ctx->rec_out, &ctx->err_buf, &ctx->lz_buf})
         b->release();
     ctx->host_stage.release();
     if (ctx->graph.exec) cudaGraphExecDestroy(ctx->graph.exec);
@@ -1006,6 +1006,152 @@ int dos_reconstruct(dos_ctx *ctx, const double *mu, int M, int damping, double l
         if (phi_lambda) copy_out(phi_lambda, dphl, N_t * sizeof(double), s);
         if (!is_device_ptr(phi_hat) || (phi_lambda && !is_device_ptr(phi_lambda)))
             DOS_CUDA_TRY(cudaStreamSynchronize(s));
+    });
+}
+
+int dos_lanczos_ritz(dos_ctx *ctx, const dos_csr *Adesc, int M, int n_v, uint64_t seed,
+                     double *theta, double *weight, int *m_used, void *stream) {
+    return guarded(ctx, [&] {
+        DOS_REQUIRE(theta && weight, "theta / weight is NULL");
+        DOS_REQUIRE(n_v >= 1 && n_v <= 256, "n_v must be in [1, 256]");
+        DOS_REQUIRE(M >= 1 && M <= 4096, "M must be in [1, 4096]");
+        cudaStream_t s = (cudaStream_t)stream;
+        DevCSR A = stage_csr(ctx, Adesc, s);
+        DOS_REQUIRE(A.dtype == DOS_F64, "the Lanczos DOS runs in FP64: FP64 values needed");
+        DOS_REQUIRE(M <= A.n, "M must not exceed n");
+        std::vector<int32_t> row0 = {0, (int32_t)A.n}, tb = {0, 1};
+        SegDev seg = upload_segments(ctx, row0, tb, {0.0}, {1.0}, s);
+        validate_on_device(ctx, A, 1, seg.row0, s);
+        const int ld = (n_v + 1) / 2 * 2;
+        const int nb = lanczos_blocks(ctx->num_sms, A.n, ld);
+        // scratch: two vector blocks | partials | alpha, beta [M][ld] | m_used | QL work | out
+        const size_t nvec = (size_t)A.n * ld;
+        const size_t n_dbl = 2 * nvec + (size_t)nb * ld + 2 * (size_t)M * ld +
+                             3 * (size_t)n_v * M + 2 * (size_t)n_v * M + n_v;
+        double *buf = (double *)ctx->lz_buf.get(n_dbl * sizeof(double));
+        double *q0 = buf, *q1 = q0 + nvec, *part = q1 + nvec, *alpha = part + (size_t)nb * ld;
+        double *beta = alpha + (size_t)M * ld, *work = beta + (size_t)M * ld;
+        double *th = work + 3 * (size_t)n_v * M, *wt = th + (size_t)n_v * M;
+        int *mu_dev = (int *)(wt + (size_t)n_v * M);
+        SweepArgs a{};
+        a.precision = DOS_PREC_F64;
+        a.n_rows = A.n;
+        a.n_v = n_v;
+        a.ld = ld;
+        a.B = 1;
+        a.seg_row0 = seg.row0;
+        a.x0 = q0;
+        a.seed = seed;
+        launch_init_vectors(a, s);
+        launch_unit_scale(A.n, ld, n_v, q0, ctx->num_sms, s);
+        DOS_CUDA_TRY(cudaMemsetAsync(q1, 0, nvec * sizeof(double), s));
+        double *cur = q0, *prev = q1;
+        const double *val = (const double *)A.val;
+        for (int j = 0; j < M; ++j) {
+            launch_lanczos_block_spmm(A.n, ld, n_v, A.row_ptr, A.col_idx, val, cur, prev,
+                                      j ? beta + (size_t)(j - 1) * ld : nullptr, part, nb, s);
+            launch_column_sum(part, nb, ld, alpha + (size_t)j * ld, 0, s);
+            launch_lanczos_block_axpy(A.n, ld, n_v, alpha + (size_t)j * ld, cur, prev, part, nb, s);
+            launch_column_sum(part, nb, ld, beta + (size_t)j * ld, 1, s);
+            launch_lanczos_block_scale(A.n, ld, beta + (size_t)j * ld, prev, ctx->num_sms, s);
+            std::swap(cur, prev);
+        }
+        std::vector<double> ha((size_t)M * ld), hb((size_t)M * ld);
+        DOS_CUDA_TRY(cudaMemcpyAsync(ha.data(), alpha, ha.size() * 8, cudaMemcpyDeviceToHost, s));
+        DOS_CUDA_TRY(cudaMemcpyAsync(hb.data(), beta, hb.size() * 8, cudaMemcpyDeviceToHost, s));
+        DOS_CUDA_TRY(cudaStreamSynchronize(s));
+        // invariant subspace per run: beta_j <= 1e-12 * running norm estimate
+        std::vector<int> mus(n_v, M);
+        for (int l = 0; l < n_v; ++l) {
+            double scale = 0.0;
+            for (int j = 0; j < M; ++j) {
+                const double al = ha[(size_t)j * ld + l], be = hb[(size_t)j * ld + l];
+                const double bp = j ? hb[(size_t)(j - 1) * ld + l] : 0.0;
+                DOS_REQUIRE(isfinite(al) && isfinite(be), "Lanczos produced non-finite values");
+                scale = std::max(scale, fabs(al) + be + bp);
+                if (!(be > 1e-12 * scale)) {
+                    mus[l] = j + 1;
+                    break;
+                }
+            }
+        }
+        DOS_CUDA_TRY(cudaMemcpyAsync(mu_dev, mus.data(), n_v * sizeof(int), cudaMemcpyHostToDevice, s));
+        launch_tridiag_ritz(alpha, beta, mu_dev, M, ld, n_v, work, th, wt, s);
+        copy_out(theta, th, (size_t)n_v * M * sizeof(double), s);
+        copy_out(weight, wt, (size_t)n_v * M * sizeof(double), s);
+        DOS_CUDA_TRY(cudaStreamSynchronize(s));
+        if (m_used) memcpy(m_used, mus.data(), n_v * sizeof(int));
+    });
+}
+
+int dos_lanczos_dos(dos_ctx *ctx, const double *theta, const double *weight, int n_v, int M,
+                    double sigma, const double *x, int N_x, double *phi, void *stream) {
+    return guarded(ctx, [&] {
+        DOS_REQUIRE(theta && weight && x && phi, "NULL argument");
+        DOS_REQUIRE(n_v >= 1 && M >= 1 && (int64_t)n_v * M <= (int64_t(1) << 28), "bad n_v / M");
+        DOS_REQUIRE(N_x >= 1 && N_x <= 10000000, "N_x must be in [1, 10^7]");
+        DOS_REQUIRE(isfinite(sigma) && sigma > 0.0, "sigma must be > 0");
+        cudaStream_t s = (cudaStream_t)stream;
+        const size_t np = (size_t)n_v * M;
+        double *buf = (double *)ctx->err_buf.get((2 * np + 2 * (size_t)N_x) * sizeof(double));
+        double *dp = buf, *dw = dp + np, *dx = dw + np, *dphi = dx + N_x;
+        DOS_CUDA_TRY(cudaMemcpyAsync(dp, theta, np * 8, cudaMemcpyDefault, s));
+        DOS_CUDA_TRY(cudaMemcpyAsync(dw, weight, np * 8, cudaMemcpyDefault, s));
+        DOS_CUDA_TRY(cudaMemcpyAsync(dx, x, (size_t)N_x * 8, cudaMemcpyDefault, s));
+        launch_weighted_gauss(dp, dw, (int64_t)np, 1.0 / n_v, sigma, dx, 0.0, 0.0, N_x, dphi, s);
+        copy_out(phi, dphi, (size_t)N_x * 8, s);
+        if (!is_device_ptr(phi)) DOS_CUDA_TRY(cudaStreamSynchronize(s));
+    });
+}
+
+int dos_points_error(dos_ctx *ctx, const double *pts, const double *wts, int64_t n_pts,
+                     double lb, double ub, const double *eig, int64_t n_eig, const double *ref_mu,
+                     int M_ref, int ref_damping, double sigma, int N_x, double *err_l1,
+                     double *err_inf, void *stream) {
+    return guarded(ctx, [&] {
+        DOS_REQUIRE(pts && wts && n_pts >= 1, "points / weights missing");
+        DOS_REQUIRE(isfinite(lb) && isfinite(ub) && ub > lb, "need ub > lb");
+        DOS_REQUIRE(isfinite(sigma) && sigma > 0.0, "sigma must be > 0");
+        DOS_REQUIRE(N_x >= 2 && N_x <= 1000000, "N_x must be in [2, 10^6]");
+        DOS_REQUIRE(eig ? n_eig >= 1 : (ref_mu != nullptr && M_ref >= 0 && M_ref <= 100000),
+                    "need eigenvalues or reference moments");
+        cudaStream_t s = (cudaStream_t)stream;
+        // weights are normalised by their sum on the host
+        std::vector<double> hw((size_t)n_pts);
+        DOS_CUDA_TRY(cudaMemcpyAsync(hw.data(), wts, hw.size() * 8, cudaMemcpyDefault, s));
+        DOS_CUDA_TRY(cudaStreamSynchronize(s));
+        double wsum = 0.0;
+        for (double v : hw) wsum += v;
+        DOS_REQUIRE(wsum > 0.0 && isfinite(wsum), "weights must have a positive finite sum");
+        const double d = 0.5 * (ub - lb);
+        const int Mr = eig ? 0 : M_ref;
+        const int64_t nq64 = std::max<int64_t>(4 * (int64_t)(Mr + 1), (int64_t)ceil(40.0 * d / sigma));
+        const int N_q = (int)std::min<int64_t>(nq64, 1 << 24);
+        const double x0 = lb - 6.0 * sigma, h = (ub - lb + 12.0 * sigma) / (N_x - 1);
+        const size_t n_ref = eig ? 0 : (size_t)M_ref + 1;
+        const size_t neig = eig ? (size_t)n_eig : 0;
+        const size_t nd = 2 * (size_t)n_pts + n_ref + (size_t)(Mr + 1) + 2 * (size_t)N_q +
+                          2 * (size_t)N_x + 2 + neig;
+        double *buf = (double *)ctx->err_buf.get(nd * sizeof(double));
+        double *dp = buf, *dw = dp + n_pts, *dref = dw + n_pts, *poly = dref + n_ref;
+        double *approx = poly + (Mr + 1) + 2 * (size_t)N_q, *ref = approx + N_x, *out = ref + N_x;
+        double *deig = out + 2;
+        DOS_CUDA_TRY(cudaMemcpyAsync(dp, pts, (size_t)n_pts * 8, cudaMemcpyDefault, s));
+        DOS_CUDA_TRY(cudaMemcpyAsync(dw, wts, (size_t)n_pts * 8, cudaMemcpyDefault, s));
+        launch_weighted_gauss(dp, dw, n_pts, 1.0 / wsum, sigma, nullptr, x0, h, N_x, approx, s);
+        if (eig) {
+            DOS_CUDA_TRY(cudaMemcpyAsync(deig, eig, neig * 8, cudaMemcpyDefault, s));
+            launch_blur_eigs(deig, n_eig, sigma, x0, h, N_x, ref, s);
+        } else {
+            DOS_CUDA_TRY(cudaMemcpyAsync(dref, ref_mu, n_ref * 8, cudaMemcpyDefault, s));
+            launch_blur_kpm(dref, M_ref, ref_damping, lb, ub, sigma, N_q, x0, h, N_x, poly, ref, s);
+        }
+        launch_error_norms(approx, ref, N_x, h, out, s);
+        double hv[2];
+        DOS_CUDA_TRY(cudaMemcpyAsync(hv, out, sizeof(hv), cudaMemcpyDeviceToHost, s));
+        DOS_CUDA_TRY(cudaStreamSynchronize(s));
+        if (err_l1) *err_l1 = hv[0];
+        if (err_inf) *err_inf = hv[1];
     });
 }
 

@@ -108,6 +108,8 @@ struct dos_ctx {
     dos::Buffer xbuf, partial, dotsum, tiles, segs, status, mu_dev, mupv_dev;
     // bounds scratch
     dos::Buffer bnd_vec, bnd_part, bnd_out;
+    // Lanczos DOS scratch
+    dos::Buffer lz_buf;
     // reconstruct / error scratch
     dos::Buffer rec_in, rec_out, err_buf;
     dos::PinnedBuffer host_stage;
@@ -238,5 +240,25 @@ void launch_blur_eigs(const double *eig, int64_t n_eig, double sigma, double x0,
 void launch_error_norms(const double *a, const double *b, int N_x, double h, double *out,
                         cudaStream_t s);
 void launch_grid_moments(const double *phi, int N, int M, double *mu, cudaStream_t s);
+
+// Lanczos DOS (block of n_vec independent runs, FP64)
+int lanczos_blocks(int num_sms, int64_t n, int ld);
+void launch_lanczos_block_spmm(int64_t n, int ld, int n_vec, const int32_t *row_ptr,
+                               const int32_t *col_idx, const double *val, const double *q,
+                               double *qprev_w, const double *beta_prev, double *part,
+                               int n_blocks, cudaStream_t s);
+void launch_lanczos_block_axpy(int64_t n, int ld, int n_vec, const double *alpha, const double *q,
+                               double *w, double *part, int n_blocks, cudaStream_t s);
+void launch_column_sum(const double *part, int n_blocks, int ld, double *out, int take_sqrt,
+                       cudaStream_t s);
+void launch_lanczos_block_scale(int64_t n, int ld, const double *beta, double *w, int num_sms,
+                                cudaStream_t s);
+void launch_unit_scale(int64_t n, int ld, int n_vec, double *q, int num_sms, cudaStream_t s);
+// work: 3 * n_vec * M doubles
+void launch_tridiag_ritz(const double *alpha, const double *beta, const int *m_used, int M, int ld,
+                         int n_vec, double *work, double *theta, double *weight, cudaStream_t s);
+void launch_weighted_gauss(const double *pts, const double *w, int64_t n_pts, double scale,
+                           double sigma, const double *x, double x0, double h, int N_x,
+                           double *out, cudaStream_t s);
 
 }  // namespace dos

@@ -1,0 +1,270 @@
+// Lanczos DOS (Section 3.2.1, Eq. landos): n_v independent M-step Lanczos runs
+// advanced together as a block, Ritz values and Gauss weights per run, and the
+// Gaussian-blurred DOS from them.  FP64 throughout.
+//
+// Block layout as in the moment sweep: Q[i*ld + l].  Step j (per vector l):
+//   w = A q_j - beta_{j-1} q_{j-1}          (SpMM pass; w overwrites q_{j-1})
+//   alpha_j = q_j . w                        (per-vector partials, fixed-order reduce)
+//   w -= alpha_j q_j;  beta_j = ||w||        (vector pass + reduce)
+//   q_{j+1} = w / beta_j                     (scale pass, in place)
+// A run whose beta_j falls to 1e-12 times its running norm estimate has reached
+// an invariant subspace; the host keeps its first j+1 coefficients only.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+#include "dos_internal.h"
+
+namespace dos {
+namespace {
+
+constexpr int kThreads = 256;
+
+// One thread per matrix row and vector pair (rows are short); ld = n_v padded to 2.
+__global__ void lanczos_spmm_kernel(int64_t n, int ld, const int32_t *__restrict__ row_ptr,
+                                    const int32_t *__restrict__ col_idx,
+                                    const double *__restrict__ val,
+                                    const double *__restrict__ q,      // q_j
+                                    double *__restrict__ qprev_w,      // q_{j-1} in, w out
+                                    const double *__restrict__ beta_prev,  // [ld] or NULL
+                                    double *__restrict__ part, int n_vec) {
+    // part layout: [blocks][ld]; each block reduces its rows per vector column
+    extern __shared__ double sh[];
+    const int cols = ld;
+    const int rows_per_block = blockDim.x / cols;  // blockDim.x is a multiple of ld
+    const int rloc = threadIdx.x / cols, l = threadIdx.x % cols;
+    double acc = 0.0;
+    for (int64_t i = (int64_t)blockIdx.x * rows_per_block + rloc; i < n;
+         i += (int64_t)gridDim.x * rows_per_block) {
+        double y = 0.0;
+        for (int e = row_ptr[i]; e < row_ptr[i + 1]; ++e) y = fma(val[e], q[(size_t)col_idx[e] * ld + l], y);
+        const size_t o = (size_t)i * ld + l;
+        const double bp = beta_prev ? beta_prev[l] : 0.0;
+        const double w = y - bp * qprev_w[o];
+        qprev_w[o] = w;
+        if (l < n_vec) acc = fma(q[o], w, acc);
+    }
+    sh[threadIdx.x] = acc;
+    __syncthreads();
+    if (threadIdx.x < cols) {
+        double s = 0.0;
+        for (int r = 0; r < rows_per_block; ++r) s += sh[r * cols + threadIdx.x];
+        part[(size_t)blockIdx.x * cols + threadIdx.x] = s;
+    }
+}
+
+// w -= alpha q (per column), partial ||w||^2 per column
+__global__ void lanczos_axpy_kernel(int64_t n, int ld, const double *__restrict__ alpha,
+                                    const double *__restrict__ q, double *__restrict__ w,
+                                    double *__restrict__ part, int n_vec) {
+    extern __shared__ double sh[];
+    const int cols = ld;
+    const int rows_per_block = blockDim.x / cols;
+    const int rloc = threadIdx.x / cols, l = threadIdx.x % cols;
+    const double a = alpha[l];
+    double acc = 0.0;
+    for (int64_t i = (int64_t)blockIdx.x * rows_per_block + rloc; i < n;
+         i += (int64_t)gridDim.x * rows_per_block) {
+        const size_t o = (size_t)i * ld + l;
+        const double v = w[o] - a * q[o];
+        w[o] = v;
+        if (l < n_vec) acc = fma(v, v, acc);
+    }
+    sh[threadIdx.x] = acc;
+    __syncthreads();
+    if (threadIdx.x < cols) {
+        double s = 0.0;
+        for (int r = 0; r < rows_per_block; ++r) s += sh[r * cols + threadIdx.x];
+        part[(size_t)blockIdx.x * cols + threadIdx.x] = s;
+    }
+}
+
+// out[l] = sum over blocks of part[b][l] (fixed order), optionally sqrt
+__global__ void column_sum_kernel(const double *__restrict__ part, int n_blocks, int ld,
+                                  double *__restrict__ out, int take_sqrt) {
+    const int l = blockIdx.x * blockDim.x + threadIdx.x;
+    if (l >= ld) return;
+    double s = 0.0;
+    for (int b = 0; b < n_blocks; ++b) s += part[(size_t)b * ld + l];
+    out[l] = take_sqrt ? sqrt(s) : s;
+}
+
+// q <- w / beta (per column; a zero beta leaves the column at zero)
+__global__ void lanczos_scale_kernel(int64_t n, int ld, const double *__restrict__ beta,
+                                     double *__restrict__ w) {
+    const int64_t total = n * ld;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const double b = beta[t % ld];
+        w[t] = b > 0.0 ? w[t] / b : 0.0;
+    }
+}
+
+// start block: Rademacher vector columns divided by sqrt(n)
+__global__ void unit_scale_kernel(int64_t n, int ld, int n_vec, double *__restrict__ q) {
+    const double inv = 1.0 / sqrt((double)n);
+    const int64_t total = n * ld;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
+         t += (int64_t)gridDim.x * blockDim.x)
+        q[t] = (t % ld) < n_vec ? q[t] * inv : 0.0;
+}
+
+// Golub-Welsch on each run's tridiagonal T (diagonal alpha, off-diagonal beta):
+// implicit QL with Wilkinson-style shifts (the classical tql1/tql2 iteration),
+// applying every plane rotation to the first row of the eigenvector matrix only.
+// One thread per run; work arrays in local memory.
+__global__ void tridiag_ritz_kernel(const double *__restrict__ alpha,
+                                    const double *__restrict__ beta,  // [M][ld], beta[j] = ||f_{j+1}||
+                                    const int *__restrict__ m_used, int M, int ld, int n_vec,
+                                    double *__restrict__ d, double *__restrict__ e,
+                                    double *__restrict__ z, double *__restrict__ theta,
+                                    double *__restrict__ weight) {
+    const int l = blockIdx.x * blockDim.x + threadIdx.x;
+    if (l >= n_vec) return;
+    const int m = m_used[l];
+    double *dd = d + (size_t)l * M, *ee = e + (size_t)l * M, *zz = z + (size_t)l * M;
+    for (int i = 0; i < m; ++i) {
+        dd[i] = alpha[(size_t)i * ld + l];
+        ee[i] = i + 1 < m ? beta[(size_t)i * ld + l] : 0.0;
+        zz[i] = i == 0 ? 1.0 : 0.0;
+    }
+    for (int lo = 0; lo < m; ++lo) {
+        for (int iter = 0; iter < 60; ++iter) {
+            int mm = lo;
+            for (; mm < m - 1; ++mm) {
+                const double dsum = fabs(dd[mm]) + fabs(dd[mm + 1]);
+                if (fabs(ee[mm]) <= 2.2e-16 * dsum) break;
+            }
+            if (mm == lo) break;
+            double g = (dd[lo + 1] - dd[lo]) / (2.0 * ee[lo]);
+            double r = hypot(g, 1.0);
+            g = dd[mm] - dd[lo] + ee[lo] / (g + (g >= 0.0 ? fabs(r) : -fabs(r)));
+            double s = 1.0, c = 1.0, p = 0.0;
+            int i = mm - 1;
+            bool underflow = false;
+            for (; i >= lo; --i) {
+                const double f = s * ee[i], b = c * ee[i];
+                r = hypot(f, g);
+                ee[i + 1] = r;
+                if (r == 0.0) {
+                    dd[i + 1] -= p;
+                    ee[mm] = 0.0;
+                    underflow = true;
+                    break;
+                }
+                s = f / r;
+                c = g / r;
+                g = dd[i + 1] - p;
+                r = (dd[i] - g) * s + 2.0 * c * b;
+                p = s * r;
+                dd[i + 1] = g + p;
+                g = c * r - b;
+                const double zf = zz[i + 1];
+                zz[i + 1] = s * zz[i] + c * zf;
+                zz[i] = c * zz[i] - s * zf;
+            }
+            if (underflow) continue;
+            dd[lo] -= p;
+            ee[lo] = g;
+            ee[mm] = 0.0;
+        }
+    }
+    for (int i = 0; i < M; ++i) {
+        theta[(size_t)l * M + i] = i < m ? dd[i] : 0.0;
+        weight[(size_t)l * M + i] = i < m ? zz[i] * zz[i] : 0.0;
+    }
+}
+
+// phi(x_i) = (1/n_vec) sum_{l,k} weight[l,k] g_sigma(x_i - theta[l,k]); one block per point.
+__global__ void weighted_gauss_kernel(const double *__restrict__ pts, const double *__restrict__ w,
+                                      int64_t n_pts, double scale, double sigma,
+                                      const double *__restrict__ x, double x0, double h, int N_x,
+                                      double *__restrict__ out) {
+    __shared__ double sh[32];
+    const double inv_s = 1.0 / sigma, norm = 1.0 / sqrt(2.0 * M_PI * sigma * sigma);
+    for (int m = blockIdx.x; m < N_x; m += gridDim.x) {
+        const double xm = x ? x[m] : x0 + m * h;
+        double s = 0.0;
+        for (int64_t j = threadIdx.x; j < n_pts; j += blockDim.x) {
+            const double z = (xm - pts[j]) * inv_s;
+            if (fabs(z) < 38.7) s += w[j] * norm * exp(-0.5 * z * z);
+        }
+        for (int off = 16; off > 0; off >>= 1) s += __shfl_down_sync(0xffffffffu, s, off);
+        if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = s;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double t = 0.0;
+            for (int q = 0; q < (int)(blockDim.x >> 5); ++q) t += sh[q];
+            out[m] = t * scale;
+        }
+        __syncthreads();
+    }
+}
+
+int block_threads_for(int ld) { return (kThreads / ld) * ld; }  // ld <= 256
+
+}  // namespace
+
+int lanczos_blocks(int num_sms, int64_t n, int ld) {
+    const int bt = block_threads_for(ld);
+    const int rows = bt / ld;
+    int64_t b = (n + rows - 1) / rows;
+    const int64_t cap = (int64_t)num_sms * 8;
+    return (int)std::max<int64_t>(1, std::min(b, cap));
+}
+
+void launch_lanczos_block_spmm(int64_t n, int ld, int n_vec, const int32_t *row_ptr,
+                               const int32_t *col_idx, const double *val, const double *q,
+                               double *qprev_w, const double *beta_prev, double *part,
+                               int n_blocks, cudaStream_t s) {
+    const int bt = block_threads_for(ld);
+    lanczos_spmm_kernel<<<n_blocks, bt, bt * sizeof(double), s>>>(n, ld, row_ptr, col_idx, val, q,
+                                                                   qprev_w, beta_prev, part, n_vec);
+    DOS_LAUNCHED();
+}
+
+void launch_lanczos_block_axpy(int64_t n, int ld, int n_vec, const double *alpha, const double *q,
+                               double *w, double *part, int n_blocks, cudaStream_t s) {
+    const int bt = block_threads_for(ld);
+    lanczos_axpy_kernel<<<n_blocks, bt, bt * sizeof(double), s>>>(n, ld, alpha, q, w, part, n_vec);
+    DOS_LAUNCHED();
+}
+
+void launch_column_sum(const double *part, int n_blocks, int ld, double *out, int take_sqrt,
+                       cudaStream_t s) {
+    column_sum_kernel<<<(ld + 127) / 128, 128, 0, s>>>(part, n_blocks, ld, out, take_sqrt);
+    DOS_LAUNCHED();
+}
+
+void launch_lanczos_block_scale(int64_t n, int ld, const double *beta, double *w, int num_sms,
+                                cudaStream_t s) {
+    int64_t g = (n * ld + kThreads - 1) / kThreads;
+    if (g > (int64_t)num_sms * 16) g = (int64_t)num_sms * 16;
+    lanczos_scale_kernel<<<(int)std::max<int64_t>(g, 1), kThreads, 0, s>>>(n, ld, beta, w);
+    DOS_LAUNCHED();
+}
+
+void launch_unit_scale(int64_t n, int ld, int n_vec, double *q, int num_sms, cudaStream_t s) {
+    int64_t g = (n * ld + kThreads - 1) / kThreads;
+    if (g > (int64_t)num_sms * 16) g = (int64_t)num_sms * 16;
+    unit_scale_kernel<<<(int)std::max<int64_t>(g, 1), kThreads, 0, s>>>(n, ld, n_vec, q);
+    DOS_LAUNCHED();
+}
+
+void launch_tridiag_ritz(const double *alpha, const double *beta, const int *m_used, int M, int ld,
+                         int n_vec, double *work, double *theta, double *weight, cudaStream_t s) {
+    double *d = work, *e = work + (size_t)n_vec * M, *z = work + 2 * (size_t)n_vec * M;
+    tridiag_ritz_kernel<<<(n_vec + 63) / 64, 64, 0, s>>>(alpha, beta, m_used, M, ld, n_vec, d, e, z,
+                                                         theta, weight);
+    DOS_LAUNCHED();
+}
+
+void launch_weighted_gauss(const double *pts, const double *w, int64_t n_pts, double scale,
+                           double sigma, const double *x, double x0, double h, int N_x,
+                           double *out, cudaStream_t s) {
+    weighted_gauss_kernel<<<N_x < 65535 ? N_x : 65535, 256, 0, s>>>(pts, w, n_pts, scale, sigma, x,
+                                                                    x0, h, N_x, out);
+    DOS_LAUNCHED();
+}
+
+}  // namespace dos

@@ -77,6 +77,10 @@ _SIGS = {
     "dos_smoothed_error": (_i, [_vp, _vp, _i, _i, _d, _d, _vp, _i64, _vp, _i, _i, _d, _i, _dp,
                                 _dp, _vp]),
     "dos_moments_from_grid": (_i, [_vp, _vp, _i, _i, _vp, _vp]),
+    "dos_lanczos_ritz": (_i, [_vp, C.POINTER(dos_csr), _i, _i, _u64, _vp, _vp, _vp, _vp]),
+    "dos_lanczos_dos": (_i, [_vp, _vp, _vp, _i, _i, _d, _vp, _i, _vp, _vp]),
+    "dos_points_error": (_i, [_vp, _vp, _vp, _i64, _d, _d, _vp, _i64, _vp, _i, _i, _d, _i, _dp,
+                              _dp, _vp]),
 }
 _SIGS.update({
     "dos_mlp_create": (_i, [_vp, _i, _i, _i, _u64, C.POINTER(_vp)]),
@@ -313,6 +317,43 @@ class Context:
         self._check(_lib.dos_reconstruct(self._h, pmu, int(M), damp, float(lb), float(ub), pt,
                                          int(N_t), po, pl, _stream_of(mu, out)))
         return (out, outl) if want_lambda or phi_lambda is not None else out
+
+    def dos_lanczos_ritz(self, A: CSRArrays, M: int, n_v: int, seed: int):
+        """(theta, weight, m_used): Ritz values / weights per run, shape (n_v, M)."""
+        theta = np.empty((n_v, M))
+        weight = np.empty((n_v, M))
+        m_used = np.empty(n_v, dtype=np.int32)
+        self._check(_lib.dos_lanczos_ritz(self._h, C.byref(A.desc), int(M), int(n_v), int(seed),
+                                          theta.ctypes.data, weight.ctypes.data,
+                                          m_used.ctypes.data, _stream_of(A.row_ptr)))
+        return theta, weight, m_used
+
+    def dos_lanczos_dos(self, theta, weight, sigma: float, x):
+        n_v, M = theta.shape
+        out = np.empty(x.shape[0])
+        th = np.ascontiguousarray(theta, dtype=np.float64)
+        wt = np.ascontiguousarray(weight, dtype=np.float64)
+        xx = np.ascontiguousarray(x, dtype=np.float64)
+        self._check(_lib.dos_lanczos_dos(self._h, th.ctypes.data, wt.ctypes.data, int(n_v), int(M),
+                                         float(sigma), xx.ctypes.data, int(xx.shape[0]),
+                                         out.ctypes.data, C.c_void_p(0)))
+        return out
+
+    def dos_points_error(self, pts, wts, lb: float, ub: float, sigma: float, eig=None,
+                         ref_mu=None, ref_damping="jackson", N_x: int = 4000):
+        p = np.ascontiguousarray(pts, dtype=np.float64).ravel()
+        w = np.ascontiguousarray(wts, dtype=np.float64).ravel()
+        pe, _, k1 = _ptr(eig)
+        pr, _, k2 = _ptr(ref_mu)
+        n_eig = 0 if eig is None else int(eig.shape[0])
+        M_ref = -1 if ref_mu is None else int(ref_mu.shape[0]) - 1
+        rdamp = DAMPINGS[ref_damping] if isinstance(ref_damping, str) else int(ref_damping)
+        e1, einf = C.c_double(), C.c_double()
+        self._check(_lib.dos_points_error(self._h, p.ctypes.data, w.ctypes.data, int(p.shape[0]),
+                                          float(lb), float(ub), pe, n_eig, pr, M_ref, rdamp,
+                                          float(sigma), int(N_x), C.byref(e1), C.byref(einf),
+                                          C.c_void_p(0)))
+        return e1.value, einf.value
 
     def dos_moments_from_grid(self, phi_hat, M_out: int, mu=None):
         """Moments mu_0..mu_M_out of a DOS given at the Chebyshev nodes."""
