@@ -389,6 +389,25 @@ int dos_points_error(dos_ctx *ctx, const double *pts, const double *wts, int64_t
                      int M_ref, int ref_damping, double sigma, int N_x, double *err_l1,
                      double *err_inf, void *stream);
 
+/* ---- an observable: the heat capacity (Section 4.3) ------------------------ */
+/*
+ * <phi, g_beta> for each beta in betas (n_beta values, host or device) with the
+ * heat-capacity kernel of Eq. gfunc up to its constant factor,
+ *     g_beta(lambda) = x^2 e^{-x} / (1 - e^{-x})^2,  x = beta sqrt(max(lambda, 0))
+ * (beta = hbar c / (k_B T); the paper normalises C_v to a maximum of one, so
+ * constants do not matter; g -> 1 as x -> 0).  The density is either
+ *   - KPM moments mu (M+1, host or device, normalised as dos_kpm_moments) with
+ *     damping, integrated by Gauss-Chebyshev quadrature on max(4(M+1), 2048)
+ *     nodes of [lb, ub]: (1/N_q) sum_i P(t_i) g(c + d t_i); pts must be NULL;
+ *   - or weighted points (Ritz values and weights of dos_lanczos_ritz, or exact
+ *     eigenvalues with equal weights): sum_j w_j g(p_j) / sum_j w_j; mu NULL.
+ * The error of an estimate is Eq. errormetric_g: |<phi,g> - <phi_tilde,g>|.
+ * cv: n_beta doubles (host or device).  Synchronises `stream`.
+ */
+int dos_heat_capacity(dos_ctx *ctx, const double *mu, int M, int damping, double lb, double ub,
+                      const double *pts, const double *wts, int64_t n_pts, const double *betas,
+                      int n_beta, double *cv, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -1155,6 +1155,47 @@ int dos_points_error(dos_ctx *ctx, const double *pts, const double *wts, int64_t
     });
 }
 
+int dos_heat_capacity(dos_ctx *ctx, const double *mu, int M, int damping, double lb, double ub,
+                      const double *pts, const double *wts, int64_t n_pts, const double *betas,
+                      int n_beta, double *cv, void *stream) {
+    return guarded(ctx, [&] {
+        DOS_REQUIRE(betas && cv && n_beta >= 1 && n_beta <= (1 << 20), "betas / cv / n_beta");
+        DOS_REQUIRE((mu != nullptr) != (pts != nullptr), "give either moments or points");
+        cudaStream_t s = (cudaStream_t)stream;
+        if (mu) {
+            DOS_REQUIRE(M >= 0 && M <= 100000, "M must be in [0, 100000]");
+            DOS_REQUIRE(isfinite(lb) && isfinite(ub) && ub > lb, "need ub > lb");
+            DOS_REQUIRE(damping == DOS_DAMP_NONE || damping == DOS_DAMP_JACKSON, "bad damping");
+            const int N_q = std::max(4 * (M + 1), 2048);
+            const size_t nd = (size_t)(M + 1) + (M + 1) + 2 * (size_t)N_q + 2 * (size_t)n_beta;
+            double *buf = (double *)ctx->err_buf.get(nd * sizeof(double));
+            double *dmu = buf, *scr = dmu + (M + 1), *db = scr + (M + 1) + 2 * (size_t)N_q;
+            double *dout = db + n_beta;
+            DOS_CUDA_TRY(cudaMemcpyAsync(dmu, mu, (M + 1) * 8, cudaMemcpyDefault, s));
+            DOS_CUDA_TRY(cudaMemcpyAsync(db, betas, n_beta * 8, cudaMemcpyDefault, s));
+            launch_heat_kpm(dmu, M, damping, lb, ub, N_q, db, n_beta, scr, dout, s);
+            copy_out(cv, dout, n_beta * 8, s);
+        } else {
+            DOS_REQUIRE(wts && n_pts >= 1, "weights / n_pts");
+            std::vector<double> hw((size_t)n_pts);
+            DOS_CUDA_TRY(cudaMemcpyAsync(hw.data(), wts, hw.size() * 8, cudaMemcpyDefault, s));
+            DOS_CUDA_TRY(cudaStreamSynchronize(s));
+            double wsum = 0.0;
+            for (double v : hw) wsum += v;
+            DOS_REQUIRE(wsum > 0.0 && isfinite(wsum), "weights must have a positive finite sum");
+            const size_t nd = 2 * (size_t)n_pts + 2 * (size_t)n_beta;
+            double *buf = (double *)ctx->err_buf.get(nd * sizeof(double));
+            double *dp = buf, *dw = dp + n_pts, *db = dw + n_pts, *dout = db + n_beta;
+            DOS_CUDA_TRY(cudaMemcpyAsync(dp, pts, (size_t)n_pts * 8, cudaMemcpyDefault, s));
+            DOS_CUDA_TRY(cudaMemcpyAsync(dw, wts, (size_t)n_pts * 8, cudaMemcpyDefault, s));
+            DOS_CUDA_TRY(cudaMemcpyAsync(db, betas, n_beta * 8, cudaMemcpyDefault, s));
+            launch_heat_points(dp, dw, n_pts, 1.0 / wsum, db, n_beta, dout, s);
+            copy_out(cv, dout, n_beta * 8, s);
+        }
+        DOS_CUDA_TRY(cudaStreamSynchronize(s));
+    });
+}
+
 int dos_moments_from_grid(dos_ctx *ctx, const double *phi_hat, int N_t, int M_out, double *mu,
                           void *stream) {
     return guarded(ctx, [&] {

@@ -240,6 +240,11 @@ void launch_blur_eigs(const double *eig, int64_t n_eig, double sigma, double x0,
 void launch_error_norms(const double *a, const double *b, int N_x, double h, double *out,
                         cudaStream_t s);
 void launch_grid_moments(const double *phi, int N, int M, double *mu, cudaStream_t s);
+void launch_heat_kpm(const double *mu, int M, int damping, double lb, double ub, int N_q,
+                     const double *betas, int n_beta, double *scratch, double *out,
+                     cudaStream_t s);
+void launch_heat_points(const double *pts, const double *w, int64_t n_pts, double scale,
+                        const double *betas, int n_beta, double *out, cudaStream_t s);
 
 // Lanczos DOS (block of n_vec independent runs, FP64)
 int lanczos_blocks(int num_sms, int64_t n, int ld);

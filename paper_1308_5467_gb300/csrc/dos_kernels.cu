@@ -146,6 +146,29 @@ __global__ void grid_moments_kernel(const double *__restrict__ phi, int N, int M
     }
 }
 
+// Heat-capacity kernel of Eq. gfunc up to its constant factor:
+// g(lambda) = x^2 e^{-x} / (1 - e^{-x})^2 with x = beta sqrt(max(lambda, 0)); g -> 1 as x -> 0.
+__device__ __forceinline__ double heat_kernel(double lambda, double beta) {
+    const double x = beta * sqrt(fmax(lambda, 0.0));
+    if (x < 1e-6) return 1.0 - x * x / 12.0;
+    const double em = exp(-x);
+    const double den = -expm1(-x);  // 1 - e^{-x}
+    return x * x * em / (den * den);
+}
+
+// out[b] = sum_j w_j g(p_j; beta_b) * scale; one block per beta, fixed-order sums.
+__global__ void heat_points_kernel(const double *__restrict__ pts, const double *__restrict__ w,
+                                   int64_t n_pts, double scale, const double *__restrict__ betas,
+                                   int n_beta, double *__restrict__ out) {
+    for (int b = blockIdx.x; b < n_beta; b += gridDim.x) {
+        const double beta = betas[b];
+        double s = 0.0;
+        for (int64_t j = threadIdx.x; j < n_pts; j += blockDim.x) s += w[j] * heat_kernel(pts[j], beta);
+        s = block_sum_d(s);
+        if (threadIdx.x == 0) out[b] = s * scale;
+    }
+}
+
 int grid_cap(int64_t work, int block, int cap) {
     int64_t g = (work + block - 1) / block;
     return (int)(g < 1 ? 1 : (g > cap ? cap : g));
@@ -181,6 +204,29 @@ void launch_blur_eigs(const double *eig, int64_t n_eig, double sigma, double x0,
                       int N_x, double *out, cudaStream_t s) {
     blur_eigs_kernel<<<N_x < 65535 ? N_x : 65535, 256, 0, s>>>(eig, n_eig, sigma, x0, h, N_x,
                                                                 out);
+    DOS_LAUNCHED();
+}
+
+// KPM: P(t_i) at N_q Gauss-Chebyshev nodes (positions Y) then the quadrature
+// (1/N_q) sum_i P(t_i) g(Y_i); scratch: (M+1) + 2 N_q doubles.
+void launch_heat_kpm(const double *mu, int M, int damping, double lb, double ub, int N_q,
+                     const double *betas, int n_beta, double *scratch, double *out,
+                     cudaStream_t s) {
+    double *a = scratch, *P = scratch + (M + 1), *Y = P + N_q;
+    coef_kernel<<<grid_cap(M + 1, 256, 1024), 256, 0, s>>>(mu, M, damping, a);
+    DOS_LAUNCHED();
+    nodes_kernel<<<grid_cap(N_q, 256, 4096), 256, 0, s>>>(a, M, N_q, 0.5 * (lb + ub),
+                                                          0.5 * (ub - lb), P, Y);
+    DOS_LAUNCHED();
+    heat_points_kernel<<<n_beta < 65535 ? n_beta : 65535, 256, 0, s>>>(Y, P, N_q, 1.0 / N_q,
+                                                                      betas, n_beta, out);
+    DOS_LAUNCHED();
+}
+
+void launch_heat_points(const double *pts, const double *w, int64_t n_pts, double scale,
+                        const double *betas, int n_beta, double *out, cudaStream_t s) {
+    heat_points_kernel<<<n_beta < 65535 ? n_beta : 65535, 256, 0, s>>>(pts, w, n_pts, scale, betas,
+                                                                      n_beta, out);
     DOS_LAUNCHED();
 }
 

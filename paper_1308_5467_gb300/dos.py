@@ -77,6 +77,7 @@ _SIGS = {
     "dos_smoothed_error": (_i, [_vp, _vp, _i, _i, _d, _d, _vp, _i64, _vp, _i, _i, _d, _i, _dp,
                                 _dp, _vp]),
     "dos_moments_from_grid": (_i, [_vp, _vp, _i, _i, _vp, _vp]),
+    "dos_heat_capacity": (_i, [_vp, _vp, _i, _i, _d, _d, _vp, _vp, _i64, _vp, _i, _vp, _vp]),
     "dos_lanczos_ritz": (_i, [_vp, C.POINTER(dos_csr), _i, _i, _u64, _vp, _vp, _vp, _vp]),
     "dos_lanczos_dos": (_i, [_vp, _vp, _vp, _i, _i, _d, _vp, _i, _vp, _vp]),
     "dos_points_error": (_i, [_vp, _vp, _vp, _i64, _d, _d, _vp, _i64, _vp, _i, _i, _d, _i, _dp,
@@ -354,6 +355,27 @@ class Context:
                                           float(sigma), int(N_x), C.byref(e1), C.byref(einf),
                                           C.c_void_p(0)))
         return e1.value, einf.value
+
+    def dos_heat_capacity(self, betas, mu=None, M=None, damping="jackson", lb=-1.0, ub=1.0,
+                          pts=None, wts=None):
+        """<phi, g_beta> for each beta, from KPM moments or from weighted points."""
+        b = np.ascontiguousarray(betas, dtype=np.float64)
+        out = np.empty(b.shape[0])
+        damp = DAMPINGS[damping] if isinstance(damping, str) else int(damping)
+        if mu is not None:
+            m = np.ascontiguousarray(mu, dtype=np.float64)
+            self._check(_lib.dos_heat_capacity(self._h, m.ctypes.data,
+                                               int(M if M is not None else m.shape[0] - 1), damp,
+                                               float(lb), float(ub), None, None, 0,
+                                               b.ctypes.data, int(b.shape[0]), out.ctypes.data,
+                                               C.c_void_p(0)))
+        else:
+            p = np.ascontiguousarray(pts, dtype=np.float64).ravel()
+            w = np.ascontiguousarray(wts, dtype=np.float64).ravel()
+            self._check(_lib.dos_heat_capacity(self._h, None, 0, damp, 0.0, 1.0, p.ctypes.data,
+                                               w.ctypes.data, int(p.shape[0]), b.ctypes.data,
+                                               int(b.shape[0]), out.ctypes.data, C.c_void_p(0)))
+        return out
 
     def dos_moments_from_grid(self, phi_hat, M_out: int, mu=None):
         """Moments mu_0..mu_M_out of a DOS given at the Chebyshev nodes."""
