@@ -377,6 +377,18 @@ int dos_lanczos_dos(dos_ctx *ctx, const double *theta, const double *weight, int
                     double sigma, const double *x, int N_x, double *phi, void *stream);
 
 /*
+ * Haydock's method (Section 3.2.2): the Lorentzian-blurred DOS
+ *   phi_eta(x) = (1/n_v) sum_l sum_k weight[l*M+k] (eta/pi) / ((x - theta[l*M+k])^2 + eta^2),
+ * which is -(1/pi) Im of the runs' M-step continued fraction
+ * e_1^T ((x + i eta) I - T_M)^{-1} e_1 averaged over the runs, written through the
+ * Ritz pairs of dos_lanczos_ritz (unit start vectors: no extra 1/n; the 1/pi
+ * normalises the Lorentzian).  x: N_x points (host or device); phi: N_x doubles,
+ * host or device.  Synchronises `stream` when phi is host memory.
+ */
+int dos_haydock_dos(dos_ctx *ctx, const double *theta, const double *weight, int n_v, int M,
+                    double eta, const double *x, int N_x, double *phi, void *stream);
+
+/*
  * dos_smoothed_error for an approximation given as weighted points (e.g. the
  * Ritz values and weights of dos_lanczos_ritz): the approximate density is
  * sum_j w_j g_sigma(x - p_j) / sum_j w_j, blurred by nothing further (the

@@ -63,6 +63,24 @@ def lanczos_ritz(A, M: int, n_v: int, seed: int, batch_index: int = 0, vec_offse
     return out
 
 
+def haydock_dos(A, M: int, n_v: int, seed: int, eta: float, x: np.ndarray, **kw) -> np.ndarray:
+    """Haydock's method (Section 3.2.2): -(1/pi) Im of the continued fraction
+    e_1^T ((x + i eta) - T_M)^{-1} e_1, evaluated from the bottom up
+    (G_{m+1} = 0, G_j = 1 / (z - alpha_j - beta_j^2 G_{j+1})), averaged over the
+    unit start vectors."""
+    V = kpm.start_block(A.n, n_v, seed, kw.get("batch_index", 0), kw.get("vec_offset", 0))
+    z = np.asarray(x, dtype=np.float64) + 1j * eta
+    acc = np.zeros(z.shape[0])
+    for l in range(n_v):
+        a, b = lanczos_run(A, V[:, l], M)
+        G = np.zeros_like(z)
+        for j in range(len(a) - 1, -1, -1):
+            b2 = b[j] ** 2 if j < len(a) - 1 else 0.0
+            G = 1.0 / (z - a[j] - b2 * G)
+        acc += -G.imag / np.pi
+    return acc / n_v
+
+
 def lanczos_dos(A, M: int, n_v: int, seed: int, sigma: float, x: np.ndarray, **kw) -> np.ndarray:
     """Eq. landos on the points x."""
     acc = np.zeros_like(np.asarray(x, dtype=np.float64))

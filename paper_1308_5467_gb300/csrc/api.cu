@@ -1104,6 +1104,26 @@ int dos_lanczos_dos(dos_ctx *ctx, const double *theta, const double *weight, int
     });
 }
 
+int dos_haydock_dos(dos_ctx *ctx, const double *theta, const double *weight, int n_v, int M,
+                    double eta, const double *x, int N_x, double *phi, void *stream) {
+    return guarded(ctx, [&] {
+        DOS_REQUIRE(theta && weight && x && phi, "NULL argument");
+        DOS_REQUIRE(n_v >= 1 && M >= 1 && (int64_t)n_v * M <= (int64_t(1) << 28), "bad n_v / M");
+        DOS_REQUIRE(N_x >= 1 && N_x <= 10000000, "N_x must be in [1, 10^7]");
+        DOS_REQUIRE(isfinite(eta) && eta > 0.0, "eta must be > 0");
+        cudaStream_t s = (cudaStream_t)stream;
+        const size_t np = (size_t)n_v * M;
+        double *buf = (double *)ctx->err_buf.get((2 * np + 2 * (size_t)N_x) * sizeof(double));
+        double *dp = buf, *dw = dp + np, *dx = dw + np, *dphi = dx + N_x;
+        DOS_CUDA_TRY(cudaMemcpyAsync(dp, theta, np * 8, cudaMemcpyDefault, s));
+        DOS_CUDA_TRY(cudaMemcpyAsync(dw, weight, np * 8, cudaMemcpyDefault, s));
+        DOS_CUDA_TRY(cudaMemcpyAsync(dx, x, (size_t)N_x * 8, cudaMemcpyDefault, s));
+        launch_weighted_lorentz(dp, dw, (int64_t)np, 1.0 / n_v, eta, dx, N_x, dphi, s);
+        copy_out(phi, dphi, (size_t)N_x * 8, s);
+        if (!is_device_ptr(phi)) DOS_CUDA_TRY(cudaStreamSynchronize(s));
+    });
+}
+
 int dos_points_error(dos_ctx *ctx, const double *pts, const double *wts, int64_t n_pts,
                      double lb, double ub, const double *eig, int64_t n_eig, const double *ref_mu,
                      int M_ref, int ref_damping, double sigma, int N_x, double *err_l1,

@@ -265,5 +265,7 @@ void launch_tridiag_ritz(const double *alpha, const double *beta, const int *m_u
 void launch_weighted_gauss(const double *pts, const double *w, int64_t n_pts, double scale,
                            double sigma, const double *x, double x0, double h, int N_x,
                            double *out, cudaStream_t s);
+void launch_weighted_lorentz(const double *pts, const double *w, int64_t n_pts, double scale,
+                             double eta, const double *x, int N_x, double *out, cudaStream_t s);
 
 }  // namespace dos

@@ -201,6 +201,34 @@ __global__ void weighted_gauss_kernel(const double *__restrict__ pts, const doub
     }
 }
 
+// Haydock (Section 3.2.2): phi(x) = scale * sum w (eta/pi) / ((x - theta)^2 + eta^2),
+// the imaginary part of the M-step continued fraction e_1^T (z - T)^{-1} e_1 at
+// z = x + i eta written through the Ritz pairs.
+__global__ void weighted_lorentz_kernel(const double *__restrict__ pts,
+                                        const double *__restrict__ w, int64_t n_pts, double scale,
+                                        double eta, const double *__restrict__ x, int N_x,
+                                        double *__restrict__ out) {
+    __shared__ double sh[32];
+    const double c = eta / M_PI, e2 = eta * eta;
+    for (int m = blockIdx.x; m < N_x; m += gridDim.x) {
+        const double xm = x[m];
+        double s = 0.0;
+        for (int64_t j = threadIdx.x; j < n_pts; j += blockDim.x) {
+            const double u = xm - pts[j];
+            s += w[j] * c / (u * u + e2);
+        }
+        for (int off = 16; off > 0; off >>= 1) s += __shfl_down_sync(0xffffffffu, s, off);
+        if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = s;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double t = 0.0;
+            for (int q = 0; q < (int)(blockDim.x >> 5); ++q) t += sh[q];
+            out[m] = t * scale;
+        }
+        __syncthreads();
+    }
+}
+
 int block_threads_for(int ld) { return (kThreads / ld) * ld; }  // ld <= 256
 
 }  // namespace
@@ -256,6 +284,13 @@ void launch_tridiag_ritz(const double *alpha, const double *beta, const int *m_u
     double *d = work, *e = work + (size_t)n_vec * M, *z = work + 2 * (size_t)n_vec * M;
     tridiag_ritz_kernel<<<(n_vec + 63) / 64, 64, 0, s>>>(alpha, beta, m_used, M, ld, n_vec, d, e, z,
                                                          theta, weight);
+    DOS_LAUNCHED();
+}
+
+void launch_weighted_lorentz(const double *pts, const double *w, int64_t n_pts, double scale,
+                             double eta, const double *x, int N_x, double *out, cudaStream_t s) {
+    weighted_lorentz_kernel<<<N_x < 65535 ? N_x : 65535, 256, 0, s>>>(pts, w, n_pts, scale, eta, x,
+                                                                      N_x, out);
     DOS_LAUNCHED();
 }
 

@@ -80,6 +80,7 @@ _SIGS = {
     "dos_heat_capacity": (_i, [_vp, _vp, _i, _i, _d, _d, _vp, _vp, _i64, _vp, _i, _vp, _vp]),
     "dos_lanczos_ritz": (_i, [_vp, C.POINTER(dos_csr), _i, _i, _u64, _vp, _vp, _vp, _vp]),
     "dos_lanczos_dos": (_i, [_vp, _vp, _vp, _i, _i, _d, _vp, _i, _vp, _vp]),
+    "dos_haydock_dos": (_i, [_vp, _vp, _vp, _i, _i, _d, _vp, _i, _vp, _vp]),
     "dos_points_error": (_i, [_vp, _vp, _vp, _i64, _d, _d, _vp, _i64, _vp, _i, _i, _d, _i, _dp,
                               _dp, _vp]),
 }
@@ -337,6 +338,17 @@ class Context:
         xx = np.ascontiguousarray(x, dtype=np.float64)
         self._check(_lib.dos_lanczos_dos(self._h, th.ctypes.data, wt.ctypes.data, int(n_v), int(M),
                                          float(sigma), xx.ctypes.data, int(xx.shape[0]),
+                                         out.ctypes.data, C.c_void_p(0)))
+        return out
+
+    def dos_haydock_dos(self, theta, weight, eta: float, x):
+        n_v, M = theta.shape
+        out = np.empty(x.shape[0])
+        th = np.ascontiguousarray(theta, dtype=np.float64)
+        wt = np.ascontiguousarray(weight, dtype=np.float64)
+        xx = np.ascontiguousarray(x, dtype=np.float64)
+        self._check(_lib.dos_haydock_dos(self._h, th.ctypes.data, wt.ctypes.data, int(n_v), int(M),
+                                         float(eta), xx.ctypes.data, int(xx.shape[0]),
                                          out.ctypes.data, C.c_void_p(0)))
         return out
 

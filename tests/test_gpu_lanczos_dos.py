@@ -66,6 +66,15 @@ def test_invariant_subspace_and_dos(ctx):
     assert np.abs(phi - ref).max() < 1e-10
 
 
+def test_haydock_matches_continued_fraction(ctx):
+    A = anderson_3d(10, 6.0, seed=4)
+    theta, weight, _ = ctx.dos_lanczos_ritz(dev(A), 30, 6, seed=3)
+    x = np.linspace(-10, 10, 777)
+    phi = ctx.dos_haydock_dos(theta, weight, 0.15, x)
+    ref = old.haydock_dos(A, 30, 6, seed=3, eta=0.15, x=x)
+    assert np.abs(phi - ref).max() < 1e-8 * np.abs(ref).max()
+
+
 def test_points_error_matches_oracle(ctx):
     A = laplacian_2d(30)
     lam = np.linalg.eigvalsh(A.to_dense())

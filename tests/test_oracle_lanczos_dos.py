@@ -38,6 +38,20 @@ def test_few_distinct_values_resolved_exactly():
     assert np.abs(phi - exact).max() < 1e-10
 
 
+def test_haydock_continued_fraction_full_run_is_lorentzian_of_spectrum():
+    # With M = n the continued fraction is the exact resolvent entry, so the
+    # Haydock DOS is the Lorentzian-blurred spectral measure of the vector.
+    A = laplacian_2d(6)
+    x = np.linspace(-1, 9, 401)
+    eta = 0.25
+    phi = old.haydock_dos(A, A.n, 1, seed=7, eta=eta, x=x)
+    lam, U = np.linalg.eigh(A.to_dense())
+    v = okpm.start_block(A.n, 1, seed=7)[:, 0]
+    w = (U.T @ v) ** 2 / A.n
+    ref = (w[None, :] * (eta / np.pi) / ((x[:, None] - lam[None, :]) ** 2 + eta ** 2)).sum(axis=1)
+    assert np.abs(phi - ref).max() < 1e-9
+
+
 def test_full_run_equals_blurred_exact_dos():
     A = laplacian_2d(6)                      # n = 36, distinct eigenvalues up to symmetry
     lam = np.linalg.eigvalsh(A.to_dense())
