@@ -66,6 +66,9 @@ def start_block(n: int, n_v: int, seed: int, batch_index: int = 0, vec_offset: i
     return out
 
 
+_MODES = {"direct": 0, "doubling": 1, "legendre": 2}
+
+
 def kpm_moments_per_vector(A, lb: float, ub: float, M: int, n_v: int, seed: int, *,
                            mode: str = "doubling", batch_index: int = 0, vec_offset: int = 0,
                            reverse: bool = False, nthreads: int = 0) -> np.ndarray:
@@ -74,7 +77,7 @@ def kpm_moments_per_vector(A, lb: float, ub: float, M: int, n_v: int, seed: int,
     out = np.empty((n_v, M + 1), dtype=np.float64)
     rc = lib().oracle_kpm_moments(A.n, rp.ctypes.data, ci.ctypes.data, va.ctypes.data,
                                   float(lb), float(ub), int(M), int(n_v), int(vec_offset),
-                                  int(seed), int(batch_index), 0 if mode == "direct" else 1,
+                                  int(seed), int(batch_index), _MODES[mode],
                                   1 if reverse else 0, int(nthreads), out.ctypes.data)
     if rc != 0:
         raise ValueError("oracle_kpm_moments rejected its arguments")

@@ -20,6 +20,8 @@
  *    v_0^T T_k(B) v_0 = 2 v_p^T v_q - v_0^T T_{|p-q|}(B) v_0.
  *    (The paper prints the sign of the last term as "+"; the product formula
  *    T_p T_q = (T_{p+q} + T_{|p-q|})/2 fixes it as "-".)
+ *  - Legendre moments (Algorithm DGL, Section 3.1.3): v_1 = B v_0,
+ *    v_{k+1} = ((2k+1) B v_k - k v_{k-1}) / (k+1), nu_k = v_0^T v_k.
  *
  * Normalisation: each vector's moment is mu_k^(l) = v_l^T T_k(B) v_l / n, so
  * that the average over the n_v vectors is
@@ -99,14 +101,15 @@ static double dot(int64_t n, const double *x, const double *y, int reverse) {
 /*
  * Per-vector moments mu_per_vec[l*(M+1) + k] = v_l^T T_k(B) v_l / n for
  * l = 0..n_v-1 (start vector index vec_offset + l of matrix `batch_index`).
- * mode 0 = direct (M matrix-vector products), 1 = doubling (ceil(M/2)).
+ * mode 0 = direct (M matrix-vector products), 1 = doubling (ceil(M/2)),
+ * 2 = Legendre: mu_per_vec[l*(M+1) + k] = v_l^T L_k(B) v_l / n (M products).
  * Returns 0, or -1 on bad arguments / allocation failure.
  */
 int oracle_kpm_moments(int64_t n, const int32_t *row_ptr, const int32_t *col_idx,
                        const double *val, double lb, double ub, int M, int64_t n_v,
                        int64_t vec_offset, uint64_t seed, uint64_t batch_index, int mode,
                        int reverse, int nthreads, double *mu_per_vec) {
-    if (n <= 0 || M < 0 || n_v <= 0 || !(ub > lb) || (mode != 0 && mode != 1)) return -1;
+    if (n <= 0 || M < 0 || n_v <= 0 || !(ub > lb) || (mode < 0 || mode > 2)) return -1;
     const double c = 0.5 * (lb + ub);
     const double d = 0.5 * (ub - lb);
     int failed = 0;
@@ -139,6 +142,24 @@ int oracle_kpm_moments(int64_t n, const int32_t *row_ptr, const int32_t *col_idx
                 for (int k = 1; k < M; ++k) {
                     apply_B(n, row_ptr, col_idx, val, c, d, vcur, vnext);
                     for (int64_t i = 0; i < n; ++i) vnext[i] = 2.0 * vnext[i] - vprev[i];
+                    memcpy(vprev, vcur, sizeof(double) * n);
+                    memcpy(vcur, vnext, sizeof(double) * n);
+                    mu[k + 1] = dot(n, v0, vcur, reverse) / dn;
+                }
+            } else if (mode == 2) {
+                /* Algorithm DGL: the Legendre three-term recurrence, direct dots. */
+                memcpy(vcur, v0, sizeof(double) * n);
+                mu[0] = dot(n, v0, vcur, reverse) / dn;
+                if (M >= 1) {
+                    apply_B(n, row_ptr, col_idx, val, c, d, v0, vnext);   /* v_1 = B v_0 */
+                    memcpy(vprev, vcur, sizeof(double) * n);
+                    memcpy(vcur, vnext, sizeof(double) * n);
+                    mu[1] = dot(n, v0, vcur, reverse) / dn;
+                }
+                for (int k = 1; k < M; ++k) {
+                    apply_B(n, row_ptr, col_idx, val, c, d, vcur, vnext);
+                    const double a = (2.0 * k + 1.0) / (k + 1.0), b = (double)k / (k + 1.0);
+                    for (int64_t i = 0; i < n; ++i) vnext[i] = a * vnext[i] - b * vprev[i];
                     memcpy(vprev, vcur, sizeof(double) * n);
                     memcpy(vcur, vnext, sizeof(double) * n);
                     mu[k + 1] = dot(n, v0, vcur, reverse) / dn;

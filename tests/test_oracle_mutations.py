@@ -109,3 +109,53 @@ def test_swapped_jackson_terms_are_caught(monkeypatch):
     _, pj, _ = odos.reconstruct(mu, "jackson", t=np.linspace(-0.99, 0.99, 999))
     with pytest.raises(AssertionError):
         assert abs(g[0] - 1.0) < 1e-15 and pj.min() >= -1e-12 * pj.max()
+
+
+def legendre_pin_residual(lib):
+    """max |oracle - exact| of the dense-eig pin of the Legendre moments (mode 2)."""
+    import scipy.special
+    A = random_symmetric(60, 0.1, 1, empty_rows=2)
+    lam, U = np.linalg.eigh(A.to_dense())
+    lb, ub = lam[0] - 0.3, lam[-1] + 0.2
+    c, d = 0.5 * (lb + ub), 0.5 * (ub - lb)
+    M, nv = 30, 2
+    out = np.empty((nv, M + 1))
+    rp, ci, va = okpm._csr_arrays(A.row_ptr, A.col_idx, A.val)
+    assert lib.oracle_kpm_moments(A.n, rp.ctypes.data, ci.ctypes.data, va.ctypes.data, lb, ub,
+                                  M, nv, 0, 5, 0, 2, 0, 1, out.ctypes.data) == 0
+    W = (U.T @ okpm.start_block(A.n, nv, seed=5)) ** 2 / A.n
+    Lk = np.array([scipy.special.eval_legendre(k, (lam - c) / d) for k in range(M + 1)])
+    return np.abs(out - (Lk @ W).T).max()
+
+
+def test_legendre_recurrence_coefficient_is_caught(tmp_path):
+    (tmp_path / "good").mkdir()
+    (tmp_path / "bad").mkdir()
+    good = build_mutant(tmp_path / "good", "(2.0 * k + 1.0) / (k + 1.0)",
+                        "(2.0 * k + 1.0) / (k + 1.0)")
+    assert legendre_pin_residual(good) < 1e-12
+    bad = build_mutant(tmp_path / "bad", "(2.0 * k + 1.0) / (k + 1.0)", "(2.0 * k) / (k + 1.0)")
+    assert legendre_pin_residual(bad) > 1e-3
+
+
+def test_dgl_boundary_term_sign_is_caught():
+    """Flip the parity sign of zeta_k (Eq. eta) in a copy of the DGL oracle; the
+    quadrature pin of Eq. DGLcoeff must fail."""
+    import types
+
+    import scipy.special
+    from oracle import legendre as oleg
+    text = open(oleg.__file__).read()
+    old = "zeta = e_plus - (e_minus if k % 2 == 0 else -e_minus)"
+    assert old in text
+    mod = types.ModuleType("oracle.legendre_mutant")
+    mod.__package__ = "oracle"
+    exec(compile(text.replace(old, "zeta = e_plus + (e_minus if k % 2 == 0 else -e_minus)"),
+                 "legendre_mutant", "exec"), mod.__dict__)
+    s, w = scipy.special.roots_legendre(2000)
+    t, sigma = 0.1, 0.5                      # wide, so both boundary terms matter
+    G = np.exp(-0.5 * ((s - t) / sigma) ** 2)
+    for m, expect_ok in ((oleg, True), (mod, False)):
+        g = m.dgl_gamma(t, sigma, 200)
+        ref = np.array([np.sum(w * scipy.special.eval_legendre(k, s) * G) for k in range(g.shape[0])])
+        assert (np.abs(g - ref).max() < 1e-10) == expect_ok
