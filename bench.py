@@ -256,8 +256,8 @@ def run_batched(args, w, world, rank, local, device):
     def step(Acsr, precision):
         lb, ub = ctx.dos_bounds_batched(Acsr, seg, pad_frac=0.01)
         return lb, ub, ctx.dos_kpm_moments_batched(Acsr, seg, lb, ub, M, n_v, seed=w["seed"],
-                                                   precision=precision,
-                                                   batch_index=0)
+                                                   precision=precision, batch_index=0,
+                                                   flags=dos.DOS_OPT_NO_PDL if args.no_pdl else 0)
 
     def timed(fn, steps, warmup, profile=False):
         for _ in range(warmup):
@@ -323,7 +323,7 @@ def run_batched(args, w, world, rank, local, device):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f32+f64acc" if prec == "f32" else "f64", "data": "synthetic",
             "config": {"workload": "batched", "desc": w["desc"], "B": len(mats), "n": n_rows,
-                       "nnz": nnz, "M": M, "n_v": n_v, "precision": prec,
+                       "nnz": nnz, "M": M, "n_v": n_v, "precision": prec, "pdl": not args.no_pdl,
                        "l2": "inputs larger than L2: %.0f MB per fused step" % (alg / 1e6)},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"],
                          "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"], "traffic": None,
@@ -349,6 +349,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-f64-form", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-pdl", action="store_true",
+                    help="plain stream order between sweep steps (no programmatic dependent launch)")
     ap.add_argument("--launch", default=None,
                     help="fixed launch shape team,chunks,staged(1|2) instead of the autotuner "
                          "(used when profiling one known kernel instance)")
@@ -401,10 +403,12 @@ def main():
         ref_mu = ctx.dos_kpm_moments(Ad64, lb, ub, M, 1024, seed=seed + 1000, precision="f64",
                                      vec_offset=0)
 
+    sweep_flags = dos.DOS_OPT_NO_PDL if args.no_pdl else 0
+
     def step(Acsr, precision, host=False):
         lo, hi = ctx.dos_bounds(Acsr, "gershgorin", pad_frac=0.01)
         mu = ctx.dos_kpm_moments(Acsr, lo, hi, M, n_v, seed=seed, precision=precision,
-                                 vec_offset=vec_offset,
+                                 vec_offset=vec_offset, flags=sweep_flags,
                                  launch=fixed if precision == prec else None)
         phi = ctx.dos_reconstruct(mu, M, "jackson", lo, hi, N_t=1000)
         e1, einf = ctx.dos_smoothed_error(mu, M, "jackson", lo, hi, sigma, ref_mu=ref_mu)
@@ -515,7 +519,7 @@ def main():
                        "M": M, "n_v": n_v, "precision": prec,
                        "l2": "inputs larger than L2: %.0f MB touched per fused step"
                              % (algorithmic_bytes_per_step(A.n, A.nnz, n_v, prec) / 1e6),
-                       "sigma": sigma, "lb": lb, "ub": ub},
+                       "sigma": sigma, "lb": lb, "ub": ub, "pdl": not args.no_pdl},
             "dos_per_s": 1e3 / ms, "e1": e1, "einf": einf,
             "roofline": roofline, "forms": forms, "e2e": e2e, "cpu_baseline": cpu,
             "gpu_launches": prof["launches"], "clocks": clk.summary(),

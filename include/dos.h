@@ -81,6 +81,11 @@ extern "C" {
 #define DOS_OPT_TEST_STALL_WAIT 16u /* failure-detection tests only: the staged kernel
                                        expects 16 bytes more than it copies, so its first
                                        wait can never complete and must run out */
+#define DOS_OPT_NO_PDL 32u          /* launch consecutive sweep steps with plain stream
+                                       order instead of programmatic dependent launch
+                                       (the next step's blocks are scheduled while the
+                                       current one drains and wait on the device for its
+                                       completion before touching memory) */
 
 typedef struct dos_ctx dos_ctx;
 
@@ -400,6 +405,80 @@ int dos_points_error(dos_ctx *ctx, const double *pts, const double *wts, int64_t
                      double lb, double ub, const double *eig, int64_t n_eig, const double *ref_mu,
                      int M_ref, int ref_damping, double sigma, int N_x, double *err_l1,
                      double *err_inf, void *stream);
+
+/* ---- KPML and the Delta-Gauss-Legendre method (Sections 3.1.1, 3.1.3, App. B) */
+/*
+ * Legendre moments nu_k = (1/(n n_v)) sum_l v_l^T L_k(B) v_l, k = 0..M, of the
+ * same start vectors and B as dos_kpm_moments (Algorithm DGL, with Rademacher
+ * vectors in place of normalised ones, hence the 1/n; nu_0 = 1).
+ * Algorithm DGL forms them from M passes of the Legendre recurrence
+ * (k+1) v_{k+1} = (2k+1) B v_k - k v_{k-1}; here they come from the Chebyshev
+ * sweep (ceil(M/2) passes with the doubling identity) and the exact expansion
+ *     L_k(t) = sum_{m=0}^{floor(k/2)} e_{k-2m} h_m h_{k-m} T_{k-2m}(t),
+ *     h_m = (2m)! / (4^m (m!)^2),  e_0 = 1, e_j = 2 (j > 0),
+ * whose coefficients are non-negative and sum to L_k(1) = 1, so each nu_k is a
+ * convex combination of mu_0..mu_k and inherits their rounding error.
+ * Arguments, precision, options and errors as dos_kpm_moments_ex; nu: M+1
+ * doubles, nu_per_vec: NULL or n_v*(M+1) doubles [l*(M+1) + k] (host or device).
+ */
+int dos_legendre_moments(dos_ctx *ctx, const dos_csr *A, double lb, double ub, int M, int n_v,
+                         uint64_t seed, int precision, double *nu, double *nu_per_vec,
+                         const dos_kpm_opts *opts, void *stream);
+
+/*
+ * The expansion above applied to `count` rows of M+1 Chebyshev moments
+ * (mu[r*(M+1) + j], normalised as dos_kpm_moments) giving Legendre moments
+ * nu[r*(M+1) + k].  mu, nu: host or device, distinct.  0 <= M <= 100000.
+ * Synchronises `stream` when nu is host memory.  Errors: DOS_EINVAL,
+ * DOS_ENOMEM, DOS_ECUDA.
+ */
+int dos_cheb_to_legendre(dos_ctx *ctx, const double *mu, int64_t count, int M, double *nu,
+                         void *stream);
+
+/*
+ * KPML: the Legendre expansion of the DOS (Section 3.1.1; undamped -- the paper
+ * gives no damping for Legendre polynomials):
+ *     phi_L(t) = sum_{k=0}^{M} (k + 1/2) nu_k L_k(t),
+ * and phi(lambda) = phi_L((lambda - c)/d) / d.  nu: M+1 doubles; t: N_t points
+ * in [-1, 1] or NULL for the nodes t_i = -cos(pi (i + 1/2) / N_t); phi_t: N_t
+ * doubles; phi_lambda: NULL or N_t doubles (needs ub > lb).  All host or
+ * device.  Synchronises `stream` when an output is host memory.
+ */
+int dos_kpml_reconstruct(dos_ctx *ctx, const double *nu, int M, double lb, double ub,
+                         const double *t, int N_t, double *phi_t, double *phi_lambda,
+                         void *stream);
+
+/*
+ * DGL (Eq. dglexpansion, Algorithm DGL): at each x (eigenvalue units) with
+ * t = (x - c)/d and s = sigma/d,
+ *     phi(x) = (1/d) (2 pi s^2)^{-1/2} sum_{k=0}^{M_x} (k + 1/2) gamma_k(t) nu_k,
+ *     gamma_k(t) = int_{-1}^{1} L_k(u) exp(-((u - t)/s)^2 / 2) du   (Eq. DGLcoeff),
+ * gamma_0 from Eq. gam0 (erf), the rest from the joint recurrence of Eq. Leg3
+ * (psi_0 = 0, psi_1 = gamma_0, zeta_k of Eq. eta), stopped at the first k >= 1
+ * with |gamma_{k-1}| + |gamma_k| <= k tol (Eq. StopRecur; tol <= 0: never) or
+ * at M: M_x = that k.  phi approximates the Gaussian-blurred DOS
+ * (1/n) sum_j g_sigma(x - lambda_j) directly.
+ *   nu: M+1 doubles; x: N_x points, or NULL for the metric's grid of
+ *   dos_smoothed_error (N_x points over [lb - 6 sigma, ub + 6 sigma]);
+ *   phi: N_x doubles; m_used: NULL or N_x ints.  All host or device.
+ * Synchronises `stream` when an output is host memory.
+ */
+int dos_dgl(dos_ctx *ctx, const double *nu, int M, double lb, double ub, double sigma, double tol,
+            const double *x, int N_x, double *phi, int *m_used, void *stream);
+
+/*
+ * dos_smoothed_error for the Legendre methods: method DOS_LEG_KPML blurs phi_L
+ * as <phi_L, g_sigma(. - x)> by Gauss-Legendre quadrature on
+ * N_q = max(4(M'+1), ceil(40 d / sigma)) nodes of [-1, 1] (nodes by Newton's
+ * method on L_{N_q}); method DOS_LEG_DGL uses phi of dos_dgl as is (the paper
+ * compares DGL with the sup-norm of Eq. err2).  Reference, grid, norms and
+ * outputs as dos_smoothed_error.  Synchronises `stream`.
+ */
+enum { DOS_LEG_KPML = 0, DOS_LEG_DGL = 1 };
+int dos_legendre_error(dos_ctx *ctx, const double *nu, int M, int method, double lb, double ub,
+                       double sigma, double tol, const double *eig, int64_t n_eig,
+                       const double *ref_mu, int M_ref, int ref_damping, int N_x, double *err_l1,
+                       double *err_inf, void *stream);
 
 /* ---- an observable: the heat capacity (Section 4.3) ------------------------ */
 /*

@@ -354,6 +354,7 @@ void run_sweep(dos_ctx *ctx, const dos_csr *Adesc, SweepRequest &r, cudaStream_t
     a.status = status;
     a.spin_cycles = r.opts.wait_limit_cycles;
     a.stall_test = (r.opts.flags & DOS_OPT_TEST_STALL_WAIT) ? 1 : 0;
+    a.pdl = (r.opts.flags & DOS_OPT_NO_PDL) ? 0 : 1;
 
     const double tol = r.precision == DOS_PREC_F64 ? 1e-8 : 1e-3;
     const bool profiling = ctx->profiling;
@@ -402,7 +403,7 @@ void run_sweep(dos_ctx *ctx, const dos_csr *Adesc, SweepRequest &r, cudaStream_t
         (uint64_t)per_vec, (uint64_t)slots, (uint64_t)(uintptr_t)xb, (uint64_t)(uintptr_t)partial,
         (uint64_t)(uintptr_t)dotsum, (uint64_t)(uintptr_t)mu_dev, (uint64_t)(uintptr_t)mupv_dev,
         (uint64_t)(uintptr_t)tiles, (uint64_t)(uintptr_t)seg.row0, (uint64_t)(uintptr_t)status,
-        (uint64_t)profiling, (uint64_t)(uintptr_t)s};
+        (uint64_t)profiling, (uint64_t)(uintptr_t)s, (uint64_t)a.pdl};
     GraphCache &gc = ctx->graph;
     const bool use_graph = !(r.opts.flags & DOS_OPT_NO_GRAPH);
     // The graph runs on a context-owned stream ordered after `s` by events, so
@@ -1267,6 +1268,173 @@ int dos_smoothed_error(dos_ctx *ctx, const double *mu, int M, int damping, doubl
         double *deig = out + 2;
         DOS_CUDA_TRY(cudaMemcpyAsync(dmu, mu, (M + 1) * sizeof(double), cudaMemcpyDefault, s));
         launch_blur_kpm(dmu, M, damping, lb, ub, sigma, N_q, x0, h, N_x, poly, approx, s);
+        if (eig) {
+            DOS_CUDA_TRY(cudaMemcpyAsync(deig, eig, neig * sizeof(double), cudaMemcpyDefault, s));
+            launch_blur_eigs(deig, n_eig, sigma, x0, h, N_x, ref, s);
+        } else {
+            DOS_CUDA_TRY(cudaMemcpyAsync(dref, ref_mu, n_ref * sizeof(double), cudaMemcpyDefault, s));
+            launch_blur_kpm(dref, M_ref, ref_damping, lb, ub, sigma, N_q, x0, h, N_x, poly, ref, s);
+        }
+        launch_error_norms(approx, ref, N_x, h, out, s);
+        double hv[2];
+        DOS_CUDA_TRY(cudaMemcpyAsync(hv, out, sizeof(hv), cudaMemcpyDeviceToHost, s));
+        DOS_CUDA_TRY(cudaStreamSynchronize(s));
+        if (err_l1) *err_l1 = hv[0];
+        if (err_inf) *err_inf = hv[1];
+    });
+}
+
+// ---- KPML and DGL (Sections 3.1.1, 3.1.3, Appendix B) -------------------------
+
+int dos_legendre_moments(dos_ctx *ctx, const dos_csr *A, double lb, double ub, int M, int n_v,
+                         uint64_t seed, int precision, double *nu, double *nu_per_vec,
+                         const dos_kpm_opts *opts, void *stream) {
+    return guarded(ctx, [&] {
+        DOS_REQUIRE(A != nullptr, "matrix descriptor is NULL");
+        DOS_REQUIRE(nu != nullptr, "nu is NULL");
+        DOS_REQUIRE(M >= 0 && M <= 100000, "M must be in [0, 100000]");
+        DOS_REQUIRE(n_v >= 1 && n_v <= (1 << 20), "n_v must be in [1, 2^20]");
+        cudaStream_t s = (cudaStream_t)stream;
+        const size_t per = (size_t)M + 1;
+        const size_t rows = 1 + (nu_per_vec ? (size_t)n_v : 0);
+        // scratch: Chebyshev moments (averaged row, then per-vector rows) | Legendre | h
+        double *buf = (double *)ctx->leg_buf.get((2 * rows * per + per) * sizeof(double));
+        double *dmu = buf, *dnu = buf + rows * per, *h = dnu + rows * per;
+        SweepRequest r;
+        r.B = 1;
+        r.seg_rows = {0, A->n};
+        r.lb = {lb};
+        r.ub = {ub};
+        r.M = M;
+        r.n_v = n_v;
+        r.seed = seed;
+        r.precision = precision;
+        r.mu = dmu;
+        r.mu_pv = nu_per_vec ? dmu + per : nullptr;
+        r.opts = opts ? *opts : default_opts();
+        run_sweep(ctx, A, r, s);
+        launch_cheb_to_legendre(dmu, (int64_t)rows, M, h, dnu, s);
+        copy_out(nu, dnu, per * sizeof(double), s);
+        if (nu_per_vec) copy_out(nu_per_vec, dnu + per, (size_t)n_v * per * sizeof(double), s);
+        if (!is_device_ptr(nu) || (nu_per_vec && !is_device_ptr(nu_per_vec)))
+            DOS_CUDA_TRY(cudaStreamSynchronize(s));
+    });
+}
+
+int dos_cheb_to_legendre(dos_ctx *ctx, const double *mu, int64_t count, int M, double *nu,
+                         void *stream) {
+    return guarded(ctx, [&] {
+        DOS_REQUIRE(mu && nu && mu != nu, "mu / nu is NULL or aliased");
+        DOS_REQUIRE(M >= 0 && M <= 100000, "M must be in [0, 100000]");
+        DOS_REQUIRE(count >= 1 && count * ((int64_t)M + 1) <= (int64_t(1) << 30),
+                    "count * (M+1) must be in [1, 2^30]");
+        cudaStream_t s = (cudaStream_t)stream;
+        const size_t tot = (size_t)count * (M + 1);
+        double *buf = (double *)ctx->leg_buf.get((2 * tot + M + 1) * sizeof(double));
+        double *dmu = buf, *dnu = buf + tot, *h = dnu + tot;
+        DOS_CUDA_TRY(cudaMemcpyAsync(dmu, mu, tot * sizeof(double), cudaMemcpyDefault, s));
+        launch_cheb_to_legendre(dmu, count, M, h, dnu, s);
+        copy_out(nu, dnu, tot * sizeof(double), s);
+        if (!is_device_ptr(nu)) DOS_CUDA_TRY(cudaStreamSynchronize(s));
+    });
+}
+
+int dos_kpml_reconstruct(dos_ctx *ctx, const double *nu, int M, double lb, double ub,
+                         const double *t, int N_t, double *phi_t, double *phi_lambda,
+                         void *stream) {
+    return guarded(ctx, [&] {
+        DOS_REQUIRE(nu && phi_t, "nu / phi_t is NULL");
+        DOS_REQUIRE(M >= 0 && M <= 100000, "M must be in [0, 100000]");
+        DOS_REQUIRE(N_t >= 1 && N_t <= (1 << 26), "N_t must be in [1, 2^26]");
+        DOS_REQUIRE(!phi_lambda || (isfinite(lb) && isfinite(ub) && ub > lb), "need ub > lb");
+        cudaStream_t s = (cudaStream_t)stream;
+        const size_t per = (size_t)M + 1;
+        double *buf = (double *)ctx->leg_buf.get((per + 3 * (size_t)N_t) * sizeof(double));
+        double *dnu = buf, *dt = buf + per, *dphi = dt + N_t, *dphl = dphi + N_t;
+        DOS_CUDA_TRY(cudaMemcpyAsync(dnu, nu, per * sizeof(double), cudaMemcpyDefault, s));
+        if (t) DOS_CUDA_TRY(cudaMemcpyAsync(dt, t, N_t * sizeof(double), cudaMemcpyDefault, s));
+        const double inv_d = phi_lambda ? 1.0 / (0.5 * (ub - lb)) : 0.0;
+        launch_kpml(dnu, M, t ? dt : nullptr, nullptr, N_t, inv_d, dphi,
+                    phi_lambda ? dphl : nullptr, s);
+        copy_out(phi_t, dphi, N_t * sizeof(double), s);
+        if (phi_lambda) copy_out(phi_lambda, dphl, N_t * sizeof(double), s);
+        if (!is_device_ptr(phi_t) || (phi_lambda && !is_device_ptr(phi_lambda)))
+            DOS_CUDA_TRY(cudaStreamSynchronize(s));
+    });
+}
+
+int dos_dgl(dos_ctx *ctx, const double *nu, int M, double lb, double ub, double sigma, double tol,
+            const double *x, int N_x, double *phi, int *m_used, void *stream) {
+    return guarded(ctx, [&] {
+        DOS_REQUIRE(nu && phi, "nu / phi is NULL");
+        DOS_REQUIRE(M >= 0 && M <= 100000, "M must be in [0, 100000]");
+        DOS_REQUIRE(isfinite(lb) && isfinite(ub) && ub > lb, "need ub > lb");
+        DOS_REQUIRE(isfinite(sigma) && sigma > 0.0, "sigma must be > 0");
+        DOS_REQUIRE(isfinite(tol), "tol must be finite");
+        DOS_REQUIRE(N_x >= (x ? 1 : 2) && N_x <= 1000000, "N_x must be in [1 (2 for the grid), 10^6]");
+        cudaStream_t s = (cudaStream_t)stream;
+        const size_t per = (size_t)M + 1;
+        double *buf = (double *)ctx->leg_buf.get((per + 2 * (size_t)N_x) * sizeof(double) +
+                                                 (size_t)N_x * sizeof(int));
+        double *dnu = buf, *dx = buf + per, *dphi = dx + N_x;
+        int *dused = (int *)(dphi + N_x);
+        DOS_CUDA_TRY(cudaMemcpyAsync(dnu, nu, per * sizeof(double), cudaMemcpyDefault, s));
+        if (x) DOS_CUDA_TRY(cudaMemcpyAsync(dx, x, N_x * sizeof(double), cudaMemcpyDefault, s));
+        const double x0 = lb - 6.0 * sigma;
+        const double h = x ? 0.0 : (ub - lb + 12.0 * sigma) / (N_x - 1);
+        launch_dgl(dnu, M, 0.5 * (lb + ub), 0.5 * (ub - lb), sigma, tol, x ? dx : nullptr, x0, h,
+                   N_x, dphi, m_used ? dused : nullptr, s);
+        copy_out(phi, dphi, N_x * sizeof(double), s);
+        if (m_used) copy_out(m_used, dused, N_x * sizeof(int), s);
+        if (!is_device_ptr(phi) || (m_used && !is_device_ptr(m_used)))
+            DOS_CUDA_TRY(cudaStreamSynchronize(s));
+    });
+}
+
+int dos_legendre_error(dos_ctx *ctx, const double *nu, int M, int method, double lb, double ub,
+                       double sigma, double tol, const double *eig, int64_t n_eig,
+                       const double *ref_mu, int M_ref, int ref_damping, int N_x, double *err_l1,
+                       double *err_inf, void *stream) {
+    return guarded(ctx, [&] {
+        DOS_REQUIRE(nu != nullptr, "nu is NULL");
+        DOS_REQUIRE(method == DOS_LEG_KPML || method == DOS_LEG_DGL, "bad method");
+        DOS_REQUIRE(M >= 0 && M <= 100000, "M must be in [0, 100000]");
+        DOS_REQUIRE(isfinite(lb) && isfinite(ub) && ub > lb, "need ub > lb");
+        DOS_REQUIRE(isfinite(sigma) && sigma > 0.0, "sigma must be > 0");
+        DOS_REQUIRE(isfinite(tol), "tol must be finite");
+        DOS_REQUIRE(N_x >= 2 && N_x <= 1000000, "N_x must be in [2, 10^6]");
+        DOS_REQUIRE(eig ? n_eig >= 1 : (ref_mu != nullptr && M_ref >= 0 && M_ref <= 100000),
+                    "need eigenvalues or reference moments");
+        DOS_REQUIRE(eig || ref_damping == DOS_DAMP_NONE || ref_damping == DOS_DAMP_JACKSON,
+                    "bad ref_damping");
+        cudaStream_t s = (cudaStream_t)stream;
+        const int Meff = eig ? M : std::max(M, M_ref);
+        const double c = 0.5 * (lb + ub), d = 0.5 * (ub - lb);
+        const int64_t nq64 = std::max<int64_t>(4 * (int64_t)(Meff + 1),
+                                               (int64_t)ceil(40.0 * d / sigma));
+        // Gauss-Legendre nodes cost O(N_q^2); the Chebyshev reference takes up to 2^24
+        DOS_REQUIRE(nq64 <= (method == DOS_LEG_KPML ? (1 << 17) : (1 << 24)),
+                    "sigma too small for the quadrature");
+        const int N_q = (int)nq64;
+        const double x0 = lb - 6.0 * sigma, h = (ub - lb + 12.0 * sigma) / (N_x - 1);
+        const size_t per = (size_t)M + 1, n_ref = eig ? 0 : (size_t)M_ref + 1;
+        const size_t neig = eig ? (size_t)n_eig : 0;
+        // scratch: nu | ref_mu | blur_kpm scratch | approx | ref | out | eig | GL t, w, y, P
+        const size_t nd = per + n_ref + (size_t)(Meff + 1) + 2 * (size_t)N_q + 2 * (size_t)N_x +
+                          2 + neig + 4 * (size_t)N_q;
+        double *buf = (double *)ctx->leg_aux.get(nd * sizeof(double));
+        double *dnu = buf, *dref = dnu + per, *poly = dref + n_ref;
+        double *approx = poly + (Meff + 1) + 2 * (size_t)N_q, *ref = approx + N_x;
+        double *out = ref + N_x, *deig = out + 2, *gt = deig + neig, *gw = gt + N_q;
+        double *gy = gw + N_q, *gP = gy + N_q;
+        DOS_CUDA_TRY(cudaMemcpyAsync(dnu, nu, per * sizeof(double), cudaMemcpyDefault, s));
+        if (method == DOS_LEG_KPML) {
+            launch_gauss_legendre(N_q, c, d, gt, gw, gy, s);
+            launch_kpml(dnu, M, gt, gw, N_q, 0.0, gP, nullptr, s);
+            launch_weighted_gauss(gy, gP, N_q, 1.0, sigma, nullptr, x0, h, N_x, approx, s);
+        } else {
+            launch_dgl(dnu, M, c, d, sigma, tol, nullptr, x0, h, N_x, approx, nullptr, s);
+        }
         if (eig) {
             DOS_CUDA_TRY(cudaMemcpyAsync(deig, eig, neig * sizeof(double), cudaMemcpyDefault, s));
             launch_blur_eigs(deig, n_eig, sigma, x0, h, N_x, ref, s);

@@ -110,6 +110,8 @@ struct dos_ctx {
     dos::Buffer bnd_vec, bnd_part, bnd_out;
     // Lanczos DOS scratch
     dos::Buffer lz_buf;
+    // Legendre (KPML / DGL) scratch: moments, conversion table, nodes and grids
+    dos::Buffer leg_buf, leg_aux;
     // reconstruct / error scratch
     dos::Buffer rec_in, rec_out, err_buf;
     dos::PinnedBuffer host_stage;
@@ -174,6 +176,7 @@ struct SweepArgs {
     int *status = nullptr;    // device flags: bit 1 spectrum, bit 2 wait timeout
     long long spin_cycles = 0;  // bounded-wait limit (0: about one second)
     int stall_test = 0;       // tests only: make the staged kernel's first wait run out
+    int pdl = 1;              // programmatic dependent launch of the direct step kernel
 };
 
 // Occupancy-derived default shape for (precision, ld).
@@ -245,6 +248,21 @@ void launch_heat_kpm(const double *mu, int M, int damping, double lb, double ub,
                      cudaStream_t s);
 void launch_heat_points(const double *pts, const double *w, int64_t n_pts, double scale,
                         const double *betas, int n_beta, double *out, cudaStream_t s);
+
+// KPML / DGL (FP64).  h_scratch: M+1 doubles.
+void launch_cheb_to_legendre(const double *mu, int64_t count, int M, double *h_scratch,
+                             double *nu, cudaStream_t s);
+// out_t[i] = phi_L(t_i) (times w[i] when w is given; t NULL: Chebyshev nodes),
+// out_l[i] = phi_L(t_i) * inv_d when out_l is given.
+void launch_kpml(const double *nu, int M, const double *t, const double *w, int N, double inv_d,
+                 double *out_t, double *out_l, cudaStream_t s);
+// Gauss-Legendre nodes t (ascending), weights w, positions y = c + d t (y may be NULL).
+void launch_gauss_legendre(int N, double c, double d, double *t, double *w, double *y,
+                           cudaStream_t s);
+// DGL density at x[i] (or x0 + i h when x is NULL); used may be NULL.
+void launch_dgl(const double *nu, int M, double c, double d, double sigma, double tol,
+                const double *x, double x0, double h, int N, double *phi, int *used,
+                cudaStream_t s);
 
 // Lanczos DOS (block of n_vec independent runs, FP64)
 int lanczos_blocks(int num_sms, int64_t n, int ld);

@@ -296,6 +296,12 @@ __global__ void __launch_bounds__(kBlock, 3) step_kernel(const StepParams<T> p) 
     constexpr int U = CPT >= 4 ? 4 : 8;  // nonzeros per gather batch (bounded registers)
     extern __shared__ double red[];
 
+    // Programmatic dependent launch: let the next step's grid be scheduled now,
+    // and wait until the previous grid has completed and its writes are visible
+    // before reading anything it produced.  Both are no-ops for a plain launch.
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+
     const int4 tl = p.tiles[blockIdx.x];
     const int rb = tl.x, re = tl.y, seg = tl.z;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -1289,7 +1295,17 @@ static void launch_step_t(const SweepArgs &a, int k, int slot, cudaStream_t s) {
         auto fn = pick<T>(a.shape.team, a.shape.chunks, a.per_vec != 0);
         if (!fn) throw Error{DOS_EINVAL, "unsupported launch shape"};
         p.panel_rows = 0;
-        fn<<<a.n_tiles, a.shape.block, step_smem(a.shape.block, a.ld), s>>>(p);
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3((unsigned)a.n_tiles);
+        cfg.blockDim = dim3((unsigned)a.shape.block);
+        cfg.dynamicSmemBytes = step_smem(a.shape.block, a.ld);
+        cfg.stream = s;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+        attr[0].val.programmaticStreamSerializationAllowed = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = a.pdl ? 1 : 0;
+        DOS_CUDA_TRY(cudaLaunchKernelEx(&cfg, fn, p));
     }
     DOS_LAUNCHED();
 }

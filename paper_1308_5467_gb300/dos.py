@@ -31,10 +31,13 @@ DOS_BOUNDS_GERSHGORIN, DOS_BOUNDS_LANCZOS = 0, 1
 DOS_DAMP_NONE, DOS_DAMP_JACKSON = 0, 1
 DOS_OPT_NO_VALIDATE, DOS_OPT_NO_SPECTRUM_CHECK, DOS_OPT_NO_GRAPH, DOS_OPT_AUTOTUNE = 1, 2, 4, 8
 DOS_OPT_TEST_STALL_WAIT = 16
+DOS_OPT_NO_PDL = 32
+DOS_LEG_KPML, DOS_LEG_DGL = 0, 1
 
 PRECISIONS = {"f64": DOS_PREC_F64, "f32": DOS_PREC_F32_ACC64}
 DAMPINGS = {"none": DOS_DAMP_NONE, "jackson": DOS_DAMP_JACKSON}
 BOUNDS = {"gershgorin": DOS_BOUNDS_GERSHGORIN, "lanczos": DOS_BOUNDS_LANCZOS}
+LEGENDRE_METHODS = {"kpml": DOS_LEG_KPML, "dgl": DOS_LEG_DGL}
 
 
 class dos_csr(C.Structure):
@@ -83,6 +86,13 @@ _SIGS = {
     "dos_haydock_dos": (_i, [_vp, _vp, _vp, _i, _i, _d, _vp, _i, _vp, _vp]),
     "dos_points_error": (_i, [_vp, _vp, _vp, _i64, _d, _d, _vp, _i64, _vp, _i, _i, _d, _i, _dp,
                               _dp, _vp]),
+    "dos_legendre_moments": (_i, [_vp, C.POINTER(dos_csr), _d, _d, _i, _i, _u64, _i, _vp, _vp,
+                                  C.POINTER(dos_kpm_opts), _vp]),
+    "dos_cheb_to_legendre": (_i, [_vp, _vp, _i64, _i, _vp, _vp]),
+    "dos_kpml_reconstruct": (_i, [_vp, _vp, _i, _d, _d, _vp, _i, _vp, _vp, _vp]),
+    "dos_dgl": (_i, [_vp, _vp, _i, _d, _d, _d, _d, _vp, _i, _vp, _vp, _vp]),
+    "dos_legendre_error": (_i, [_vp, _vp, _i, _i, _d, _d, _d, _d, _vp, _i64, _vp, _i, _i, _i,
+                                _dp, _dp, _vp]),
 }
 _SIGS.update({
     "dos_mlp_create": (_i, [_vp, _i, _i, _i, _u64, C.POINTER(_vp)]),
@@ -411,6 +421,89 @@ class Context:
         self._check(_lib.dos_smoothed_error(self._h, pmu, int(M), damp, float(lb), float(ub), pe,
                                             n_eig, pr, M_ref, rdamp, float(sigma), int(N_x),
                                             C.byref(e1), C.byref(einf), _stream_of(mu)))
+        return e1.value, einf.value
+
+    def dos_legendre_moments(self, A: CSRArrays, lb: float, ub: float, M: int, n_v: int,
+                             seed: int, precision="f64", nu=None, nu_per_vec=None, flags=0,
+                             vec_offset=0, batch_index=0, launch=None):
+        """Legendre moments nu_0..nu_M of the same start vectors as dos_kpm_moments."""
+        prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+        out = np.empty(M + 1, dtype=np.float64) if nu is None else nu
+        pnu, _, k0 = _ptr(out)
+        ppv, _, k1 = _ptr(nu_per_vec)
+        opts = self._opts(flags, vec_offset, batch_index, launch)
+        self._check(_lib.dos_legendre_moments(self._h, C.byref(A.desc), float(lb), float(ub),
+                                              int(M), int(n_v), int(seed), prec, pnu, ppv,
+                                              C.byref(opts), _stream_of(A.row_ptr, out)))
+        return out
+
+    def dos_cheb_to_legendre(self, mu, nu=None):
+        """Rows of Chebyshev moments (last axis M+1) to Legendre moments."""
+        M = int(mu.shape[-1]) - 1
+        count = int(np.prod(mu.shape[:-1])) if len(mu.shape) > 1 else 1
+        if nu is None:
+            src = np.ascontiguousarray(mu, dtype=np.float64) if not _is_torch(mu) else mu
+            out = np.empty(tuple(mu.shape), dtype=np.float64) if not _is_torch(mu) else \
+                mu.new_empty(mu.shape)
+        else:
+            src, out = mu, nu
+        pm, _, k0 = _ptr(src)
+        po, _, k1 = _ptr(out)
+        self._check(_lib.dos_cheb_to_legendre(self._h, pm, count, M, po, _stream_of(src, out)))
+        return out
+
+    def dos_kpml_reconstruct(self, nu, lb: float = -1.0, ub: float = 1.0, t=None,
+                             N_t: int = 1000, want_lambda: bool = False):
+        n = np.ascontiguousarray(nu, dtype=np.float64)
+        tt = None if t is None else np.ascontiguousarray(t, dtype=np.float64)
+        if tt is not None:
+            N_t = int(tt.shape[0])
+        out = np.empty(N_t)
+        outl = np.empty(N_t) if want_lambda else None
+        self._check(_lib.dos_kpml_reconstruct(self._h, n.ctypes.data, int(n.shape[0]) - 1,
+                                              float(lb), float(ub),
+                                              None if tt is None else tt.ctypes.data, int(N_t),
+                                              out.ctypes.data,
+                                              None if outl is None else outl.ctypes.data,
+                                              C.c_void_p(0)))
+        return (out, outl) if want_lambda else out
+
+    def dos_dgl(self, nu, lb: float, ub: float, sigma: float, tol: float = 1e-6, x=None,
+                N_x: int = 4000):
+        """(phi, m_used) of the DGL density at x (eigenvalue units; None: the metric grid)."""
+        n = np.ascontiguousarray(nu, dtype=np.float64)
+        xx = None if x is None else np.ascontiguousarray(x, dtype=np.float64)
+        if xx is not None:
+            N_x = int(xx.shape[0])
+        phi = np.empty(N_x)
+        used = np.empty(N_x, dtype=np.int32)
+        self._check(_lib.dos_dgl(self._h, n.ctypes.data, int(n.shape[0]) - 1, float(lb),
+                                 float(ub), float(sigma), float(tol),
+                                 None if xx is None else xx.ctypes.data, int(N_x),
+                                 phi.ctypes.data, used.ctypes.data, C.c_void_p(0)))
+        return phi, used
+
+    def dos_legendre_error(self, nu, method, lb: float, ub: float, sigma: float,
+                           tol: float = 1e-6, eig=None, ref_mu=None, ref_damping="jackson",
+                           N_x: int = 4000):
+        meth = LEGENDRE_METHODS[method] if isinstance(method, str) else int(method)
+        rdamp = DAMPINGS[ref_damping] if isinstance(ref_damping, str) else int(ref_damping)
+        if not _is_torch(nu):
+            nu = np.ascontiguousarray(nu, dtype=np.float64)
+        if eig is not None and not _is_torch(eig):
+            eig = np.ascontiguousarray(eig, dtype=np.float64)
+        if ref_mu is not None and not _is_torch(ref_mu):
+            ref_mu = np.ascontiguousarray(ref_mu, dtype=np.float64)
+        pn, _, k0 = _ptr(nu)
+        pe, _, k1 = _ptr(eig)
+        pr, _, k2 = _ptr(ref_mu)
+        n_eig = 0 if eig is None else int(eig.shape[0])
+        M_ref = -1 if ref_mu is None else int(ref_mu.shape[0]) - 1
+        e1, einf = C.c_double(), C.c_double()
+        self._check(_lib.dos_legendre_error(self._h, pn, int(nu.shape[0]) - 1, meth, float(lb),
+                                            float(ub), float(sigma), float(tol), pe, n_eig, pr,
+                                            M_ref, rdamp, int(N_x), C.byref(e1), C.byref(einf),
+                                            _stream_of(nu)))
         return e1.value, einf.value
 
 
