@@ -187,7 +187,7 @@ __global__ void weighted_gauss_kernel(const double *__restrict__ pts, const doub
         double s = 0.0;
         for (int64_t j = threadIdx.x; j < n_pts; j += blockDim.x) {
             const double z = (xm - pts[j]) * inv_s;
-            if (fabs(z) < 38.7) s += w[j] * norm * exp(-0.5 * z * z);
+            if (fabs(z) < 12.0) s += w[j] * norm * exp(-0.5 * z * z);  // beyond: < 5e-32 of the peak
         }
         for (int off = 16; off > 0; off >>= 1) s += __shfl_down_sync(0xffffffffu, s, off);
         if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = s;
