@@ -105,7 +105,7 @@ typedef struct {
 /* Launch shape of the fused sweep kernel.  Zero fields mean "choose". */
 typedef struct {
     int32_t team;            /* threads that share one matrix row (1..32, power of 2) */
-    int32_t chunks;          /* 16-byte vector chunks per thread (1, 2, 4 or 8) */
+    int32_t chunks;          /* vector chunks per thread (1, 2 or 4) */
     int32_t block;           /* threads per block (64..1024, multiple of 32) */
     int32_t tiles;           /* row tiles = blocks per sweep step */
     int32_t staged;          /* 1: rows of X_k / X_{k-1} loaded by the threads;
@@ -114,6 +114,9 @@ typedef struct {
                                 3: every gather issued as a 16-byte asynchronous copy into
                                 shared memory, two chunks of nonzeros in flight per
                                 thread (0: choose) */
+    int32_t chunk_bytes;     /* bytes per chunk: 16, or 32 (256-bit loads and stores;
+                                with staged 1 only, and rows of whole 32-byte chunks)
+                                (0: 16, or the autotuned choice) */
 } dos_launch;
 
 /* Optional arguments of the _ex / _batched entry points (NULL = defaults). */

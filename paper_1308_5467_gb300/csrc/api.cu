@@ -186,7 +186,7 @@ Shape tune_shape(dos_ctx *ctx, const dos_csr *A, int B, const int64_t *seg_rows,
 Shape choose_shape(dos_ctx *ctx, const SweepRequest &r, const dos_csr *Adesc, int ld,
                    int64_t n_rows, int64_t nnz, cudaStream_t s) {
     const dos_launch &o = r.opts.launch;
-    if (o.team || o.chunks || o.block || o.tiles || o.staged) {
+    if (o.team || o.chunks || o.block || o.tiles || o.staged || o.chunk_bytes) {
         Shape d = default_shape(r.precision, ld, ctx->num_sms, n_rows);
         Shape sh;
         sh.team = o.team ? o.team : d.team;
@@ -194,10 +194,13 @@ Shape choose_shape(dos_ctx *ctx, const SweepRequest &r, const dos_csr *Adesc, in
         sh.block = o.block ? o.block : d.block;
         DOS_REQUIRE(o.staged >= 0 && o.staged <= 3, "launch.staged must be 0, 1, 2 or 3");
         sh.staged = o.staged ? o.staged - 1 : d.staged;
+        DOS_REQUIRE(o.chunk_bytes == 0 || o.chunk_bytes == 16 || o.chunk_bytes == 32,
+                    "launch.chunk_bytes must be 0, 16 or 32");
+        sh.cb = o.chunk_bytes ? o.chunk_bytes : 16;
         sh.tiles = 1;
         DOS_REQUIRE(shape_supported(r.precision, sh, ld),
-                    "launch override does not cover the vector block (team*chunks*16B >= row) "
-                    "or uses an unsupported team/chunks/block/staged combination");
+                    "launch override does not cover the vector block (team*chunks*chunk_bytes >= row) "
+                    "or uses an unsupported team/chunks/block/staged/chunk_bytes combination");
         if (o.tiles) {
             sh.tiles = o.tiles;
         } else {
@@ -400,6 +403,7 @@ void run_sweep(dos_ctx *ctx, const dos_csr *Adesc, SweepRequest &r, cudaStream_t
         (uint64_t)(uintptr_t)val, (uint64_t)A.n, (uint64_t)A.nnz, (uint64_t)B, (uint64_t)ld,
         (uint64_t)r.n_v, (uint64_t)r.M, r.seed, (uint64_t)r.opts.vec_offset, r.opts.batch_index,
         (uint64_t)sh.team, (uint64_t)sh.chunks, (uint64_t)sh.block, (uint64_t)plan.n_tiles,
+        (uint64_t)sh.staged, (uint64_t)sh.cb,
         (uint64_t)per_vec, (uint64_t)slots, (uint64_t)(uintptr_t)xb, (uint64_t)(uintptr_t)partial,
         (uint64_t)(uintptr_t)dotsum, (uint64_t)(uintptr_t)mu_dev, (uint64_t)(uintptr_t)mupv_dev,
         (uint64_t)(uintptr_t)tiles, (uint64_t)(uintptr_t)seg.row0, (uint64_t)(uintptr_t)status,
@@ -496,11 +500,11 @@ Shape tune_shape(dos_ctx *ctx, const dos_csr *A, int B, const int64_t *seg_rows,
     DOS_REQUIRE(n_v >= 1 && n_v <= 4096, "n_v must be in [1, 4096]");
     DOS_REQUIRE(precision == DOS_PREC_F64 || precision == DOS_PREC_F32_ACC64, "bad precision");
     const int vpt = precision == DOS_PREC_F64 ? 2 : 4;
+    const int esz = precision == DOS_PREC_F64 ? 8 : 4;
     const int pw = std::min(n_v, kPanelMax);
     const int n_panels = (n_v + kPanelMax - 1) / kPanelMax;
     const int panel_nv = (n_v + n_panels - 1) / n_panels;
     const int ld = (panel_nv + vpt - 1) / vpt * vpt;
-    const int chunks = ld / vpt;
     std::vector<int64_t> rows;
     if (B == 1) rows = {0, A->n};
     else rows.assign(seg_rows, seg_rows + B + 1);
@@ -514,16 +518,23 @@ Shape tune_shape(dos_ctx *ctx, const dos_csr *A, int B, const int64_t *seg_rows,
     Shape best;
     double best_t = INFINITY;
     bool first = true;
+    // variants: direct loads, TMA panels, asynchronous gathers (16-byte chunks),
+    // and direct loads with 32-byte chunks
+    const int variants[4][2] = {{0, 16}, {1, 16}, {2, 16}, {0, 32}};
     for (int G = 1; G <= 32; G <<= 1) {
         for (int C : {1, 2, 4})
-        for (int staged : {0, 1, 2}) {  // direct loads, TMA panels, asynchronous gathers
+        for (const auto &var : variants) {
+            const int cb = var[1];
+            if (ld % (cb / esz) != 0) continue;
+            const int chunks = ld / (cb / esz);
             const int cover = G * C;
             if (cover < chunks || (cover > 1 && cover / 2 >= chunks)) continue;
             Shape sh;
             sh.team = G;
             sh.chunks = C;
             sh.block = 256;
-            sh.staged = staged;
+            sh.staged = var[0];
+            sh.cb = cb;
             sh.tiles = 1;
             if (!shape_supported(precision, sh, ld)) continue;
             const int occ = max_active_blocks(precision, sh, ld);
@@ -554,6 +565,7 @@ Shape tune_shape(dos_ctx *ctx, const dos_csr *A, int B, const int64_t *seg_rows,
                         r.opts.launch.block = sh.block;
                         r.opts.launch.tiles = sh.tiles;
                         r.opts.launch.staged = sh.staged + 1;
+                        r.opts.launch.chunk_bytes = sh.cb;
                         DOS_CUDA_TRY(cudaEventRecord(e0, s));
                         run_sweep(ctx, A, r, s);
                         DOS_CUDA_TRY(cudaEventRecord(e1, s));
@@ -564,8 +576,10 @@ Shape tune_shape(dos_ctx *ctx, const dos_csr *A, int B, const int64_t *seg_rows,
                     per_step = std::min(per_step, (double)(ms[1] - ms[0]) / 16.0);
                 }
                 if (getenv("DOS_TUNE_VERBOSE"))
-                    fprintf(stderr, "dos_tune: team %d chunks %d staged %d tiles %d: %.4f ms/step\n",
-                            sh.team, sh.chunks, sh.staged, sh.tiles, per_step);
+                    fprintf(stderr,
+                            "dos_tune: team %d chunks %d staged %d chunk_bytes %d tiles %d: "
+                            "%.4f ms/step\n",
+                            sh.team, sh.chunks, sh.staged, sh.cb, sh.tiles, per_step);
                 if (per_step < best_t) {
                     best_t = per_step;
                     best = sh;
@@ -858,6 +872,7 @@ int dos_tune(dos_ctx *ctx, const dos_csr *A, int B, const int64_t *seg_rows, int
             best->block = sh.block;
             best->tiles = sh.tiles;
             best->staged = sh.staged + 1;
+            best->chunk_bytes = sh.cb;
         }
     });
 }

@@ -112,6 +112,57 @@ __device__ __forceinline__ void store16(T *p, const T (&v)[Traits<T>::VPT]) {
     }
 }
 
+// A chunk is the W consecutive vector entries one thread moves with one
+// instruction: 16 bytes (float4 / double2) or 32 bytes (the 256-bit
+// ld.global.v8.f32 / .v4.f64 and st.global forms of this GPU).  The 32-byte
+// forms are inline PTX marked volatile so that none of them is moved above the
+// grid-dependency wait at the top of the step kernel.
+template <typename T, int W>
+__device__ __forceinline__ void load_chunk(const T *p, T (&v)[W]) {
+    static_assert(sizeof(T) * W == 16 || sizeof(T) * W == 32, "16- or 32-byte chunks");
+    if constexpr (sizeof(T) * W == 16) {
+        load16(p, v);
+    } else if constexpr (sizeof(T) == 4) {
+        asm volatile("ld.global.nc.v8.f32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                     : "=f"(v[0]), "=f"(v[1]), "=f"(v[2]), "=f"(v[3]), "=f"(v[4]), "=f"(v[5]),
+                       "=f"(v[6]), "=f"(v[7])
+                     : "l"(p));
+    } else {
+        asm volatile("ld.global.nc.v4.f64 {%0,%1,%2,%3}, [%4];"
+                     : "=d"(v[0]), "=d"(v[1]), "=d"(v[2]), "=d"(v[3])
+                     : "l"(p));
+    }
+}
+// X_{k-1}[i]: read once, then overwritten by the same thread (no L1 allocation
+// for the 32-byte form, so the stream does not evict gathered rows of X_k).
+template <typename T, int W>
+__device__ __forceinline__ void load_chunk_prev(const T *p, T (&v)[W]) {
+    if constexpr (sizeof(T) * W == 16) {
+        load16(p, v);
+    } else if constexpr (sizeof(T) == 4) {
+        asm volatile("ld.global.L1::no_allocate.v8.f32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                     : "=f"(v[0]), "=f"(v[1]), "=f"(v[2]), "=f"(v[3]), "=f"(v[4]), "=f"(v[5]),
+                       "=f"(v[6]), "=f"(v[7])
+                     : "l"(p));
+    } else {
+        asm volatile("ld.global.L1::no_allocate.v4.f64 {%0,%1,%2,%3}, [%4];"
+                     : "=d"(v[0]), "=d"(v[1]), "=d"(v[2]), "=d"(v[3])
+                     : "l"(p));
+    }
+}
+template <typename T, int W>
+__device__ __forceinline__ void store_chunk(T *p, const T (&v)[W]) {
+    if constexpr (sizeof(T) * W == 16) {
+        store16(p, v);
+    } else if constexpr (sizeof(T) == 4) {
+        asm volatile("st.global.v8.f32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};" ::"l"(p), "f"(v[0]),
+                     "f"(v[1]), "f"(v[2]), "f"(v[3]), "f"(v[4]), "f"(v[5]), "f"(v[6]), "f"(v[7]));
+    } else {
+        asm volatile("st.global.v4.f64 [%0], {%1,%2,%3,%4};" ::"l"(p), "d"(v[0]), "d"(v[1]),
+                     "d"(v[2]), "d"(v[3]));
+    }
+}
+
 // ---- start vectors (step a2) ---------------------------------------------------
 template <typename T>
 __global__ void init_vectors_kernel(T *__restrict__ x, int64_t n_rows, int ld, int n_v, int B,
@@ -288,12 +339,12 @@ __device__ __forceinline__ void block_reduce_scalar(const Acc &acc, double *out,
 // each thread first sums its row's products over its own vectors in the
 // working precision (at most 4*CPT terms, an error at the level of the FP32
 // rounding of the vectors themselves) and accumulates those row sums.
-template <typename T, int G, int CPT, bool PV>
+template <typename T, int G, int CPT, bool PV, int CB>
 __global__ void __launch_bounds__(kBlock, 3) step_kernel(const StepParams<T> p) {
-    constexpr int VPT = Traits<T>::VPT;
+    constexpr int VPT = CB / (int)sizeof(T);  // vector entries per chunk
     using Acc = typename Traits<T>::Acc;
     constexpr int TPW = 32 / G;  // teams per warp
-    constexpr int U = CPT >= 4 ? 4 : 8;  // nonzeros per gather batch (bounded registers)
+    constexpr int U = CPT * CB >= 64 ? 4 : 8;  // nonzeros per gather batch (bounded registers)
     extern __shared__ double red[];
 
     // Programmatic dependent launch: let the next step's grid be scheduled now,
@@ -349,8 +400,8 @@ __global__ void __launch_bounds__(kBlock, 3) step_kernel(const StepParams<T> p) 
         for (int cc = 0; cc < CPT; ++cc) {
             if (valid[cc]) {
                 const int off = (g + cc * G) * VPT;
-                load16(xc + roff + off, xk[cc]);
-                if (!first) load16(xn + roff + off, xo[cc]);
+                load_chunk(xc + roff + off, xk[cc]);
+                if (!first) load_chunk_prev(xn + roff + off, xo[cc]);
             }
         }
         const int nrow = row + n_teams;
@@ -376,7 +427,7 @@ __global__ void __launch_bounds__(kBlock, 3) step_kernel(const StepParams<T> p) 
                     for (int cc = 0; cc < CPT; ++cc) {
                         if (valid[cc]) {
                             T xv[VPT];
-                            load16(src + (g + cc * G) * VPT, xv);
+                            load_chunk(src + (g + cc * G) * VPT, xv);
 #pragma unroll
                             for (int j = 0; j < VPT; ++j) y[cc][j] = fma(a[u], xv[j], y[cc][j]);
                         }
@@ -398,7 +449,7 @@ __global__ void __launch_bounds__(kBlock, 3) step_kernel(const StepParams<T> p) 
                 for (int j = 0; j < VPT; ++j)
                     xnew[j] = fma(T(2), fma(-c, xk[cc][j], y[cc][j]) * inv_d, -xo[cc][j]);
             }
-            store16(xn + roff + off, xnew);
+            store_chunk(xn + roff + off, xnew);
 #pragma unroll
             for (int j = 0; j < VPT; ++j) {
                 if constexpr (PV) {
@@ -925,11 +976,16 @@ size_t staged_smem(int block, int team, int ld, int esz) {
 }
 
 template <typename T>
-StepFn<T> pick(int G, int CPT, bool per_vec) {
-#define DOS_CASE(GG, CC) \
-    if (G == GG && CPT == CC) return per_vec ? step_kernel<T, GG, CC, true> : step_kernel<T, GG, CC, false>;
-#define DOS_CASES(GG) DOS_CASE(GG, 1) DOS_CASE(GG, 2) DOS_CASE(GG, 4)
+StepFn<T> pick(int G, int CPT, bool per_vec, int cb = 16) {
+#define DOS_CASE(GG, CC, BB)                                                                  \
+    if (G == GG && CPT == CC && cb == BB)                                                    \
+        return per_vec ? step_kernel<T, GG, CC, true, BB> : step_kernel<T, GG, CC, false, BB>;
+#define DOS_CASES(GG) DOS_CASE(GG, 1, 16) DOS_CASE(GG, 2, 16) DOS_CASE(GG, 4, 16)
     DOS_CASES(1) DOS_CASES(2) DOS_CASES(4) DOS_CASES(8) DOS_CASES(16) DOS_CASES(32)
+    // 32-byte chunks: the team shapes that cover 32 to 1024 vector bytes per row
+    DOS_CASE(1, 1, 32) DOS_CASE(2, 1, 32) DOS_CASE(2, 2, 32) DOS_CASE(4, 1, 32)
+    DOS_CASE(4, 2, 32) DOS_CASE(8, 1, 32) DOS_CASE(8, 2, 32) DOS_CASE(16, 1, 32)
+    DOS_CASE(16, 2, 32) DOS_CASE(32, 1, 32)
 #undef DOS_CASES
 #undef DOS_CASE
     return nullptr;
@@ -1155,12 +1211,20 @@ void launch_make_tiles(const int32_t *row_ptr, int B, const int32_t *seg_row0,
 }
 
 bool shape_supported(int precision, const Shape &sh, int ld) {
-    const int vpt = precision == DOS_PREC_F64 ? 2 : 4;
+    const int esz = precision == DOS_PREC_F64 ? 8 : 4;
     if (sh.block != kBlock) return false;
     if (sh.team < 1 || sh.team > 32 || (sh.team & (sh.team - 1))) return false;
     if (sh.chunks != 1 && sh.chunks != 2 && sh.chunks != 4) return false;
     if (sh.tiles < 1) return false;
     if (sh.staged < 0 || sh.staged > 2) return false;
+    if (sh.cb != 16 && sh.cb != 32) return false;
+    const int vpt = sh.cb / esz;
+    if (sh.cb == 32) {  // 256-bit accesses: direct loads, rows of whole 32-byte chunks
+        if (sh.staged != 0 || ld % vpt != 0) return false;
+        if (!(precision == DOS_PREC_F64 ? (void *)pick<double>(sh.team, sh.chunks, false, 32)
+                                        : (void *)pick<float>(sh.team, sh.chunks, false, 32)))
+            return false;
+    }
     if (sh.staged == 1 &&
         !(precision == DOS_PREC_F64 ? (void *)pick_staged<double>(sh.team, sh.chunks, false)
                                     : (void *)pick_staged<float>(sh.team, sh.chunks, false)))
@@ -1204,7 +1268,7 @@ static int occupancy_t(const Shape &sh, int ld) {
         allow_smem<T>(fn, sm);
         DOS_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, sh.block, sm));
     } else {
-        auto fn = pick<T>(sh.team, sh.chunks, false);
+        auto fn = pick<T>(sh.team, sh.chunks, false, sh.cb);
         if (!fn) return 0;
         DOS_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, sh.block,
                                                                     step_smem(sh.block, ld)));
@@ -1265,7 +1329,7 @@ static void launch_step_t(const SweepArgs &a, int k, int slot, cudaStream_t s) {
     p.xc = blk[k & 1];
     p.xn = blk[(k + 1) & 1];
     p.ld = a.ld;
-    p.n_chunks = a.ld / Traits<T>::VPT;
+    p.n_chunks = a.ld / (a.shape.cb / (int)sizeof(T));
     p.pv = a.per_vec ? a.ld : 1;
     p.first = k == 0;
     p.tiles = a.tiles;
@@ -1292,7 +1356,7 @@ static void launch_step_t(const SweepArgs &a, int k, int slot, cudaStream_t s) {
         allow_smem<T>(fn, sm);
         fn<<<a.n_tiles, a.shape.block, sm, s>>>(p);
     } else {
-        auto fn = pick<T>(a.shape.team, a.shape.chunks, a.per_vec != 0);
+        auto fn = pick<T>(a.shape.team, a.shape.chunks, a.per_vec != 0, a.shape.cb);
         if (!fn) throw Error{DOS_EINVAL, "unsupported launch shape"};
         p.panel_rows = 0;
         cudaLaunchConfig_t cfg = {};

@@ -48,7 +48,7 @@ class dos_csr(C.Structure):
 
 class dos_launch(C.Structure):
     _fields_ = [("team", C.c_int32), ("chunks", C.c_int32), ("block", C.c_int32),
-                ("tiles", C.c_int32), ("staged", C.c_int32)]
+                ("tiles", C.c_int32), ("staged", C.c_int32), ("chunk_bytes", C.c_int32)]
 
 
 class dos_kpm_opts(C.Structure):
@@ -265,7 +265,8 @@ class Context:
         o.wait_limit_cycles = int(wait_limit_cycles)
         if launch:
             o.launch = dos_launch(*[int(launch.get(k, 0))
-                                    for k in ("team", "chunks", "block", "tiles", "staged")])
+                                    for k in ("team", "chunks", "block", "tiles", "staged",
+                                              "chunk_bytes")])
         return o
 
     def dos_kpm_moments(self, A: CSRArrays, lb: float, ub: float, M: int, n_v: int, seed: int,
@@ -310,7 +311,8 @@ class Context:
                                   None if seg is None else seg.ctypes.data, int(n_v), prec,
                                   C.byref(best), C.byref(ms), _stream_of(A.row_ptr)))
         return {"team": best.team, "chunks": best.chunks, "block": best.block,
-                "tiles": best.tiles, "staged": best.staged}, ms.value
+                "tiles": best.tiles, "staged": best.staged,
+                "chunk_bytes": best.chunk_bytes}, ms.value
 
     def dos_reconstruct(self, mu, M: int, damping="jackson", lb: float = -1.0, ub: float = 1.0,
                         t=None, N_t: int = 1000, phi_hat=None, phi_lambda=None,

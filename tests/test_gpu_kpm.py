@@ -179,6 +179,51 @@ def test_staged_panels_parity(ctx, precision, launch):
         assert np.all(np.abs(mu_tot - ref.mean(axis=0)) <= tol)
 
 
+@pytest.mark.parametrize("precision", ["f64", "f32"])
+@pytest.mark.parametrize("launch", [{"chunk_bytes": 32},
+                                    {"team": 4, "chunks": 2, "chunk_bytes": 32},
+                                    {"team": 8, "chunks": 1, "chunk_bytes": 32, "tiles": 7},
+                                    {"team": 16, "chunks": 2, "chunk_bytes": 32, "tiles": 500},
+                                    {"team": 2, "chunks": 2, "chunk_bytes": 32}])
+def test_wide_chunk_parity(ctx, precision, launch):
+    """32-byte chunks (256-bit loads and stores): per-vector and total moments,
+    several tile counts, n_v whose padded row is whole 32-byte chunks (64, 24 in
+    FP32; 64, 20 in FP64); shapes that do not cover the row are rejected."""
+    from paper_1308_5467_gb300 import dos
+    A = anderson_3d(13, 6.0, seed=4)
+    lb, ub = -9.6, 9.6
+    dtype = np.float64 if precision == "f64" else np.float32
+    Aw = A.astype(dtype)
+    per_chunk = 4 if precision == "f64" else 8
+    for n_v in ((64, 20) if precision == "f64" else (64, 24)):
+        if launch.get("team", 0) * launch.get("chunks", 1) * per_chunk < n_v and "team" in launch:
+            with pytest.raises(dos.DosError):
+                ctx.dos_kpm_moments(dev(Aw), lb, ub, 70, n_v, seed=5, precision=precision,
+                                    launch=launch)
+            continue
+        pv = np.empty((n_v, 71))
+        mu = ctx.dos_kpm_moments(dev(Aw), lb, ub, 70, n_v, seed=5, precision=precision,
+                                 launch=launch, mu_per_vec=pv)
+        mu_tot = ctx.dos_kpm_moments(dev(Aw), lb, ub, 70, n_v, seed=5, precision=precision,
+                                     launch=launch)
+        ref = okpm.kpm_moments_per_vector(Aw, lb, ub, 70, n_v, seed=5)
+        tol = TOL64 if precision == "f64" else tol32(70)
+        assert np.all(np.abs(pv - ref) <= tol)
+        assert np.all(np.abs(mu - ref.mean(axis=0)) <= tol)
+        assert np.all(np.abs(mu_tot - ref.mean(axis=0)) <= tol)
+
+
+def test_wide_chunks_need_whole_32_byte_rows(ctx):
+    from paper_1308_5467_gb300 import dos
+    A = anderson_3d(6, 6.0, seed=4)
+    with pytest.raises(dos.DosError):       # FP32, n_v = 20 -> rows of 80 bytes
+        ctx.dos_kpm_moments(dev(A.astype(np.float32)), -9.6, 9.6, 10, 20, seed=5,
+                            precision="f32", launch={"chunk_bytes": 32})
+    with pytest.raises(dos.DosError):       # only with direct loads
+        ctx.dos_kpm_moments(dev(A), -9.6, 9.6, 10, 16, seed=5, precision="f64",
+                            launch={"chunk_bytes": 32, "staged": 2})
+
+
 def test_bounded_wait_timeout_is_reported_and_context_survives(ctx):
     """Failure detection: the staged kernel's wait is made to run out (it
     expects bytes that never arrive); the call returns DOS_ETIMEOUT after the
