@@ -39,7 +39,12 @@ sys.path.insert(0, ROOT)
 # DRAM traffic per step-kernel launch measured by ncu (dram__bytes_read.sum +
 # dram__bytes_write.sum), keyed by (workload, precision) together with the
 # SHA-256 of the kernel source at capture time; a mismatch reports null.
-NCU_TRAFFIC = {}
+NCU_TRAFFIC = {
+    # ncu --set full, one launch of step_kernel<float,4,2,0,32> (the autotuned shape):
+    # dram__bytes_read.sum 168.94 MB + dram__bytes_write.sum 38.94 MB
+    ("anderson64", "f32"): {"bytes": 207881728, "src": "5027f03651f48b9b",
+                            "launch": {"team": 4, "chunks": 2, "staged": 1, "chunk_bytes": 32}},
+}
 
 WORKLOADS = {
     "anderson64": dict(kind="anderson", L=64, W=4.0, seed=2, M=500, n_v=64,
@@ -457,7 +462,9 @@ def main():
         achieved = alg / (launch_ms * 1e-3) / 1e9
         key = (args.workload, prec)
         tr = NCU_TRAFFIC.get(key)
-        traffic = tr["bytes"] if tr and tr["src"] == kernel_source_hash() else None
+        same_launch = tr is not None and all(tuned_shape.get(k) == v
+                                             for k, v in tr.get("launch", {}).items())
+        traffic = tr["bytes"] if tr and tr["src"] == kernel_source_hash() and same_launch else None
         roofline = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"],
                     "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"], "traffic": traffic,
                     "peak_source": peak_kind, "kernel": "step_kernel<float>",
