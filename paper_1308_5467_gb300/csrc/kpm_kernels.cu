@@ -339,7 +339,10 @@ __device__ __forceinline__ void block_reduce_scalar(const Acc &acc, double *out,
 // each thread first sums its row's products over its own vectors in the
 // working precision (at most 4*CPT terms, an error at the level of the FP32
 // rounding of the vectors themselves) and accumulates those row sums.
-template <typename T, int G, int CPT, bool PV, int CB>
+// FIRST: the step X_1 = B X_0 (no X_{k-1}; also accumulates X_0 . X_0).  Being a
+// template parameter, the 249-of-250 ordinary steps carry no branch on it, which
+// frees registers and lets the compiler schedule the gathers of a batch together.
+template <typename T, int G, int CPT, bool PV, int CB, bool FIRST>
 __global__ void __launch_bounds__(kBlock, 3) step_kernel(const StepParams<T> p) {
     constexpr int VPT = CB / (int)sizeof(T);  // vector entries per chunk
     using Acc = typename Traits<T>::Acc;
@@ -371,7 +374,7 @@ __global__ void __launch_bounds__(kBlock, 3) step_kernel(const StepParams<T> p) 
     const T *__restrict__ val = p.val;
     T *xn = p.xn;
 
-    const bool first = p.first != 0;
+    constexpr bool first = FIRST;
     constexpr int NA = PV ? CPT : 1, NJ = PV ? VPT : 1;
     Acc accR[NA][NJ], accS[NA][NJ], acc0[NA][NJ];
 #pragma unroll
@@ -979,7 +982,8 @@ template <typename T>
 StepFn<T> pick(int G, int CPT, bool per_vec, int cb = 16) {
 #define DOS_CASE(GG, CC, BB)                                                                  \
     if (G == GG && CPT == CC && cb == BB)                                                    \
-        return per_vec ? step_kernel<T, GG, CC, true, BB> : step_kernel<T, GG, CC, false, BB>;
+        return per_vec ? step_kernel<T, GG, CC, true, BB, false>                             \
+                       : step_kernel<T, GG, CC, false, BB, false>;
 #define DOS_CASES(GG) DOS_CASE(GG, 1, 16) DOS_CASE(GG, 2, 16) DOS_CASE(GG, 4, 16)
     DOS_CASES(1) DOS_CASES(2) DOS_CASES(4) DOS_CASES(8) DOS_CASES(16) DOS_CASES(32)
     // 32-byte chunks: the team shapes that cover 32 to 1024 vector bytes per row
@@ -989,6 +993,18 @@ StepFn<T> pick(int G, int CPT, bool per_vec, int cb = 16) {
 #undef DOS_CASES
 #undef DOS_CASE
     return nullptr;
+}
+
+// The first step (k = 0) of a sweep with direct loads: one fixed shape that
+// covers any panel (teams of 32 threads, 16-byte chunks: 256 floats or doubles
+// per row), the same tiles and partial-sum layout as the shape of the later steps.
+constexpr int kFirstTeam = 32;
+template <typename T>
+constexpr int first_chunks() { return sizeof(T) == 4 ? 2 : 4; }
+template <typename T>
+StepFn<T> pick_first(bool per_vec) {
+    return per_vec ? step_kernel<T, kFirstTeam, first_chunks<T>(), true, 16, true>
+                   : step_kernel<T, kFirstTeam, first_chunks<T>(), false, 16, true>;
 }
 
 size_t step_smem(int block, int ld) { return (size_t)(block / 32) * ld * sizeof(double); }
@@ -1356,8 +1372,14 @@ static void launch_step_t(const SweepArgs &a, int k, int slot, cudaStream_t s) {
         allow_smem<T>(fn, sm);
         fn<<<a.n_tiles, a.shape.block, sm, s>>>(p);
     } else {
-        auto fn = pick<T>(a.shape.team, a.shape.chunks, a.per_vec != 0, a.shape.cb);
+        auto fn = k == 0 ? pick_first<T>(a.per_vec != 0)
+                         : pick<T>(a.shape.team, a.shape.chunks, a.per_vec != 0, a.shape.cb);
         if (!fn) throw Error{DOS_EINVAL, "unsupported launch shape"};
+        if (k == 0) {
+            if (kFirstTeam * first_chunks<T>() * (16 / (int)sizeof(T)) < a.ld)
+                throw Error{DOS_EINVAL, "vector panel wider than the first-step kernel covers"};
+            p.n_chunks = a.ld / (16 / (int)sizeof(T));
+        }
         p.panel_rows = 0;
         cudaLaunchConfig_t cfg = {};
         cfg.gridDim = dim3((unsigned)a.n_tiles);
