@@ -110,10 +110,7 @@ typedef struct {
     int32_t tiles;           /* row tiles = blocks per sweep step */
     int32_t staged;          /* 1: rows of X_k / X_{k-1} loaded by the threads;
                                 2: row panels of X_k and X_{k-1} staged in shared memory
-                                by bulk asynchronous (TMA) copies;
-                                3: every gather issued as a 16-byte asynchronous copy into
-                                shared memory, two chunks of nonzeros in flight per
-                                thread (0: choose) */
+                                by bulk asynchronous (TMA) copies (0: choose) */
     int32_t chunk_bytes;     /* bytes per chunk: 16, or 32 (256-bit loads and stores;
                                 with staged 1 only, and rows of whole 32-byte chunks)
                                 (0: 16, or the autotuned choice) */

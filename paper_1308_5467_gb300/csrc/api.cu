@@ -192,7 +192,7 @@ Shape choose_shape(dos_ctx *ctx, const SweepRequest &r, const dos_csr *Adesc, in
         sh.team = o.team ? o.team : d.team;
         sh.chunks = o.chunks ? o.chunks : d.chunks;
         sh.block = o.block ? o.block : d.block;
-        DOS_REQUIRE(o.staged >= 0 && o.staged <= 3, "launch.staged must be 0, 1, 2 or 3");
+        DOS_REQUIRE(o.staged >= 0 && o.staged <= 2, "launch.staged must be 0, 1 or 2");
         sh.staged = o.staged ? o.staged - 1 : d.staged;
         DOS_REQUIRE(o.chunk_bytes == 0 || o.chunk_bytes == 16 || o.chunk_bytes == 32,
                     "launch.chunk_bytes must be 0, 16 or 32");
@@ -492,7 +492,7 @@ dos_kpm_opts default_opts() {
 }
 
 // Autotuner: for every launch shape that covers the vector block without more
-// than 2x idle lanes, and tile counts of 1x/2x/4x the resident blocks, time
+// than 2x idle lanes, and tile counts of 1x/2x/4x/8x the resident blocks, time
 // sweeps of 8 and 24 Chebyshev steps with CUDA events; the difference / 16 is
 // the per-step time (fixed per-call costs cancel).  Best of two runs.
 Shape tune_shape(dos_ctx *ctx, const dos_csr *A, int B, const int64_t *seg_rows, int n_v,
@@ -518,9 +518,9 @@ Shape tune_shape(dos_ctx *ctx, const dos_csr *A, int B, const int64_t *seg_rows,
     Shape best;
     double best_t = INFINITY;
     bool first = true;
-    // variants: direct loads, TMA panels, asynchronous gathers (16-byte chunks),
-    // and direct loads with 32-byte chunks
-    const int variants[4][2] = {{0, 16}, {1, 16}, {2, 16}, {0, 32}};
+    // variants: direct loads and TMA panels (16-byte chunks), and direct loads
+    // with 32-byte chunks
+    const int variants[3][2] = {{0, 16}, {1, 16}, {0, 32}};
     for (int G = 1; G <= 32; G <<= 1) {
         for (int C : {1, 2, 4})
         for (const auto &var : variants) {
@@ -541,7 +541,7 @@ Shape tune_shape(dos_ctx *ctx, const dos_csr *A, int B, const int64_t *seg_rows,
             if (occ <= 0) continue;
             const int teams = (256 / 32) * (32 / G);
             const int64_t max_tiles = std::max<int64_t>(B, (A->n + teams - 1) / teams);
-            for (int mult : {1, 2, 4}) {
+            for (int mult : {1, 2, 4, 8}) {
                 sh.tiles = (int)std::min<int64_t>((int64_t)ctx->num_sms * occ * mult, max_tiles);
                 double per_step = INFINITY;
                 for (int rep = 0; rep < 2; ++rep) {

@@ -82,8 +82,7 @@ struct PinnedBuffer {
 // Launch shape of the fused step kernel.
 struct Shape {
     int team = 0, chunks = 0, block = 0, tiles = 0;
-    int staged = 0;  // 0 direct loads, 1 TMA-staged row panels (step_staged_kernel),
-                     // 2 asynchronous-copy gathers (step_async_kernel)
+    int staged = 0;  // 0 direct loads, 1 TMA-staged row panels (step_staged_kernel)
     int cb = 16;     // bytes per chunk: 16, or 32 (direct loads only)
 };
 

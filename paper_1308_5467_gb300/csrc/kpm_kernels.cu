@@ -727,232 +727,9 @@ __global__ void __launch_bounds__(kBlock, 2) step_staged_kernel(const StepParams
     }
 }
 
-// ---- asynchronous-gather variant ---------------------------------------------------
-// The team walks its rows as a stream of chunks of up to U nonzeros.  For each
-// chunk every thread issues its gathers X_k[j, its columns] as 16-byte
-// asynchronous global->shared copies (cp.async) into its own slots -- plus, with
-// a row's last chunk, its X_k[i] and X_{k-1}[i] -- and consumes the chunk
-// issued one step earlier: two chunks are in flight per thread and the loads
-// hold no registers.  Each thread reads back only the slots it filled itself,
-// so cp.async.wait_group alone orders them; no barrier is needed.
-__device__ __forceinline__ void cp_async16(void *dst, const void *src) {
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 16;" ::"r"(smem_addr(dst)), "l"(src)
-                 : "memory");
-}
-__device__ __forceinline__ void cp_async16_stream(void *dst, const void *src) {
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_addr(dst)), "l"(src)
-                 : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() {
-    asm volatile("cp.async.commit_group;" ::: "memory");
-}
-template <int N>
-__device__ __forceinline__ void cp_async_wait() {
-    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
-}
-
-template <int CPT> struct AsyncU { static constexpr int value = CPT == 1 ? 8 : (CPT == 2 ? 4 : 2); };
-
-template <typename T, int G, int CPT, bool PV>
-__global__ void __launch_bounds__(kBlock, 2) step_async_kernel(const StepParams<T> p) {
-    constexpr int VPT = Traits<T>::VPT;
-    using Acc = typename Traits<T>::Acc;
-    constexpr int TPW = 32 / G;
-    constexpr int U = AsyncU<CPT>::value;
-    constexpr int SLOTS = (U + 2) * CPT;  // per stage: gathers, then X_k[i], X_{k-1}[i]
-    extern __shared__ __align__(128) unsigned char smem[];
-    const int ld = p.ld;
-    // per-thread slot area: [2 stages][SLOTS] x 16 bytes; the block reduction
-    // scratch follows all threads' slots
-    T *myslots = reinterpret_cast<T *>(smem) + (size_t)threadIdx.x * 2 * SLOTS * VPT;
-    double *red = reinterpret_cast<double *>(smem + (size_t)blockDim.x * 2 * SLOTS * 16);
-
-    const int4 tl = p.tiles[blockIdx.x];
-    const int rb = tl.x, re = tl.y, seg = tl.z;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int g = lane % G;
-    const int n_teams = (blockDim.x >> 5) * TPW;
-    const int team = warp * TPW + lane / G;
-    const int team_base = (lane / G) * G;
-    const unsigned team_mask = G == 32 ? 0xffffffffu : (((1u << G) - 1u) << team_base);
-    const T c = (T)p.seg_c[seg];
-    const T inv_d = (T)p.seg_inv_d[seg];
-    const T *__restrict__ xseg = p.xc + (size_t)p.seg_row0[seg] * ld;
-    const T *__restrict__ xc = p.xc;
-    const int32_t *__restrict__ row_ptr = p.row_ptr;
-    const int32_t *__restrict__ col_idx = p.col_idx;
-    const T *__restrict__ val = p.val;
-    T *xn = p.xn;
-    const bool first = p.first != 0;
-
-    constexpr int NA = PV ? CPT : 1, NJ = PV ? VPT : 1;
-    Acc accR[NA][NJ], accS[NA][NJ], acc0[NA][NJ];
-#pragma unroll
-    for (int cc = 0; cc < NA; ++cc)
-#pragma unroll
-        for (int j = 0; j < NJ; ++j) {
-            acc_zero(accR[cc][j]);
-            acc_zero(accS[cc][j]);
-            acc_zero(acc0[cc][j]);
-        }
-    bool valid[CPT];
-#pragma unroll
-    for (int cc = 0; cc < CPT; ++cc) valid[cc] = (g + cc * G) < p.n_chunks;
-
-    // chunk = (row, entries [e, min(e + U, e1)) of it); `last` when it ends the row
-    int cur_row = rb + team, cur_e = 0, cur_e1 = 0;
-    if (cur_row < re) {
-        cur_e = __ldg(row_ptr + cur_row);
-        cur_e1 = __ldg(row_ptr + cur_row + 1);
-    }
-    T a_cur[U], a_nxt[U];  // values of the chunk being consumed / issued
-    auto issue = [&](int row, int e, int e1, int stage, T (&a_out)[U]) {
-        int col[U];
-        team_fetch<T, G, U>(col_idx, val, e, e1, g, team_base, team_mask, col, a_out);
-        T *slot = myslots + (size_t)stage * SLOTS * VPT;
-#pragma unroll
-        for (int u = 0; u < U; ++u) {
-            if (e + u < e1) {
-                const T *src = xseg + (size_t)col[u] * ld;
-#pragma unroll
-                for (int cc = 0; cc < CPT; ++cc)
-                    if (valid[cc]) cp_async16(slot + (u * CPT + cc) * VPT, src + (g + cc * G) * VPT);
-            }
-        }
-        if (e + U >= e1) {  // last chunk of the row: its own X_k and X_{k-1} chunks too
-            const size_t roff = (size_t)row * ld;
-#pragma unroll
-            for (int cc = 0; cc < CPT; ++cc) {
-                if (!valid[cc]) continue;
-                const int off = (g + cc * G) * VPT;
-                cp_async16_stream(slot + ((U + 0) * CPT + cc) * VPT, xc + roff + off);
-                if (!first) cp_async16_stream(slot + ((U + 1) * CPT + cc) * VPT, xn + roff + off);
-            }
-        }
-        cp_async_commit();
-    };
-
-    T y[CPT][VPT];
-#pragma unroll
-    for (int cc = 0; cc < CPT; ++cc)
-#pragma unroll
-        for (int q = 0; q < VPT; ++q) y[cc][q] = T(0);
-    int stage = 0;
-    if (cur_row < re) issue(cur_row, cur_e, cur_e1, 0, a_cur);
-    while (cur_row < re) {
-        // the chunk after the current one
-        int nxt_row = cur_row, nxt_e = cur_e + U, nxt_e1 = cur_e1;
-        if (nxt_e >= cur_e1) {
-            nxt_row = cur_row + n_teams;
-            if (nxt_row < re) {
-                nxt_e = __ldg(row_ptr + nxt_row);
-                nxt_e1 = __ldg(row_ptr + nxt_row + 1);
-            }
-        }
-        const bool has_next = nxt_row < re;
-        if (has_next) {
-            issue(nxt_row, nxt_e, nxt_e1, stage ^ 1, a_nxt);
-            cp_async_wait<1>();
-        } else {
-            cp_async_wait<0>();
-        }
-        // consume the current chunk
-        const T *slot = myslots + (size_t)stage * SLOTS * VPT;
-#pragma unroll
-        for (int u = 0; u < U; ++u) {
-            if (cur_e + u < cur_e1) {
-#pragma unroll
-                for (int cc = 0; cc < CPT; ++cc) {
-                    if (valid[cc]) {
-                        T xv[VPT];
-                        load16(slot + (u * CPT + cc) * VPT, xv);
-#pragma unroll
-                        for (int q = 0; q < VPT; ++q) y[cc][q] = fma(a_cur[u], xv[q], y[cc][q]);
-                    }
-                }
-            }
-        }
-        if (cur_e + U >= cur_e1) {  // the row is complete
-            const size_t roff = (size_t)cur_row * ld;
-            T rr = T(0), ss = T(0), zz = T(0);
-#pragma unroll
-            for (int cc = 0; cc < CPT; ++cc) {
-                if (!valid[cc]) continue;
-                const int off = (g + cc * G) * VPT;
-                T xk[VPT], xo[VPT], xnew[VPT];
-                load16(slot + ((U + 0) * CPT + cc) * VPT, xk);
-                if (first) {
-#pragma unroll
-                    for (int q = 0; q < VPT; ++q) xnew[q] = fma(-c, xk[q], y[cc][q]) * inv_d;
-                } else {
-                    load16(slot + ((U + 1) * CPT + cc) * VPT, xo);
-#pragma unroll
-                    for (int q = 0; q < VPT; ++q)
-                        xnew[q] = fma(T(2), fma(-c, xk[q], y[cc][q]) * inv_d, -xo[q]);
-                }
-                store16(xn + roff + off, xnew);
-#pragma unroll
-                for (int q = 0; q < VPT; ++q) {
-                    if constexpr (PV) {
-                        acc_add_prod(accR[cc][q], xnew[q], xk[q]);
-                        acc_add_prod(accS[cc][q], xnew[q], xnew[q]);
-                        if (first) acc_add_prod(acc0[cc][q], xk[q], xk[q]);
-                    } else {
-                        rr = fma(xnew[q], xk[q], rr);
-                        ss = fma(xnew[q], xnew[q], ss);
-                        zz = fma(xk[q], xk[q], zz);
-                    }
-                    y[cc][q] = T(0);
-                }
-            }
-            if constexpr (!PV) {
-                acc_add(accR[0][0], rr);
-                acc_add(accS[0][0], ss);
-                if (first) acc_add(acc0[0][0], zz);
-            }
-        }
-        cur_row = nxt_row;
-        cur_e = nxt_e;
-        cur_e1 = nxt_e1;
-        stage ^= 1;
-#pragma unroll
-        for (int u = 0; u < U; ++u) a_cur[u] = a_nxt[u];
-    }
-    __syncthreads();
-    if constexpr (PV) {
-        double *out = p.part + (size_t)blockIdx.x * 2 * p.pv;
-        block_reduce_store<Acc, G, CPT, VPT>(accR, out, ld, p.n_chunks, p.pv, red);
-        block_reduce_store<Acc, G, CPT, VPT>(accS, out + p.pv, ld, p.n_chunks, p.pv, red);
-        if (first)
-            block_reduce_store<Acc, G, CPT, VPT>(acc0, p.part0 + (size_t)blockIdx.x * p.pv, ld,
-                                                 p.n_chunks, p.pv, red);
-    } else {
-        double *out = p.part + (size_t)blockIdx.x * 2;
-        block_reduce_scalar(accR[0][0], out, red);
-        block_reduce_scalar(accS[0][0], out + 1, red);
-        if (first) block_reduce_scalar(acc0[0][0], p.part0 + blockIdx.x, red);
-    }
-}
-
 // ---- kernel table --------------------------------------------------------------
 template <typename T>
 using StepFn = void (*)(const StepParams<T>);
-
-template <typename T>
-StepFn<T> pick_async(int G, int CPT, bool per_vec) {
-#define DOS_CASE(GG, CC)                                                                     \
-    if (G == GG && CPT == CC)                                                                \
-        return per_vec ? step_async_kernel<T, GG, CC, true> : step_async_kernel<T, GG, CC, false>;
-    DOS_CASE(4, 1) DOS_CASE(8, 1) DOS_CASE(16, 1) DOS_CASE(32, 1)
-    DOS_CASE(4, 2) DOS_CASE(8, 2) DOS_CASE(16, 2) DOS_CASE(32, 2) DOS_CASE(4, 4) DOS_CASE(8, 4)
-    DOS_CASE(32, 4)
-#undef DOS_CASE
-    return nullptr;
-}
-size_t async_smem(int block, int chunks, int ld) {
-    const int U = chunks == 1 ? 8 : (chunks == 2 ? 4 : 2);
-    return (size_t)block * 2 * (U + 2) * chunks * 16 + (size_t)(block / 32) * ld * sizeof(double);
-}
 
 template <typename T>
 StepFn<T> pick_staged(int G, int CPT, bool per_vec) {
@@ -1232,7 +1009,7 @@ bool shape_supported(int precision, const Shape &sh, int ld) {
     if (sh.team < 1 || sh.team > 32 || (sh.team & (sh.team - 1))) return false;
     if (sh.chunks != 1 && sh.chunks != 2 && sh.chunks != 4) return false;
     if (sh.tiles < 1) return false;
-    if (sh.staged < 0 || sh.staged > 2) return false;
+    if (sh.staged < 0 || sh.staged > 1) return false;
     if (sh.cb != 16 && sh.cb != 32) return false;
     const int vpt = sh.cb / esz;
     if (sh.cb == 32) {  // 256-bit accesses: direct loads, rows of whole 32-byte chunks
@@ -1244,10 +1021,6 @@ bool shape_supported(int precision, const Shape &sh, int ld) {
     if (sh.staged == 1 &&
         !(precision == DOS_PREC_F64 ? (void *)pick_staged<double>(sh.team, sh.chunks, false)
                                     : (void *)pick_staged<float>(sh.team, sh.chunks, false)))
-        return false;
-    if (sh.staged == 2 &&
-        !(precision == DOS_PREC_F64 ? (void *)pick_async<double>(sh.team, sh.chunks, false)
-                                    : (void *)pick_async<float>(sh.team, sh.chunks, false)))
         return false;
     return sh.team * sh.chunks * vpt >= ld;
 }
@@ -1275,12 +1048,6 @@ static int occupancy_t(const Shape &sh, int ld) {
         auto fn = pick_staged<T>(sh.team, sh.chunks, false);
         if (!fn) return 0;
         const size_t sm = staged_smem(sh.block, sh.team, ld, sizeof(T));
-        allow_smem<T>(fn, sm);
-        DOS_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, sh.block, sm));
-    } else if (sh.staged == 2) {
-        auto fn = pick_async<T>(sh.team, sh.chunks, false);
-        if (!fn) return 0;
-        const size_t sm = async_smem(sh.block, sh.chunks, ld);
         allow_smem<T>(fn, sm);
         DOS_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, sh.block, sm));
     } else {
@@ -1362,13 +1129,6 @@ static void launch_step_t(const SweepArgs &a, int k, int slot, cudaStream_t s) {
         if (!fn) throw Error{DOS_EINVAL, "unsupported staged launch shape"};
         p.panel_rows = staged_panel_rows(a.shape.block, a.shape.team, a.ld, sizeof(T));
         const size_t sm = staged_smem(a.shape.block, a.shape.team, a.ld, sizeof(T));
-        allow_smem<T>(fn, sm);
-        fn<<<a.n_tiles, a.shape.block, sm, s>>>(p);
-    } else if (a.shape.staged == 2) {
-        auto fn = pick_async<T>(a.shape.team, a.shape.chunks, a.per_vec != 0);
-        if (!fn) throw Error{DOS_EINVAL, "unsupported asynchronous-gather launch shape"};
-        p.panel_rows = 0;
-        const size_t sm = async_smem(a.shape.block, a.shape.chunks, a.ld);
         allow_smem<T>(fn, sm);
         fn<<<a.n_tiles, a.shape.block, sm, s>>>(p);
     } else {
