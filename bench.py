@@ -40,9 +40,9 @@ sys.path.insert(0, ROOT)
 # dram__bytes_write.sum), keyed by (workload, precision) together with the
 # SHA-256 of the kernel source at capture time; a mismatch reports null.
 NCU_TRAFFIC = {
-    # ncu --set full, one launch of step_kernel<float,4,2,0,32> (the autotuned shape):
-    # dram__bytes_read.sum 168.94 MB + dram__bytes_write.sum 38.94 MB
-    ("anderson64", "f32"): {"bytes": 207881728, "src": "5027f03651f48b9b",
+    # ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum, three launches of
+    # step_kernel<float,4,2,0,32,0> (the autotuned shape), mean read + write per launch
+    ("anderson64", "f32"): {"bytes": 203235243, "src": "85c03835d98f07aa",
                             "launch": {"team": 4, "chunks": 2, "staged": 1, "chunk_bytes": 32}},
 }
 

@@ -52,14 +52,24 @@ def test_anderson64_f64_full(ctx, anderson64, oracle_mu):
     err = np.abs(mu - pv_ref.mean(axis=0))
     print("f64 max |dmu| =", err.max())
     assert err.max() < 1e-12
+    # the launch configuration the benchmark times: the autotuner's choice, cached
+    shape, _ = ctx.dos_tune(A, 64, "f64")
+    mu_t = ctx.dos_kpm_moments(A, lb, ub, 500, 64, seed=2, precision="f64")
+    print("f64 tuned", shape, "max |dmu| =", np.abs(mu_t - pv_ref.mean(axis=0)).max())
+    assert np.abs(mu_t - pv_ref.mean(axis=0)).max() < 1e-12
 
 
 def test_anderson64_f32_full(ctx, anderson64, oracle_mu):
     from paper_1308_5467_gb300 import dos
     lb, ub, pv64, pv32 = oracle_mu
     A = dos.CSRArrays.from_synthetic(anderson64, device="cuda", dtype=np.float32)
+    bound = 2e-7 * (np.arange(501) + 1) + 1e-6
     mu = ctx.dos_kpm_moments(A, lb, ub, 500, 64, seed=2, precision="f32")
     err = np.abs(mu - pv32.mean(axis=0))
-    bound = 2e-7 * (np.arange(501) + 1) + 1e-6
     print("f32 max |dmu| =", err.max(), " vs f64 values:", np.abs(mu - pv64.mean(axis=0)).max())
     assert np.all(err <= bound)
+    # the launch configuration the benchmark times: the autotuner's choice, cached
+    shape, _ = ctx.dos_tune(A, 64, "f32")
+    mu_t = ctx.dos_kpm_moments(A, lb, ub, 500, 64, seed=2, precision="f32")
+    print("f32 tuned", shape, "max |dmu| =", np.abs(mu_t - pv32.mean(axis=0)).max())
+    assert np.all(np.abs(mu_t - pv32.mean(axis=0)) <= bound)

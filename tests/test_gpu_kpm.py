@@ -301,6 +301,23 @@ def test_graph_replay_matches_direct_launches(ctx):
         assert np.array_equal(r, direct)
 
 
+@pytest.mark.parametrize("launch", [None, {"team": 4, "chunks": 2, "chunk_bytes": 32},
+                                    {"staged": 2}])
+def test_dependent_launch_matches_plain_stream_order(ctx, launch):
+    """Programmatic dependent launch between sweep steps changes when blocks are
+    scheduled, not what they compute: bitwise equal to plain stream order, with
+    and without graph capture."""
+    from paper_1308_5467_gb300 import dos
+    A = dev(anderson_3d(11, 5.0, seed=8).astype(np.float32))
+    kw = dict(precision="f32", launch=launch)
+    ref = ctx.dos_kpm_moments(A, -9.0, 9.0, 90, 64, 6, flags=dos.DOS_OPT_NO_PDL | dos.DOS_OPT_NO_GRAPH,
+                              **kw)
+    for flags in (0, dos.DOS_OPT_NO_GRAPH, dos.DOS_OPT_NO_PDL):
+        for _ in range(3):                    # the third identical call replays a graph
+            assert np.array_equal(ctx.dos_kpm_moments(A, -9.0, 9.0, 90, 64, 6, flags=flags, **kw),
+                                  ref)
+
+
 def test_profiling_counts_step_launches(ctx):
     A = dev(laplacian_2d(30))
     ctx.dos_profile_enable(True)
