@@ -59,6 +59,18 @@ WORKLOADS = {
 }
 
 
+# Per-method settings of the methods the paper compares with KPM (run with
+# --method on the single-matrix workloads): Lanczos steps for the Lanczos DOS /
+# Haydock (the paper reaches KPM's accuracy with about half the degree), the
+# Lorentzian width for Haydock (in units of ub - lb), the DGL stop tolerance.
+METHODS = {
+    "lanczos": dict(M={"anderson64": 100, "laplacian40": 60}, precision="f64"),
+    "haydock": dict(M={"anderson64": 100, "laplacian40": 60}, precision="f64", eta_frac=0.01),
+    "kpml": dict(tol=1e-6),
+    "dgl": dict(tol=1e-6),
+}
+
+
 def make_matrix(w):
     from synthetic import anderson_3d, chung_lu_normalized_laplacian, laplacian_2d
     if w["kind"] == "anderson":
@@ -198,6 +210,8 @@ def run_reference(args):
     if w["kind"] == "batched":
         print(json.dumps({"impl": "reference", "unavailable": "batched workload has no oracle arm"}))
         return 0
+    if args.method != "kpm":
+        return run_reference_method(args, w)
     from oracle import bounds as obounds
     from oracle import kpm as okpm
     A = make_matrix(w)
@@ -228,6 +242,55 @@ def run_reference(args):
             "cpu_baseline": {"value": value, "unit": "moments/s", "cores": min(cores, nv),
                              "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": "moments/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+def run_reference_method(args, w):
+    """Reference arm for --method: the method's oracle on a sample of start vectors."""
+    from oracle import bounds as obounds
+    from oracle import lanczos_dos as old
+    from oracle import legendre as oleg
+    method = args.method
+    A = make_matrix(w)
+    lanczos = method in ("lanczos", "haydock")
+    if not lanczos and args.precision == "f32":
+        A = A.astype(np.float32)
+    M = METHODS[method]["M"][args.workload] if lanczos else w["M"]
+    lb, ub = obounds.bounds(A, "gershgorin", pad_frac=0.01)
+    cores = os.cpu_count() or 1
+    nv = 2 if lanczos else max(1, min(cores, w["n_v"]))
+
+    def one():
+        if lanczos:
+            old.lanczos_ritz(A, M, nv, w["seed"])
+        else:
+            oleg.legendre_moments_per_vector(A, lb, ub, M, nv, w["seed"], nthreads=cores)
+    if args.warmup:
+        one()
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        one()
+        times.append(time.perf_counter() - t0)
+    t = sum(times) / len(times)
+    value = A.nnz * nv * M / t
+    unit = "products/s" if lanczos else "moments/s"
+    threads = 1 if lanczos else min(cores, nv)
+    sample = (f"each step: {nv} of the {w['n_v']} start vectors of {args.workload}, "
+              f"{method} oracle (M={M}, FP64) on {threads} host threads")
+    line = {"metric": ("Lanczos block products/sec (nnz*n_v*M/s)" if lanczos
+                       else "Legendre moments/sec (nnz*n_v*M/s)"),
+            "value": value, "unit": unit, "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * t, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": args.workload, "method": method, "n": A.n, "nnz": A.nnz,
+                       "M": M, "n_v": w["n_v"], "n_v_sample": nv},
+            "impl": "reference",
+            "cpu_baseline": {"value": value, "unit": unit, "cores": threads, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": unit, "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
     return 0
@@ -343,6 +406,186 @@ def run_batched(args, w, world, rank, local, device):
     return 0
 
 
+def lanczos_spmm_bytes(n, nnz, ld):
+    """Compulsory bytes of one Lanczos block-SpMM launch (FP64): CSR once, q_j read
+    once, q_{j-1} read and w written."""
+    return nnz * 12 + 4 * (n + 1) + 3 * n * ld * 8
+
+
+def cpu_baseline_method(method, A, lb, ub, M, n_v_full, seed, target_s=10.0):
+    """The oracle of the method, as it stands, on a bounded sample of start vectors."""
+    from oracle import lanczos_dos as old
+    from oracle import legendre as oleg
+    cores = os.cpu_count() or 1
+    if method in ("lanczos", "haydock"):
+        t0 = time.perf_counter()
+        old.lanczos_ritz(A, M, 1, seed)
+        t1 = time.perf_counter() - t0
+        nv = int(max(1, min(n_v_full, target_s / max(t1, 1e-3))))
+        t0 = time.perf_counter()
+        old.lanczos_ritz(A, M, nv, seed)
+        t = time.perf_counter() - t0
+        return {"value": A.nnz * nv * M / t, "unit": "products/s", "cores": 1, "kind": "oracle",
+                "sample": f"{nv} start vectors, {M} Lanczos steps each (FP64, one thread, "
+                          f"NumPy vector updates around the C sparse product), {t:.1f} s"}
+    probe = max(1, min(cores, n_v_full))
+    t0 = time.perf_counter()
+    oleg.legendre_moments_per_vector(A, lb, ub, M, probe, seed, nthreads=cores)
+    t = time.perf_counter() - t0
+    nv = probe
+    if t < target_s / 2:
+        nv = int(min(4 * n_v_full, probe * target_s / max(t, 1e-3)))
+        nv = max(probe, (nv // cores) * cores)
+        t0 = time.perf_counter()
+        oleg.legendre_moments_per_vector(A, lb, ub, M, nv, seed, nthreads=cores)
+        t = time.perf_counter() - t0
+    return {"value": A.nnz * nv * M / t, "unit": "moments/s", "cores": min(cores, nv),
+            "kind": "oracle",
+            "sample": f"{nv} start vectors, Legendre recurrence of Algorithm DGL (M={M} "
+                      f"products per vector, FP64), {t:.1f} s on {min(cores, nv)} threads"}
+
+
+def run_method(args, w, world, rank, local, device):
+    """The paper's other estimators on the same workload and start vectors.
+
+    lanczos / haydock: a step is Gershgorin bounds, an M-step Lanczos run of the
+    n_v start vectors (block FP64 kernels), Ritz values and weights, and the
+    Gaussian-blurred (lanczos, with the smoothed error against the reference) or
+    Lorentzian-blurred (haydock, on the metric grid) DOS.  Metric: block
+    matrix-vector products per second, nnz * n_v * M / t.
+    kpml / dgl: a step is bounds, the Legendre moments (doubling Chebyshev sweep +
+    exact basis change) and the KPML or DGL smoothed error; metric as KPM."""
+    import torch
+    import torch.distributed as dist
+
+    from paper_1308_5467_gb300 import dos
+    method = args.method
+    cfg = METHODS[method]
+    if w["kind"] not in ("anderson", "laplacian"):
+        raise SystemExit(f"--method {method} runs on the single-matrix workloads "
+                         "anderson64 and laplacian40")
+    A = make_matrix(w)
+    n_v, seed = w["n_v"], w["seed"]
+    lanczos = method in ("lanczos", "haydock")
+    M = cfg["M"][args.workload] if lanczos else w["M"]
+    prec = "f64" if lanczos else args.precision
+    vdt = np.float64 if prec == "f64" else np.float32
+    Ad = dos.CSRArrays.from_synthetic(A, device=device, dtype=vdt)
+    Ad64 = dos.CSRArrays.from_synthetic(A, device=device, dtype=np.float64)
+    ctx = dos.Context(local)
+    vec_offset = rank * n_v
+    lb, ub = ctx.dos_bounds(Ad64, "gershgorin", pad_frac=0.01)
+    sigma = 0.02 * (ub - lb)
+    ref_mu = ctx.dos_kpm_moments(Ad64, lb, ub, 500, 1024, seed=seed + 1000, precision="f64")
+    if not lanczos:
+        ctx.dos_tune(Ad, n_v, prec)
+    x_grid = np.linspace(lb - 6 * sigma, ub + 6 * sigma, 4000)
+
+    def step(Acsr):
+        lo, hi = ctx.dos_bounds(Acsr, "gershgorin", pad_frac=0.01)
+        if lanczos:
+            theta, weight, _ = ctx.dos_lanczos_ritz(Acsr, M, n_v, seed)
+            if method == "lanczos":
+                return ctx.dos_points_error(theta, weight, lo, hi, sigma, ref_mu=ref_mu)
+            phi = ctx.dos_haydock_dos(theta, weight, cfg["eta_frac"] * (hi - lo), x_grid)
+            return float(phi.sum()), None
+        nu = ctx.dos_legendre_moments(Acsr, lo, hi, M, n_v, seed, precision=prec,
+                                      vec_offset=vec_offset)
+        return ctx.dos_legendre_error(nu, method, lo, hi, sigma, tol=cfg["tol"], ref_mu=ref_mu)
+
+    def timed(fn, steps, warmup, profile=False):
+        for _ in range(warmup):
+            fn()
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+        if profile:
+            ctx.dos_profile_enable(True)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        out = None
+        for _ in range(steps):
+            out = fn()
+        e1.record()
+        torch.cuda.synchronize()
+        prof = ctx.dos_profile_read() if profile else None
+        if profile:
+            ctx.dos_profile_enable(False)
+        ms = e0.elapsed_time(e1) / steps
+        if world > 1:
+            t = torch.tensor([ms], device=device, dtype=torch.float64)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms = float(t.item())
+        return ms, out, prof
+
+    with ClockSampler(gpu_id_for(local)) as clk:
+        ms, out, prof = timed(lambda: step(Ad64 if lanczos else Ad), args.steps, args.warmup,
+                              profile=True)
+    units = A.nnz * n_v * M
+    value = units * world / (ms * 1e-3)
+    peaks, peak_kind = measured_peaks()
+    launch_ms = prof["step_ms"] / max(1, prof["step_launches"])
+    if lanczos:
+        ld = (n_v + 1) // 2 * 2
+        flops = 2 * A.nnz * n_v
+        byts = lanczos_spmm_bytes(A.n, A.nnz, ld)
+        f_alu = flops / (launch_ms * 1e-3) / 1e12 / 1.25
+        f_hbm = byts / (launch_ms * 1e-3) / 1e9 / peaks["hbm_gbs"]
+        if f_alu >= f_hbm:
+            roofline = {"bound": "alu", "achieved": f_alu * 1.25, "peak": 1.25,
+                        "unit": "TFLOP/s", "frac": f_alu, "traffic": None,
+                        "peak_source": "nominal FP64 rate of GB300 (1.25 TFLOP/s)",
+                        "kernel": "lanczos_spmm_kernel", "flops_per_launch": flops,
+                        "launch_ms": launch_ms, "hbm_frac": f_hbm}
+        else:
+            roofline = {"bound": "hbm", "achieved": f_hbm * peaks["hbm_gbs"],
+                        "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": f_hbm,
+                        "traffic": None, "peak_source": peak_kind,
+                        "kernel": "lanczos_spmm_kernel", "algorithmic_bytes_per_launch": byts,
+                        "launch_ms": launch_ms, "alu_frac": f_alu}
+        metric, unit = "Lanczos block products/sec (nnz*n_v*M/s)", "products/s"
+    else:
+        alg = algorithmic_bytes_per_step(A.n, A.nnz, n_v, prec)
+        achieved = alg / (launch_ms * 1e-3) / 1e9
+        roofline = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"],
+                    "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"], "traffic": None,
+                    "peak_source": peak_kind, "kernel": "step_kernel",
+                    "algorithmic_bytes_per_launch": alg, "launch_ms": launch_ms}
+        metric, unit = "Legendre moments/sec (nnz*n_v*M/s)", "moments/s"
+
+    e2e = None
+    if not args.no_e2e:
+        rp = torch.from_numpy(A.row_ptr).pin_memory()
+        ci = torch.from_numpy(A.col_idx).pin_memory()
+        va = torch.from_numpy(A.val.astype(np.float64 if lanczos else vdt)).pin_memory()
+        Ah = dos.CSRArrays(A.n, rp, ci, va)
+        ms_e2e, _, _ = timed(lambda: step(Ah), max(3, args.steps // 2), 1)
+        h2d = 2 * (rp.numel() * 4 + ci.numel() * 4 + va.numel() * va.element_size())
+        d2h = (2 * n_v * M * 8 + 16) if lanczos else (8 * (M + 1) + 16)
+        e2e = {"value": units * world / (ms_e2e * 1e-3), "unit": unit,
+               "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms_per_step": ms_e2e}
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        Ac = A if lanczos or prec == "f64" else A.astype(np.float32)
+        cpu = cpu_baseline_method(method, Ac, lb, ub, M, n_v, seed)
+    if rank == 0:
+        line = {
+            "metric": metric, "value": value, "unit": unit, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64" if prec == "f64" else "f32+f64acc", "data": "synthetic",
+            "config": {"workload": args.workload, "method": method, "desc": w["desc"],
+                       "n": A.n, "nnz": A.nnz, "M": M, "n_v": n_v, "precision": prec,
+                       "sigma": sigma, "lb": lb, "ub": ub,
+                       "l2": "inputs larger than L2 (vector blocks of the step)"},
+            "e1": out[0], "einf": out[1], "roofline": roofline, "e2e": e2e,
+            "cpu_baseline": cpu, "gpu_launches": prof["launches"], "clocks": clk.summary(),
+        }
+        print(json.dumps(line))
+    ctx.close()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -350,6 +593,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--workload", default="anderson64", choices=sorted(WORKLOADS))
+    ap.add_argument("--method", default="kpm", choices=["kpm"] + sorted(METHODS),
+                    help="kpm (the benchmark) or one of the paper's other estimators")
     ap.add_argument("--precision", default="f32", choices=["f32", "f64"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-f64-form", action="store_true")
@@ -378,6 +623,8 @@ def main():
     device = torch.device("cuda", local)
 
     w = WORKLOADS[args.workload]
+    if args.method != "kpm":
+        return run_method(args, w, world, rank, local, device)
     if w["kind"] == "batched":
         return run_batched(args, w, world, rank, local, device)
     A = make_matrix(w)

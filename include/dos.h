@@ -150,6 +150,8 @@ const char *dos_status_string(int status);
  * just before its first and just after its last fused-step launch (per vector
  * panel) and adds the elapsed time and the number of step launches to the
  * context's counters; each sweep then synchronises its stream at the end.
+ * dos_lanczos_ritz counts the same way around each of its block-SpMM launches
+ * (its dominant kernel), as one "sweep" of M step launches.
  * dos_profile_enable resets the counters.  The paper has no counterpart: this
  * is measurement plumbing. */
 int dos_profile_enable(dos_ctx *ctx, int on);

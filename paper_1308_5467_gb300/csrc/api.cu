@@ -1063,9 +1063,19 @@ int dos_lanczos_ritz(dos_ctx *ctx, const dos_csr *Adesc, int M, int n_v, uint64_
         DOS_CUDA_TRY(cudaMemsetAsync(q1, 0, nvec * sizeof(double), s));
         double *cur = q0, *prev = q1;
         const double *val = (const double *)A.val;
+        const bool profiling = ctx->profiling;
+        if (profiling) {  // two events per step, around its block-SpMM launch
+            while ((int)ctx->prof_events.size() < 2 * M) {
+                cudaEvent_t e;
+                DOS_CUDA_TRY(cudaEventCreate(&e));
+                ctx->prof_events.push_back(e);
+            }
+        }
         for (int j = 0; j < M; ++j) {
+            if (profiling) DOS_CUDA_TRY(cudaEventRecord(ctx->prof_events[2 * j], s));
             launch_lanczos_block_spmm(A.n, ld, n_v, A.row_ptr, A.col_idx, val, cur, prev,
                                       j ? beta + (size_t)(j - 1) * ld : nullptr, part, nb, s);
+            if (profiling) DOS_CUDA_TRY(cudaEventRecord(ctx->prof_events[2 * j + 1], s));
             launch_column_sum(part, nb, ld, alpha + (size_t)j * ld, 0, s);
             launch_lanczos_block_axpy(A.n, ld, n_v, alpha + (size_t)j * ld, cur, prev, part, nb, s);
             launch_column_sum(part, nb, ld, beta + (size_t)j * ld, 1, s);
@@ -1076,6 +1086,16 @@ int dos_lanczos_ritz(dos_ctx *ctx, const dos_csr *Adesc, int M, int n_v, uint64_
         DOS_CUDA_TRY(cudaMemcpyAsync(ha.data(), alpha, ha.size() * 8, cudaMemcpyDeviceToHost, s));
         DOS_CUDA_TRY(cudaMemcpyAsync(hb.data(), beta, hb.size() * 8, cudaMemcpyDeviceToHost, s));
         DOS_CUDA_TRY(cudaStreamSynchronize(s));
+        if (profiling) {
+            for (int j = 0; j < M; ++j) {
+                float ms = 0.f;
+                DOS_CUDA_TRY(cudaEventElapsedTime(&ms, ctx->prof_events[2 * j],
+                                                  ctx->prof_events[2 * j + 1]));
+                ctx->prof_step_ms += ms;
+            }
+            ctx->prof_step_launches += M;
+            ctx->prof_sweeps += 1;
+        }
         // invariant subspace per run: beta_j <= 1e-12 * running norm estimate
         std::vector<int> mus(n_v, M);
         for (int l = 0; l < n_v; ++l) {
