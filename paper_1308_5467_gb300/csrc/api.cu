@@ -1043,12 +1043,13 @@ int dos_lanczos_ritz(dos_ctx *ctx, const dos_csr *Adesc, int M, int n_v, uint64_
         // scratch: two vector blocks | partials | alpha, beta [M][ld] | m_used | QL work | out
         const size_t nvec = (size_t)A.n * ld;
         const size_t n_dbl = 2 * nvec + (size_t)nb * ld + 2 * (size_t)M * ld +
-                             3 * (size_t)n_v * M + 2 * (size_t)n_v * M + n_v;
+                             3 * (size_t)n_v * M + 2 * (size_t)n_v * M + n_v + ld;
         double *buf = (double *)ctx->lz_buf.get(n_dbl * sizeof(double));
         double *q0 = buf, *q1 = q0 + nvec, *part = q1 + nvec, *alpha = part + (size_t)nb * ld;
         double *beta = alpha + (size_t)M * ld, *work = beta + (size_t)M * ld;
         double *th = work + 3 * (size_t)n_v * M, *wt = th + (size_t)n_v * M;
-        int *mu_dev = (int *)(wt + (size_t)n_v * M);
+        double *inv_beta = wt + (size_t)n_v * M;
+        int *mu_dev = (int *)(inv_beta + ld);
         SweepArgs a{};
         a.precision = DOS_PREC_F64;
         a.n_rows = A.n;
@@ -1076,10 +1077,10 @@ int dos_lanczos_ritz(dos_ctx *ctx, const dos_csr *Adesc, int M, int n_v, uint64_
             launch_lanczos_block_spmm(A.n, ld, n_v, A.row_ptr, A.col_idx, val, cur, prev,
                                       j ? beta + (size_t)(j - 1) * ld : nullptr, part, nb, s);
             if (profiling) DOS_CUDA_TRY(cudaEventRecord(ctx->prof_events[2 * j + 1], s));
-            launch_column_sum(part, nb, ld, alpha + (size_t)j * ld, 0, s);
+            launch_column_sum(part, nb, ld, alpha + (size_t)j * ld, nullptr, 0, s);
             launch_lanczos_block_axpy(A.n, ld, n_v, alpha + (size_t)j * ld, cur, prev, part, nb, s);
-            launch_column_sum(part, nb, ld, beta + (size_t)j * ld, 1, s);
-            launch_lanczos_block_scale(A.n, ld, beta + (size_t)j * ld, prev, ctx->num_sms, s);
+            launch_column_sum(part, nb, ld, beta + (size_t)j * ld, inv_beta, 1, s);
+            launch_lanczos_block_scale(A.n, ld, inv_beta, prev, ctx->num_sms, s);
             std::swap(cur, prev);
         }
         std::vector<double> ha((size_t)M * ld), hb((size_t)M * ld);

@@ -272,9 +272,9 @@ void launch_lanczos_block_spmm(int64_t n, int ld, int n_vec, const int32_t *row_
                                int n_blocks, cudaStream_t s);
 void launch_lanczos_block_axpy(int64_t n, int ld, int n_vec, const double *alpha, const double *q,
                                double *w, double *part, int n_blocks, cudaStream_t s);
-void launch_column_sum(const double *part, int n_blocks, int ld, double *out, int take_sqrt,
-                       cudaStream_t s);
-void launch_lanczos_block_scale(int64_t n, int ld, const double *beta, double *w, int num_sms,
+void launch_column_sum(const double *part, int n_blocks, int ld, double *out, double *inv,
+                       int take_sqrt, cudaStream_t s);
+void launch_lanczos_block_scale(int64_t n, int ld, const double *inv_beta, double *w, int num_sms,
                                 cudaStream_t s);
 void launch_unit_scale(int64_t n, int ld, int n_vec, double *q, int num_sms, cudaStream_t s);
 // work: 3 * n_vec * M doubles

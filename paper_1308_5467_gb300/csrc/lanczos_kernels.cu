@@ -79,24 +79,38 @@ __global__ void lanczos_axpy_kernel(int64_t n, int ld, const double *__restrict_
     }
 }
 
-// out[l] = sum over blocks of part[b][l] (fixed order), optionally sqrt
+// out[l] = sum over blocks of part[b][l], optionally sqrt; inv (if given) gets
+// 1 / out[l] (0 for a zero sum).  One block per column: each thread sums a
+// strided slice in order, then a fixed shuffle tree and a fixed warp order, so
+// the result is reproducible.
 __global__ void column_sum_kernel(const double *__restrict__ part, int n_blocks, int ld,
-                                  double *__restrict__ out, int take_sqrt) {
-    const int l = blockIdx.x * blockDim.x + threadIdx.x;
-    if (l >= ld) return;
+                                  double *__restrict__ out, double *__restrict__ inv,
+                                  int take_sqrt) {
+    __shared__ double sh[32];
+    const int l = blockIdx.x;
     double s = 0.0;
-    for (int b = 0; b < n_blocks; ++b) s += part[(size_t)b * ld + l];
-    out[l] = take_sqrt ? sqrt(s) : s;
+    for (int b = threadIdx.x; b < n_blocks; b += blockDim.x) s += part[(size_t)b * ld + l];
+    for (int off = 16; off > 0; off >>= 1) s += __shfl_down_sync(0xffffffffu, s, off);
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += sh[w];
+        const double v = take_sqrt ? sqrt(t) : t;
+        out[l] = v;
+        if (inv) inv[l] = v > 0.0 ? 1.0 / v : 0.0;
+    }
 }
 
-// q <- w / beta (per column; a zero beta leaves the column at zero)
-__global__ void lanczos_scale_kernel(int64_t n, int ld, const double *__restrict__ beta,
+// q <- w * (1 / beta) per column (a zero beta leaves the column at zero); the
+// reciprocal comes from column_sum_kernel, so the pass has no FP64 division.
+__global__ void lanczos_scale_kernel(int64_t n, int ld, const double *__restrict__ inv_beta,
                                      double *__restrict__ w) {
     const int64_t total = n * ld;
     for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
          t += (int64_t)gridDim.x * blockDim.x) {
-        const double b = beta[t % ld];
-        w[t] = b > 0.0 ? w[t] / b : 0.0;
+        const int l = (int)(t % ld);
+        w[t] *= inv_beta[l];
     }
 }
 
@@ -144,16 +158,22 @@ __global__ void tridiag_ritz_kernel(const double *__restrict__ alpha,
             bool underflow = false;
             for (; i >= lo; --i) {
                 const double f = s * ee[i], b = c * ee[i];
-                r = hypot(f, g);
-                ee[i + 1] = r;
-                if (r == 0.0) {
+                // r = hypot(f, g), s = f / r, c = g / r through one reciprocal square
+                // root (FP64 division and hypot are long dependent sequences here);
+                // |f|, |g| are of the order of the entries of T, far from overflow.
+                const double h2 = fma(f, f, g * g);
+                if (h2 == 0.0) {
+                    ee[i + 1] = 0.0;
                     dd[i + 1] -= p;
                     ee[mm] = 0.0;
                     underflow = true;
                     break;
                 }
-                s = f / r;
-                c = g / r;
+                const double ir = rsqrt(h2);
+                r = h2 * ir;
+                ee[i + 1] = r;
+                s = f * ir;
+                c = g * ir;
                 g = dd[i + 1] - p;
                 r = (dd[i] - g) * s + 2.0 * c * b;
                 p = s * r;
@@ -258,17 +278,17 @@ void launch_lanczos_block_axpy(int64_t n, int ld, int n_vec, const double *alpha
     DOS_LAUNCHED();
 }
 
-void launch_column_sum(const double *part, int n_blocks, int ld, double *out, int take_sqrt,
-                       cudaStream_t s) {
-    column_sum_kernel<<<(ld + 127) / 128, 128, 0, s>>>(part, n_blocks, ld, out, take_sqrt);
+void launch_column_sum(const double *part, int n_blocks, int ld, double *out, double *inv,
+                       int take_sqrt, cudaStream_t s) {
+    column_sum_kernel<<<ld, 256, 0, s>>>(part, n_blocks, ld, out, inv, take_sqrt);
     DOS_LAUNCHED();
 }
 
-void launch_lanczos_block_scale(int64_t n, int ld, const double *beta, double *w, int num_sms,
+void launch_lanczos_block_scale(int64_t n, int ld, const double *inv_beta, double *w, int num_sms,
                                 cudaStream_t s) {
     int64_t g = (n * ld + kThreads - 1) / kThreads;
     if (g > (int64_t)num_sms * 16) g = (int64_t)num_sms * 16;
-    lanczos_scale_kernel<<<(int)std::max<int64_t>(g, 1), kThreads, 0, s>>>(n, ld, beta, w);
+    lanczos_scale_kernel<<<(int)std::max<int64_t>(g, 1), kThreads, 0, s>>>(n, ld, inv_beta, w);
     DOS_LAUNCHED();
 }
 
