@@ -70,6 +70,23 @@ def test_laplacian_40x40_f64_full_config(ctx):
 
 
 @pytest.mark.parametrize("precision", ["f64", "f32"])
+def test_matrix_without_nonzeros(ctx, precision):
+    """nnz = 0: every eigenvalue is 0, so for any start vectors mu_k = T_k(-c/d)
+    exactly; with bounds [-1, 1], T_k(0) = cos(k pi / 2)."""
+    from synthetic.matrices import CSR
+    n = 50
+    A = CSR(n, np.zeros(n + 1, dtype=np.int32), np.zeros(0, dtype=np.int32),
+            np.zeros(0, dtype=np.float64), {"family": "zero"})
+    dtype = np.float64 if precision == "f64" else np.float32
+    mu = ctx.dos_kpm_moments(dev(A, dtype), -1.0, 1.0, 9, 5, seed=3, precision=precision)
+    assert np.array_equal(mu, np.round(np.cos(np.arange(10) * np.pi / 2)))
+    ref = okpm.kpm_moments(A, -1.0, 1.0, 9, 5, seed=3)
+    assert np.array_equal(ref, mu)
+    lb, ub = ctx.dos_bounds(dev(A, dtype), "gershgorin", pad_frac=0.01)
+    assert (lb, ub) == (-0.5, 0.5)           # a single eigenvalue gets +-0.5
+
+
+@pytest.mark.parametrize("precision", ["f64", "f32"])
 @pytest.mark.parametrize("n,M,n_v", [(1, 5, 3), (37, 0, 4), (37, 1, 4), (37, 2, 7), (97, 33, 1),
                                      (97, 64, 20), (300, 81, 33), (513, 50, 64)])
 def test_random_ragged_parity(ctx, precision, n, M, n_v):
