@@ -535,13 +535,13 @@ def run_method(args, w, world, rank, local, device):
             roofline = {"bound": "alu", "achieved": f_alu * 1.25, "peak": 1.25,
                         "unit": "TFLOP/s", "frac": f_alu, "traffic": None,
                         "peak_source": "nominal FP64 rate of GB300 (1.25 TFLOP/s)",
-                        "kernel": "lanczos_spmm_kernel", "flops_per_launch": flops,
+                        "kernel": "lanczos_team_spmm_kernel", "flops_per_launch": flops,
                         "launch_ms": launch_ms, "hbm_frac": f_hbm}
         else:
             roofline = {"bound": "hbm", "achieved": f_hbm * peaks["hbm_gbs"],
                         "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": f_hbm,
                         "traffic": None, "peak_source": peak_kind,
-                        "kernel": "lanczos_spmm_kernel", "algorithmic_bytes_per_launch": byts,
+                        "kernel": "lanczos_team_spmm_kernel", "algorithmic_bytes_per_launch": byts,
                         "launch_ms": launch_ms, "alu_frac": f_alu}
         metric, unit = "Lanczos block products/sec (nnz*n_v*M/s)", "products/s"
     else:

@@ -1039,7 +1039,9 @@ int dos_lanczos_ritz(dos_ctx *ctx, const dos_csr *Adesc, int M, int n_v, uint64_
         SegDev seg = upload_segments(ctx, row0, tb, {0.0}, {1.0}, s);
         validate_on_device(ctx, A, 1, seg.row0, s);
         const int ld = (n_v + 1) / 2 * 2;
-        const int nb = lanczos_blocks(ctx->num_sms, A.n, ld);
+        const int nb_axpy = lanczos_blocks(ctx->num_sms, A.n, ld);
+        const int nb_spmm = lanczos_team_blocks(ctx->num_sms, A.n, ld);
+        const int nb = std::max(nb_axpy, nb_spmm);  // rows of the partial-sum buffer
         // scratch: two vector blocks | partials | alpha, beta [M][ld] | m_used | QL work | out
         const size_t nvec = (size_t)A.n * ld;
         const size_t n_dbl = 2 * nvec + (size_t)nb * ld + 2 * (size_t)M * ld +
@@ -1074,12 +1076,13 @@ int dos_lanczos_ritz(dos_ctx *ctx, const dos_csr *Adesc, int M, int n_v, uint64_
         }
         for (int j = 0; j < M; ++j) {
             if (profiling) DOS_CUDA_TRY(cudaEventRecord(ctx->prof_events[2 * j], s));
-            launch_lanczos_block_spmm(A.n, ld, n_v, A.row_ptr, A.col_idx, val, cur, prev,
-                                      j ? beta + (size_t)(j - 1) * ld : nullptr, part, nb, s);
+            launch_lanczos_team_spmm(A.n, ld, A.row_ptr, A.col_idx, val, cur, prev,
+                                     j ? beta + (size_t)(j - 1) * ld : nullptr, part, nb_spmm, s);
             if (profiling) DOS_CUDA_TRY(cudaEventRecord(ctx->prof_events[2 * j + 1], s));
-            launch_column_sum(part, nb, ld, alpha + (size_t)j * ld, nullptr, 0, s);
-            launch_lanczos_block_axpy(A.n, ld, n_v, alpha + (size_t)j * ld, cur, prev, part, nb, s);
-            launch_column_sum(part, nb, ld, beta + (size_t)j * ld, inv_beta, 1, s);
+            launch_column_sum(part, nb_spmm, ld, alpha + (size_t)j * ld, nullptr, 0, s);
+            launch_lanczos_block_axpy(A.n, ld, n_v, alpha + (size_t)j * ld, cur, prev, part,
+                                      nb_axpy, s);
+            launch_column_sum(part, nb_axpy, ld, beta + (size_t)j * ld, inv_beta, 1, s);
             launch_lanczos_block_scale(A.n, ld, inv_beta, prev, ctx->num_sms, s);
             std::swap(cur, prev);
         }

@@ -265,11 +265,14 @@ void launch_dgl(const double *nu, int M, double c, double d, double sigma, doubl
                 cudaStream_t s);
 
 // Lanczos DOS (block of n_vec independent runs, FP64)
+// Block product with the fused step's team mapping (kpm_kernels.cu): w = A q -
+// beta_prev q_prev over q_prev, per-block alpha partials [n_blocks][ld].
+int lanczos_team_blocks(int num_sms, int64_t n, int ld);
+void launch_lanczos_team_spmm(int64_t n, int ld, const int32_t *row_ptr, const int32_t *col_idx,
+                              const double *val, const double *q, double *qprev_w,
+                              const double *beta_prev, double *part, int n_blocks,
+                              cudaStream_t s);
 int lanczos_blocks(int num_sms, int64_t n, int ld);
-void launch_lanczos_block_spmm(int64_t n, int ld, int n_vec, const int32_t *row_ptr,
-                               const int32_t *col_idx, const double *val, const double *q,
-                               double *qprev_w, const double *beta_prev, double *part,
-                               int n_blocks, cudaStream_t s);
 void launch_lanczos_block_axpy(int64_t n, int ld, int n_vec, const double *alpha, const double *q,
                                double *w, double *part, int n_blocks, cudaStream_t s);
 void launch_column_sum(const double *part, int n_blocks, int ld, double *out, double *inv,

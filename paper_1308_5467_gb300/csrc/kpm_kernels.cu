@@ -1156,6 +1156,136 @@ static void launch_step_t(const SweepArgs &a, int k, int slot, cudaStream_t s) {
     DOS_LAUNCHED();
 }
 
+// ---- block Lanczos product (Section 3.2.1) with the fused step's data mapping -----
+// w = A q_j - beta_{j-1} q_{j-1} for n_vec runs at once (FP64), written over
+// q_{j-1}, and per-block partial sums of alpha_j = q_j . w per column.  A team
+// of G threads shares a matrix row, each thread owning CPT chunks of CB bytes of
+// the row of Q; CSR entries are fetched once per team and shared by shuffles.
+template <int G, int CPT, int CB>
+__global__ void __launch_bounds__(kBlock, 3) lanczos_team_spmm_kernel(
+    int64_t n, int ld, const int32_t *__restrict__ row_ptr, const int32_t *__restrict__ col_idx,
+    const double *__restrict__ val, const double *__restrict__ q, double *__restrict__ qprev_w,
+    const double *__restrict__ beta_prev, double *__restrict__ part) {
+    constexpr int VPT = CB / 8;
+    constexpr int TPW = 32 / G;
+    constexpr int U = CPT * CB >= 64 ? 4 : 8;
+    extern __shared__ double red[];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int g = lane % G;
+    const int n_teams = (blockDim.x >> 5) * TPW;
+    const int team = warp * TPW + lane / G;
+    const int team_base = (lane / G) * G;
+    const unsigned team_mask = G == 32 ? 0xffffffffu : (((1u << G) - 1u) << team_base);
+    const int n_chunks = ld / VPT;
+    bool valid[CPT];
+    double bp[CPT][VPT], acc[CPT][VPT];
+#pragma unroll
+    for (int cc = 0; cc < CPT; ++cc) {
+        valid[cc] = (g + cc * G) < n_chunks;
+#pragma unroll
+        for (int j = 0; j < VPT; ++j) {
+            bp[cc][j] = (beta_prev && valid[cc]) ? beta_prev[(g + cc * G) * VPT + j] : 0.0;
+            acc[cc][j] = 0.0;
+        }
+    }
+    for (int64_t row = (int64_t)blockIdx.x * n_teams + team; row < n;
+         row += (int64_t)gridDim.x * n_teams) {
+        const size_t roff = (size_t)row * ld;
+        const int e0 = __ldg(row_ptr + row), e1 = __ldg(row_ptr + row + 1);
+        double xk[CPT][VPT], xo[CPT][VPT], y[CPT][VPT];
+#pragma unroll
+        for (int cc = 0; cc < CPT; ++cc) {
+            if (valid[cc]) {
+                const int off = (g + cc * G) * VPT;
+                load_chunk(q + roff + off, xk[cc]);
+                load_chunk_prev(qprev_w + roff + off, xo[cc]);
+            }
+#pragma unroll
+            for (int j = 0; j < VPT; ++j) y[cc][j] = 0.0;
+        }
+        for (int e = e0; e < e1; e += U) {
+            int col[U];
+            double a[U];
+            team_fetch<double, G, U>(col_idx, val, e, e1, g, team_base, team_mask, col, a);
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                if (e + u < e1) {
+                    const double *src = q + (size_t)col[u] * ld;
+#pragma unroll
+                    for (int cc = 0; cc < CPT; ++cc) {
+                        if (valid[cc]) {
+                            double xv[VPT];
+                            load_chunk(src + (g + cc * G) * VPT, xv);
+#pragma unroll
+                            for (int j = 0; j < VPT; ++j) y[cc][j] = fma(a[u], xv[j], y[cc][j]);
+                        }
+                    }
+                }
+            }
+        }
+#pragma unroll
+        for (int cc = 0; cc < CPT; ++cc) {
+            if (!valid[cc]) continue;
+            double w[VPT];
+#pragma unroll
+            for (int j = 0; j < VPT; ++j) {
+                w[j] = y[cc][j] - bp[cc][j] * xo[cc][j];
+                acc[cc][j] = fma(xk[cc][j], w[j], acc[cc][j]);
+            }
+            store_chunk(qprev_w + roff + (g + cc * G) * VPT, w);
+        }
+    }
+    block_reduce_store<double, G, CPT, VPT>(acc, part + (size_t)blockIdx.x * ld, ld, n_chunks, ld,
+                                            red);
+}
+
+using LanczosFn = void (*)(int64_t, int, const int32_t *, const int32_t *, const double *,
+                           const double *, double *, const double *, double *);
+static LanczosFn pick_lanczos(int G, int CPT, int CB) {
+#define DOS_LZ(GG, CC, BB) \
+    if (G == GG && CPT == CC && CB == BB) return lanczos_team_spmm_kernel<GG, CC, BB>;
+    DOS_LZ(1, 1, 16) DOS_LZ(2, 1, 16) DOS_LZ(4, 1, 16) DOS_LZ(8, 1, 16) DOS_LZ(16, 1, 16)
+    DOS_LZ(32, 1, 16) DOS_LZ(32, 2, 16) DOS_LZ(32, 4, 16)
+    DOS_LZ(1, 1, 32) DOS_LZ(2, 1, 32) DOS_LZ(4, 1, 32) DOS_LZ(8, 1, 32) DOS_LZ(16, 1, 32)
+    DOS_LZ(32, 1, 32) DOS_LZ(32, 2, 32)
+#undef DOS_LZ
+    return nullptr;
+}
+
+// Smallest team (then chunk count) covering the padded row: 32-byte chunks when
+// the row is whole 32-byte chunks.
+static void lanczos_shape(int ld, int *G, int *CPT, int *CB) {
+    *CB = ld % 4 == 0 ? 32 : 16;
+    const int chunks = ld / (*CB / 8);
+    int g = 1;
+    while (g < chunks && g < 32) g <<= 1;
+    int c = 1;
+    while (g * c < chunks) c <<= 1;
+    *G = g;
+    *CPT = c;
+}
+
+int lanczos_team_blocks(int num_sms, int64_t n, int ld) {
+    int G, CPT, CB;
+    lanczos_shape(ld, &G, &CPT, &CB);
+    const int64_t teams = (int64_t)(kBlock / 32) * (32 / G);
+    const int64_t b = (n + teams - 1) / teams;
+    return (int)std::max<int64_t>(1, std::min<int64_t>(b, (int64_t)num_sms * 6));
+}
+
+void launch_lanczos_team_spmm(int64_t n, int ld, const int32_t *row_ptr, const int32_t *col_idx,
+                              const double *val, const double *q, double *qprev_w,
+                              const double *beta_prev, double *part, int n_blocks,
+                              cudaStream_t s) {
+    int G, CPT, CB;
+    lanczos_shape(ld, &G, &CPT, &CB);
+    LanczosFn fn = pick_lanczos(G, CPT, CB);
+    if (!fn) throw Error{DOS_EINVAL, "no Lanczos product kernel for this vector block"};
+    fn<<<n_blocks, kBlock, step_smem(kBlock, ld), s>>>(n, ld, row_ptr, col_idx, val, q, qprev_w,
+                                                       beta_prev, part);
+    DOS_LAUNCHED();
+}
+
 void launch_step(const SweepArgs &a, int k, int slot, cudaStream_t s) {
     if (a.precision == DOS_PREC_F64) launch_step_t<double>(a, k, slot, s);
     else launch_step_t<float>(a, k, slot, s);

@@ -3,7 +3,8 @@
 // Gaussian-blurred DOS from them.  FP64 throughout.
 //
 // Block layout as in the moment sweep: Q[i*ld + l].  Step j (per vector l):
-//   w = A q_j - beta_{j-1} q_{j-1}          (SpMM pass; w overwrites q_{j-1})
+//   w = A q_j - beta_{j-1} q_{j-1}          (SpMM pass, lanczos_team_spmm_kernel in
+//                                            kpm_kernels.cu; w overwrites q_{j-1})
 //   alpha_j = q_j . w                        (per-vector partials, fixed-order reduce)
 //   w -= alpha_j q_j;  beta_j = ||w||        (vector pass + reduce)
 //   q_{j+1} = w / beta_j                     (scale pass, in place)
@@ -19,39 +20,6 @@ namespace dos {
 namespace {
 
 constexpr int kThreads = 256;
-
-// One thread per matrix row and vector pair (rows are short); ld = n_v padded to 2.
-__global__ void lanczos_spmm_kernel(int64_t n, int ld, const int32_t *__restrict__ row_ptr,
-                                    const int32_t *__restrict__ col_idx,
-                                    const double *__restrict__ val,
-                                    const double *__restrict__ q,      // q_j
-                                    double *__restrict__ qprev_w,      // q_{j-1} in, w out
-                                    const double *__restrict__ beta_prev,  // [ld] or NULL
-                                    double *__restrict__ part, int n_vec) {
-    // part layout: [blocks][ld]; each block reduces its rows per vector column
-    extern __shared__ double sh[];
-    const int cols = ld;
-    const int rows_per_block = blockDim.x / cols;  // blockDim.x is a multiple of ld
-    const int rloc = threadIdx.x / cols, l = threadIdx.x % cols;
-    double acc = 0.0;
-    for (int64_t i = (int64_t)blockIdx.x * rows_per_block + rloc; i < n;
-         i += (int64_t)gridDim.x * rows_per_block) {
-        double y = 0.0;
-        for (int e = row_ptr[i]; e < row_ptr[i + 1]; ++e) y = fma(val[e], q[(size_t)col_idx[e] * ld + l], y);
-        const size_t o = (size_t)i * ld + l;
-        const double bp = beta_prev ? beta_prev[l] : 0.0;
-        const double w = y - bp * qprev_w[o];
-        qprev_w[o] = w;
-        if (l < n_vec) acc = fma(q[o], w, acc);
-    }
-    sh[threadIdx.x] = acc;
-    __syncthreads();
-    if (threadIdx.x < cols) {
-        double s = 0.0;
-        for (int r = 0; r < rows_per_block; ++r) s += sh[r * cols + threadIdx.x];
-        part[(size_t)blockIdx.x * cols + threadIdx.x] = s;
-    }
-}
 
 // w -= alpha q (per column), partial ||w||^2 per column
 __global__ void lanczos_axpy_kernel(int64_t n, int ld, const double *__restrict__ alpha,
@@ -126,15 +94,17 @@ __global__ void unit_scale_kernel(int64_t n, int ld, int n_vec, double *__restri
 // Golub-Welsch on each run's tridiagonal T (diagonal alpha, off-diagonal beta):
 // implicit QL with Wilkinson-style shifts (the classical tql1/tql2 iteration),
 // applying every plane rotation to the first row of the eigenvector matrix only.
-// One thread per run; work arrays in local memory.
+// One warp per run (its first lane works); work arrays in global scratch.
 __global__ void tridiag_ritz_kernel(const double *__restrict__ alpha,
                                     const double *__restrict__ beta,  // [M][ld], beta[j] = ||f_{j+1}||
                                     const int *__restrict__ m_used, int M, int ld, int n_vec,
                                     double *__restrict__ d, double *__restrict__ e,
                                     double *__restrict__ z, double *__restrict__ theta,
                                     double *__restrict__ weight) {
-    const int l = blockIdx.x * blockDim.x + threadIdx.x;
-    if (l >= n_vec) return;
+    // one run per warp (lane 0): runs deflate at different points, and runs sharing a
+    // warp would execute the union of their iteration paths
+    const int l = blockIdx.x;
+    if (threadIdx.x != 0 || l >= n_vec) return;
     const int m = m_used[l];
     double *dd = d + (size_t)l * M, *ee = e + (size_t)l * M, *zz = z + (size_t)l * M;
     for (int i = 0; i < m; ++i) {
@@ -156,15 +126,21 @@ __global__ void tridiag_ritz_kernel(const double *__restrict__ alpha,
             double s = 1.0, c = 1.0, p = 0.0;
             int i = mm - 1;
             bool underflow = false;
+            // The sweep reads d[i], z[i], e[i] and rewrites d[i+1], z[i+1], e[i+1]; d[i]
+            // is next step's d[i+1] unchanged and z[i] is passed on rotated, so both are
+            // carried in registers and the loads stay off the dependent FP64 chain.
+            double d_next = dd[mm], z_next = zz[mm];  // d[i+1], z[i+1] of step i
             for (; i >= lo; --i) {
-                const double f = s * ee[i], b = c * ee[i];
+                const double e_i = ee[i], d_i = dd[i], z_i = zz[i];
+                const double f = s * e_i, b = c * e_i;
                 // r = hypot(f, g), s = f / r, c = g / r through one reciprocal square
                 // root (FP64 division and hypot are long dependent sequences here);
                 // |f|, |g| are of the order of the entries of T, far from overflow.
                 const double h2 = fma(f, f, g * g);
                 if (h2 == 0.0) {
                     ee[i + 1] = 0.0;
-                    dd[i + 1] -= p;
+                    dd[i + 1] = d_next - p;
+                    zz[i + 1] = z_next;
                     ee[mm] = 0.0;
                     underflow = true;
                     break;
@@ -174,16 +150,17 @@ __global__ void tridiag_ritz_kernel(const double *__restrict__ alpha,
                 ee[i + 1] = r;
                 s = f * ir;
                 c = g * ir;
-                g = dd[i + 1] - p;
-                r = (dd[i] - g) * s + 2.0 * c * b;
+                g = d_next - p;
+                r = (d_i - g) * s + 2.0 * c * b;
                 p = s * r;
                 dd[i + 1] = g + p;
                 g = c * r - b;
-                const double zf = zz[i + 1];
-                zz[i + 1] = s * zz[i] + c * zf;
-                zz[i] = c * zz[i] - s * zf;
+                zz[i + 1] = s * z_i + c * z_next;
+                z_next = c * z_i - s * z_next;
+                d_next = d_i;
             }
             if (underflow) continue;
+            zz[lo] = z_next;
             dd[lo] -= p;
             ee[lo] = g;
             ee[mm] = 0.0;
@@ -261,16 +238,6 @@ int lanczos_blocks(int num_sms, int64_t n, int ld) {
     return (int)std::max<int64_t>(1, std::min(b, cap));
 }
 
-void launch_lanczos_block_spmm(int64_t n, int ld, int n_vec, const int32_t *row_ptr,
-                               const int32_t *col_idx, const double *val, const double *q,
-                               double *qprev_w, const double *beta_prev, double *part,
-                               int n_blocks, cudaStream_t s) {
-    const int bt = block_threads_for(ld);
-    lanczos_spmm_kernel<<<n_blocks, bt, bt * sizeof(double), s>>>(n, ld, row_ptr, col_idx, val, q,
-                                                                   qprev_w, beta_prev, part, n_vec);
-    DOS_LAUNCHED();
-}
-
 void launch_lanczos_block_axpy(int64_t n, int ld, int n_vec, const double *alpha, const double *q,
                                double *w, double *part, int n_blocks, cudaStream_t s) {
     const int bt = block_threads_for(ld);
@@ -302,8 +269,8 @@ void launch_unit_scale(int64_t n, int ld, int n_vec, double *q, int num_sms, cud
 void launch_tridiag_ritz(const double *alpha, const double *beta, const int *m_used, int M, int ld,
                          int n_vec, double *work, double *theta, double *weight, cudaStream_t s) {
     double *d = work, *e = work + (size_t)n_vec * M, *z = work + 2 * (size_t)n_vec * M;
-    tridiag_ritz_kernel<<<(n_vec + 63) / 64, 64, 0, s>>>(alpha, beta, m_used, M, ld, n_vec, d, e, z,
-                                                         theta, weight);
+    tridiag_ritz_kernel<<<n_vec, 32, 0, s>>>(alpha, beta, m_used, M, ld, n_vec, d, e, z, theta,
+                                             weight);
     DOS_LAUNCHED();
 }
 
