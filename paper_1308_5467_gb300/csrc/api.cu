@@ -1388,13 +1388,14 @@ int dos_kpml_reconstruct(dos_ctx *ctx, const double *nu, int M, double lb, doubl
         DOS_REQUIRE(!phi_lambda || (isfinite(lb) && isfinite(ub) && ub > lb), "need ub > lb");
         cudaStream_t s = (cudaStream_t)stream;
         const size_t per = (size_t)M + 1;
-        double *buf = (double *)ctx->leg_buf.get((per + 3 * (size_t)N_t) * sizeof(double));
+        double *buf = (double *)ctx->leg_buf.get((3 * per + 3 * (size_t)N_t) * sizeof(double));
         double *dnu = buf, *dt = buf + per, *dphi = dt + N_t, *dphl = dphi + N_t;
+        double *coef = dphl + N_t;
         DOS_CUDA_TRY(cudaMemcpyAsync(dnu, nu, per * sizeof(double), cudaMemcpyDefault, s));
         if (t) DOS_CUDA_TRY(cudaMemcpyAsync(dt, t, N_t * sizeof(double), cudaMemcpyDefault, s));
         const double inv_d = phi_lambda ? 1.0 / (0.5 * (ub - lb)) : 0.0;
         launch_kpml(dnu, M, t ? dt : nullptr, nullptr, N_t, inv_d, dphi,
-                    phi_lambda ? dphl : nullptr, s);
+                    phi_lambda ? dphl : nullptr, coef, s);
         copy_out(phi_t, dphi, N_t * sizeof(double), s);
         if (phi_lambda) copy_out(phi_lambda, dphl, N_t * sizeof(double), s);
         if (!is_device_ptr(phi_t) || (phi_lambda && !is_device_ptr(phi_lambda)))
@@ -1459,17 +1460,18 @@ int dos_legendre_error(dos_ctx *ctx, const double *nu, int M, int method, double
         const size_t per = (size_t)M + 1, n_ref = eig ? 0 : (size_t)M_ref + 1;
         const size_t neig = eig ? (size_t)n_eig : 0;
         // scratch: nu | ref_mu | blur_kpm scratch | approx | ref | out | eig | GL t, w, y, P
+        const size_t n_coef = 2 * ((size_t)std::max(M, N_q) + 1);
         const size_t nd = per + n_ref + (size_t)(Meff + 1) + 2 * (size_t)N_q + 2 * (size_t)N_x +
-                          2 + neig + 4 * (size_t)N_q;
+                          2 + neig + 4 * (size_t)N_q + n_coef;
         double *buf = (double *)ctx->leg_aux.get(nd * sizeof(double));
         double *dnu = buf, *dref = dnu + per, *poly = dref + n_ref;
         double *approx = poly + (Meff + 1) + 2 * (size_t)N_q, *ref = approx + N_x;
         double *out = ref + N_x, *deig = out + 2, *gt = deig + neig, *gw = gt + N_q;
-        double *gy = gw + N_q, *gP = gy + N_q;
+        double *gy = gw + N_q, *gP = gy + N_q, *coef = gP + N_q;
         DOS_CUDA_TRY(cudaMemcpyAsync(dnu, nu, per * sizeof(double), cudaMemcpyDefault, s));
         if (method == DOS_LEG_KPML) {
-            launch_gauss_legendre(N_q, c, d, gt, gw, gy, s);
-            launch_kpml(dnu, M, gt, gw, N_q, 0.0, gP, nullptr, s);
+            launch_gauss_legendre(N_q, c, d, gt, gw, gy, coef, s);
+            launch_kpml(dnu, M, gt, gw, N_q, 0.0, gP, nullptr, coef, s);
             launch_weighted_gauss(gy, gP, N_q, 1.0, sigma, nullptr, x0, h, N_x, approx, s);
         } else {
             launch_dgl(dnu, M, c, d, sigma, tol, nullptr, x0, h, N_x, approx, nullptr, s);

@@ -253,12 +253,13 @@ void launch_heat_points(const double *pts, const double *w, int64_t n_pts, doubl
 void launch_cheb_to_legendre(const double *mu, int64_t count, int M, double *h_scratch,
                              double *nu, cudaStream_t s);
 // out_t[i] = phi_L(t_i) (times w[i] when w is given; t NULL: Chebyshev nodes),
-// out_l[i] = phi_L(t_i) * inv_d when out_l is given.
+// out_l[i] = phi_L(t_i) * inv_d when out_l is given.  coef_scratch: 2 (M+1) doubles.
 void launch_kpml(const double *nu, int M, const double *t, const double *w, int N, double inv_d,
-                 double *out_t, double *out_l, cudaStream_t s);
+                 double *out_t, double *out_l, double *coef_scratch, cudaStream_t s);
 // Gauss-Legendre nodes t (ascending), weights w, positions y = c + d t (y may be NULL).
+// coef_scratch: 2 (N+1) doubles.
 void launch_gauss_legendre(int N, double c, double d, double *t, double *w, double *y,
-                           cudaStream_t s);
+                           double *coef_scratch, cudaStream_t s);
 // DGL density at x[i] (or x0 + i h when x is NULL); used may be NULL.
 void launch_dgl(const double *nu, int M, double c, double d, double sigma, double tol,
                 const double *x, double x0, double h, int N, double *phi, int *used,

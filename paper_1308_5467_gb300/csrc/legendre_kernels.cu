@@ -11,7 +11,8 @@
 // Legendre recurrence of Algorithm DGL gives in M.
 //
 // KPML: phi_L(t) = sum_k (k + 1/2) nu_k L_k(t) by the forward three-term
-// recurrence (k+1) L_{k+1} = (2k+1) t L_k - k L_{k-1} (|L_k| <= 1 on [-1, 1]).
+// recurrence (k+1) L_{k+1} = (2k+1) t L_k - k L_{k-1} (|L_k| <= 1 on [-1, 1]),
+// with the coefficients (2k+1)/(k+1) and k/(k+1) from a table.
 //
 // DGL: gamma_k(t) by Eq. gam0 and the joint recurrence of Eq. Leg3, stopped by
 // Eq. StopRecur, one thread per point.
@@ -61,11 +62,21 @@ __global__ void cheb_to_leg_kernel(const double *__restrict__ mu, int64_t count,
     }
 }
 
-__device__ __forceinline__ double kpml_at(const double *__restrict__ nu, int M, double t) {
+// ab[2k] = (2k+1)/(k+1), ab[2k+1] = k/(k+1): the recurrence coefficients, so the
+// per-point loops below need no FP64 division (a long dependent sequence here).
+__global__ void leg_coef_kernel(int K, double *__restrict__ ab) {
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < K; k += gridDim.x * blockDim.x) {
+        ab[2 * k] = (2.0 * k + 1.0) / (k + 1.0);
+        ab[2 * k + 1] = (double)k / (k + 1.0);
+    }
+}
+
+__device__ __forceinline__ double kpml_at(const double *__restrict__ nu, int M,
+                                          const double *__restrict__ ab, double t) {
     double Lp = 0.0, Lc = 1.0;      // L_{k-1}, L_k
     double s = 0.5 * nu[0];
     for (int k = 0; k < M; ++k) {
-        const double Ln = ((2.0 * k + 1.0) * t * Lc - k * Lp) / (k + 1.0);
+        const double Ln = fma(ab[2 * k] * t, Lc, -ab[2 * k + 1] * Lp);
         Lp = Lc;
         Lc = Ln;
         s = fma((k + 1.5) * nu[k + 1], Lc, s);
@@ -74,27 +85,28 @@ __device__ __forceinline__ double kpml_at(const double *__restrict__ nu, int M, 
 }
 
 // out_t[i] = phi_L(t_i) (times w[i] if given), out_l[i] = phi_L(t_i) / d.
-__global__ void kpml_kernel(const double *__restrict__ nu, int M, const double *__restrict__ t,
-                            const double *__restrict__ w, int N, double inv_d,
-                            double *__restrict__ out_t, double *__restrict__ out_l) {
+__global__ void kpml_kernel(const double *__restrict__ nu, int M, const double *__restrict__ ab,
+                            const double *__restrict__ t, const double *__restrict__ w, int N,
+                            double inv_d, double *__restrict__ out_t, double *__restrict__ out_l) {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) {
         const double ti = t ? t[i] : -cospi((i + 0.5) / (double)N);
-        const double v = kpml_at(nu, M, ti);
+        const double v = kpml_at(nu, M, ab, ti);
         out_t[i] = w ? w[i] * v : v;
         if (out_l) out_l[i] = v * inv_d;
     }
 }
 
 // Gauss-Legendre nodes (ascending) and weights on [-1, 1]; y[i] = c + d t[i].
-__global__ void gauss_legendre_kernel(int N, double c, double d, double *__restrict__ t,
-                                      double *__restrict__ w, double *__restrict__ y) {
+__global__ void gauss_legendre_kernel(int N, const double *__restrict__ ab, double c, double d,
+                                      double *__restrict__ t, double *__restrict__ w,
+                                      double *__restrict__ y) {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) {
         double x = cospi((i + 0.75) / (N + 0.5));
         double dp = 1.0;
         for (int it = 0; it < 100; ++it) {
             double p0 = 1.0, p1 = x;    // L_0, L_1
             for (int k = 1; k < N; ++k) {
-                const double p2 = ((2.0 * k + 1.0) * x * p1 - k * p0) / (k + 1.0);
+                const double p2 = fma(ab[2 * k] * x, p1, -ab[2 * k + 1] * p0);
                 p0 = p1;
                 p1 = p2;
             }
@@ -106,7 +118,7 @@ __global__ void gauss_legendre_kernel(int N, double c, double d, double *__restr
         // one more evaluation at the converged node for the weight
         double p0 = 1.0, p1 = x;
         for (int k = 1; k < N; ++k) {
-            const double p2 = ((2.0 * k + 1.0) * x * p1 - k * p0) / (k + 1.0);
+            const double p2 = fma(ab[2 * k] * x, p1, -ab[2 * k + 1] * p0);
             p0 = p1;
             p1 = p2;
         }
@@ -163,15 +175,20 @@ void launch_cheb_to_legendre(const double *mu, int64_t count, int M, double *h_s
 }
 
 void launch_kpml(const double *nu, int M, const double *t, const double *w, int N, double inv_d,
-                 double *out_t, double *out_l, cudaStream_t s) {
-    kpml_kernel<<<grid_for_points(N, 128, 152 * 16), 128, 0, s>>>(nu, M, t, w, N, inv_d, out_t,
-                                                                  out_l);
+                 double *out_t, double *out_l, double *coef_scratch, cudaStream_t s) {
+    leg_coef_kernel<<<grid_for_points(M + 1, 256, 152 * 4), 256, 0, s>>>(M + 1, coef_scratch);
+    DOS_LAUNCHED();
+    kpml_kernel<<<grid_for_points(N, 128, 152 * 16), 128, 0, s>>>(nu, M, coef_scratch, t, w, N,
+                                                                  inv_d, out_t, out_l);
     DOS_LAUNCHED();
 }
 
 void launch_gauss_legendre(int N, double c, double d, double *t, double *w, double *y,
-                           cudaStream_t s) {
-    gauss_legendre_kernel<<<grid_for_points(N, 128, 152 * 16), 128, 0, s>>>(N, c, d, t, w, y);
+                           double *coef_scratch, cudaStream_t s) {
+    leg_coef_kernel<<<grid_for_points(N + 1, 256, 152 * 4), 256, 0, s>>>(N + 1, coef_scratch);
+    DOS_LAUNCHED();
+    gauss_legendre_kernel<<<grid_for_points(N, 128, 152 * 16), 128, 0, s>>>(N, coef_scratch, c, d,
+                                                                           t, w, y);
     DOS_LAUNCHED();
 }
 
