@@ -477,8 +477,7 @@ def run_method(args, w, world, rank, local, device):
     lb, ub = ctx.dos_bounds(Ad64, "gershgorin", pad_frac=0.01)
     sigma = 0.02 * (ub - lb)
     ref_mu = ctx.dos_kpm_moments(Ad64, lb, ub, 500, 1024, seed=seed + 1000, precision="f64")
-    if not lanczos:
-        ctx.dos_tune(Ad, n_v, prec)
+    tuned_shape = ctx.dos_tune(Ad, n_v, prec)[0] if not lanczos else None
     x_grid = np.linspace(lb - 6 * sigma, ub + 6 * sigma, 4000)
 
     def step(Acsr):
@@ -576,7 +575,7 @@ def run_method(args, w, world, rank, local, device):
             "dtype": "f64" if prec == "f64" else "f32+f64acc", "data": "synthetic",
             "config": {"workload": args.workload, "method": method, "desc": w["desc"],
                        "n": A.n, "nnz": A.nnz, "M": M, "n_v": n_v, "precision": prec,
-                       "sigma": sigma, "lb": lb, "ub": ub,
+                       "sigma": sigma, "lb": lb, "ub": ub, "launch": tuned_shape,
                        "l2": "inputs larger than L2 (vector blocks of the step)"},
             "e1": out[0], "einf": out[1], "roofline": roofline, "e2e": e2e,
             "cpu_baseline": cpu, "gpu_launches": prof["launches"], "clocks": clk.summary(),

@@ -3,8 +3,8 @@
  * maps noisy low-order Chebyshev moments (mu_1..mu_{n_in} from a few start
  * vectors, as returned by dos_kpm_moments) to the density of states on a grid
  * (e.g. phi_hat at n_out Chebyshev nodes, as returned by dos_reconstruct).
- * The paper has no counterpart: it is an addition that plain Jackson-damped
- * KPM (Appendix A) serves as the fallback for and as the judge of.
+ * The paper has no counterpart: it is an addition, scored against plain
+ * Jackson-damped KPM (Appendix A) from the same few start vectors.
  *
  * Network:  h1 = relu(x W1^T + b1),  h2 = relu(h1 W2^T + b2),  y = h2 W3^T + b3
  * with W1 (n_hidden x n_in), W2 (n_hidden x n_hidden), W3 (n_out x n_hidden).
