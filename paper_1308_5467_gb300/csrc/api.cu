@@ -493,8 +493,9 @@ dos_kpm_opts default_opts() {
 
 // Autotuner: for every launch shape that covers the vector block without more
 // than 2x idle lanes, and tile counts of 1x/2x/4x/8x the resident blocks, time
-// sweeps of 8 and 24 Chebyshev steps with CUDA events; the difference / 16 is
-// the per-step time (fixed per-call costs cancel).  Best of two runs.
+// sweeps of 16 and 48 Chebyshev steps with CUDA events; the difference / 32 is
+// the per-step time (fixed per-call costs cancel).  Best of three runs (one when
+// a step takes more than 2 ms).
 Shape tune_shape(dos_ctx *ctx, const dos_csr *A, int B, const int64_t *seg_rows, int n_v,
                  int precision, double *best_ms, cudaStream_t s) {
     DOS_REQUIRE(n_v >= 1 && n_v <= 4096, "n_v must be in [1, 4096]");
@@ -511,7 +512,7 @@ Shape tune_shape(dos_ctx *ctx, const dos_csr *A, int B, const int64_t *seg_rows,
     // Timing only: the moments are discarded and the spectrum check is off, so
     // any bounds do (values may grow; the kernels' speed does not depend on them).
     std::vector<double> lb(B, -1.0), ub(B, 1.0);
-    double *mu_scratch = (double *)ctx->rec_out.get((size_t)B * 49 * sizeof(double));
+    double *mu_scratch = (double *)ctx->rec_out.get((size_t)B * 97 * sizeof(double));
     cudaEvent_t e0, e1;
     DOS_CUDA_TRY(cudaEventCreate(&e0));
     DOS_CUDA_TRY(cudaEventCreate(&e1));
@@ -544,7 +545,7 @@ Shape tune_shape(dos_ctx *ctx, const dos_csr *A, int B, const int64_t *seg_rows,
             for (int mult : {1, 2, 4, 8}) {
                 sh.tiles = (int)std::min<int64_t>((int64_t)ctx->num_sms * occ * mult, max_tiles);
                 double per_step = INFINITY;
-                for (int rep = 0; rep < 2; ++rep) {
+                for (int rep = 0; rep < 3; ++rep) {
                     float ms[2];
                     for (int which = 0; which < 2; ++which) {
                         SweepRequest r;
@@ -552,7 +553,7 @@ Shape tune_shape(dos_ctx *ctx, const dos_csr *A, int B, const int64_t *seg_rows,
                         r.seg_rows = rows;
                         r.lb = lb;
                         r.ub = ub;
-                        r.M = which ? 48 : 16;
+                        r.M = which ? 96 : 32;
                         r.n_v = pw;
                         r.seed = 1;
                         r.precision = precision;
@@ -573,7 +574,8 @@ Shape tune_shape(dos_ctx *ctx, const dos_csr *A, int B, const int64_t *seg_rows,
                         DOS_CUDA_TRY(cudaEventElapsedTime(&ms[which], e0, e1));
                         first = false;
                     }
-                    per_step = std::min(per_step, (double)(ms[1] - ms[0]) / 16.0);
+                    per_step = std::min(per_step, (double)(ms[1] - ms[0]) / 32.0);
+                    if (per_step > 2.0) break;  // large problems: one repetition is enough
                 }
                 if (getenv("DOS_TUNE_VERBOSE"))
                     fprintf(stderr,
