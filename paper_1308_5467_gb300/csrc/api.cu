@@ -492,7 +492,7 @@ dos_kpm_opts default_opts() {
 }
 
 // Autotuner: for every launch shape that covers the vector block without more
-// than 2x idle lanes, and tile counts of 1x/2x/4x/8x/16x the resident blocks, time
+// than 2x idle lanes, and tile counts of 1x to 32x the resident blocks, time
 // sweeps of 16 and 48 Chebyshev steps with CUDA events; the difference / 32 is
 // the per-step time (fixed per-call costs cancel).  Best of three runs (one when
 // a step takes more than 2 ms).
@@ -542,7 +542,7 @@ Shape tune_shape(dos_ctx *ctx, const dos_csr *A, int B, const int64_t *seg_rows,
             if (occ <= 0) continue;
             const int teams = (256 / 32) * (32 / G);
             const int64_t max_tiles = std::max<int64_t>(B, (A->n + teams - 1) / teams);
-            for (int mult : {1, 2, 4, 8, 16}) {
+            for (int mult : {1, 2, 4, 8, 16, 32}) {
                 sh.tiles = (int)std::min<int64_t>((int64_t)ctx->num_sms * occ * mult, max_tiles);
                 double per_step = INFINITY;
                 for (int rep = 0; rep < 3; ++rep) {
