@@ -1,0 +1,39 @@
+"""The benchmark's JSON contract, checked on the CPU through its reference arm
+(the oracle timed on the host cores) on the small Laplacian workload."""
+import json
+import os
+import subprocess
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+KEYS = {"metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step",
+        "higher_is_better", "scaling", "vs_baseline", "dtype", "data", "config", "impl",
+        "cpu_baseline", "e2e"}
+
+
+def run_bench(*args):
+    out = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), *args],
+                         capture_output=True, text=True, timeout=600, cwd=ROOT)
+    assert out.returncode == 0, out.stderr
+    return json.loads(out.stdout.strip().splitlines()[-1])
+
+
+@pytest.mark.parametrize("method", ["kpm", "lanczos", "dgl"])
+def test_reference_arm_line(method):
+    line = run_bench("--impl", "reference", "--workload", "laplacian40", "--method", method,
+                     "--steps", "1", "--warmup", "1")
+    assert KEYS <= set(line)
+    assert line["impl"] == "reference" and line["value"] > 0
+    assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["value"] == line["value"]
+    assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["e2e"]["value"] == line["value"]
+    assert line["config"]["workload"] == "laplacian40"
+
+
+def test_algorithmic_bytes_formula():
+    sys.path.insert(0, ROOT)
+    import bench
+    # Anderson 64^3, n_v = 64: CSR 1,835,008 x (4 + 4) + 4 (n + 1), three blocks of n x 64 floats
+    assert bench.algorithmic_bytes_per_step(262144, 1835008, 64, "f32") == 217055236
+    assert bench.fma_per_step(262144, 1835008, 64) == 1835008 * 64 + 4 * 262144 * 64
