@@ -599,85 +599,6 @@ Shape tune_shape(dos_ctx *ctx, const dos_csr *A, int B, const int64_t *seg_rows,
     return best;
 }
 
-// Host-side eigen-analysis of the Lanczos tridiagonal T (alpha on the diagonal,
-// beta off it): extreme eigenvalues by Sturm-sequence bisection, the matching
-// unit eigenvectors by inverse iteration with a dense partially pivoted LU.
-int sturm_count(const std::vector<double> &al, const std::vector<double> &be, double x) {
-    int cnt = 0;
-    double d = 1.0;
-    for (size_t i = 0; i < al.size(); ++i) {
-        const double b2 = i ? be[i - 1] * be[i - 1] : 0.0;
-        d = (al[i] - x) - (i ? b2 / d : 0.0);
-        if (d == 0.0) d = -1e-300;
-        if (d < 0.0) ++cnt;
-    }
-    return cnt;  // eigenvalues < x
-}
-
-double bisect_eig(const std::vector<double> &al, const std::vector<double> &be, int idx) {
-    const size_t k = al.size();
-    double lo = INFINITY, hi = -INFINITY;
-    for (size_t i = 0; i < k; ++i) {
-        const double r = (i ? fabs(be[i - 1]) : 0.0) + (i + 1 < k ? fabs(be[i]) : 0.0);
-        lo = std::min(lo, al[i] - r);
-        hi = std::max(hi, al[i] + r);
-    }
-    const double scale = std::max(fabs(lo), fabs(hi)) + 1e-300;
-    for (int it = 0; it < 2000 && hi - lo > 2e-16 * scale; ++it) {
-        const double mid = 0.5 * (lo + hi);
-        if (mid <= lo || mid >= hi) break;
-        if (sturm_count(al, be, mid) > idx) hi = mid; else lo = mid;
-    }
-    return 0.5 * (lo + hi);
-}
-
-std::vector<double> inverse_iteration(const std::vector<double> &al, const std::vector<double> &be,
-                                      double theta) {
-    const int k = (int)al.size();
-    double nrm = 0.0;
-    for (int i = 0; i < k; ++i) nrm = std::max(nrm, fabs(al[i]) + (i ? fabs(be[i - 1]) : 0.0) + (i + 1 < k ? fabs(be[i]) : 0.0));
-    const double shift = theta + 1e-13 * (nrm + 1e-300);
-    std::vector<double> Mx((size_t)k * k, 0.0);
-    for (int i = 0; i < k; ++i) {
-        Mx[(size_t)i * k + i] = al[i] - shift;
-        if (i + 1 < k) {
-            Mx[(size_t)i * k + i + 1] = be[i];
-            Mx[(size_t)(i + 1) * k + i] = be[i];
-        }
-    }
-    std::vector<int> piv(k);
-    for (int j = 0; j < k; ++j) {  // LU with partial pivoting
-        int p = j;
-        for (int i = j + 1; i < k; ++i)
-            if (fabs(Mx[(size_t)i * k + j]) > fabs(Mx[(size_t)p * k + j])) p = i;
-        piv[j] = p;
-        if (p != j)
-            for (int c = 0; c < k; ++c) std::swap(Mx[(size_t)j * k + c], Mx[(size_t)p * k + c]);
-        double dj = Mx[(size_t)j * k + j];
-        if (dj == 0.0) dj = Mx[(size_t)j * k + j] = 1e-300;
-        for (int i = j + 1; i < k; ++i) {
-            const double f = Mx[(size_t)i * k + j] / dj;
-            Mx[(size_t)i * k + j] = f;
-            if (f != 0.0)
-                for (int c = j + 1; c < k; ++c) Mx[(size_t)i * k + c] -= f * Mx[(size_t)j * k + c];
-        }
-    }
-    std::vector<double> x(k, 1.0 / sqrt((double)k));
-    for (int it = 0; it < 4; ++it) {
-        for (int j = 0; j < k; ++j) std::swap(x[j], x[piv[j]]);
-        for (int i = 0; i < k; ++i)
-            for (int c = 0; c < i; ++c) x[i] -= Mx[(size_t)i * k + c] * x[c];
-        for (int i = k - 1; i >= 0; --i) {
-            for (int c = i + 1; c < k; ++c) x[i] -= Mx[(size_t)i * k + c] * x[c];
-            x[i] /= Mx[(size_t)i * k + i];
-        }
-        double s = 0.0;
-        for (double v : x) s += v * v;
-        s = sqrt(s);
-        for (double &v : x) v /= s;
-    }
-    return x;
-}
 
 }  // namespace
 
@@ -922,34 +843,17 @@ int dos_bounds(dos_ctx *ctx, const dos_csr *Adesc, int method, int steps, uint64
                 launch_sum_final(part, nb, beta + j, 1, s);
                 if (j + 1 < k) launch_lanczos_next(A.n, beta + j, q, q_prev, w, s);
             }
-            std::vector<double> al(k), be(k);
-            DOS_CUDA_TRY(cudaMemcpyAsync(al.data(), alpha, k * sizeof(double),
-                                         cudaMemcpyDeviceToHost, s));
-            DOS_CUDA_TRY(cudaMemcpyAsync(be.data(), beta, k * sizeof(double),
-                                         cudaMemcpyDeviceToHost, s));
+            // the tridiagonal's extreme Ritz values and the last components of their
+            // unit Ritz vectors, on the device (implicit QL)
+            double *work = (double *)ctx->bnd_out.get((3 * (size_t)k + 3) * sizeof(double));
+            double *res = work + 3 * (size_t)k;
+            launch_lanczos_bounds(alpha, beta, k, work, res, s);
+            double h[3];
+            DOS_CUDA_TRY(cudaMemcpyAsync(h, res, sizeof(h), cudaMemcpyDeviceToHost, s));
             DOS_CUDA_TRY(cudaStreamSynchronize(s));
-            // An invariant subspace ends the run: beta_j <= 1e-12 * the running
-            // estimate max_{i<=j}(|alpha_i| + beta_i + beta_{i-1}) of ||A||.
-            int kk = k;
-            double scale = 0.0;
-            for (int j = 0; j < k; ++j) {
-                scale = std::max(scale, fabs(al[j]) + be[j] + (j ? be[j - 1] : 0.0));
-                if (!(be[j] > 1e-12 * scale)) {
-                    kk = j + 1;
-                    break;
-                }
-            }
-            al.resize(kk);
-            be.resize(kk);
-            for (int j = 0; j < kk; ++j)
-                DOS_REQUIRE(isfinite(al[j]) && isfinite(be[j]), "Lanczos produced non-finite values");
-            const double f = be[kk - 1];
-            std::vector<double> off(be.begin(), be.end() - 1);
-            const double tmin = bisect_eig(al, off, 0), tmax = bisect_eig(al, off, kk - 1);
-            const double ymin = kk > 1 ? fabs(inverse_iteration(al, off, tmin).back()) : 1.0;
-            const double ymax = kk > 1 ? fabs(inverse_iteration(al, off, tmax).back()) : 1.0;
-            lo = tmin - f * ymin;
-            hi = tmax + f * ymax;
+            DOS_REQUIRE(isfinite(h[0]) && isfinite(h[1]), "Lanczos produced non-finite values");
+            lo = h[0];
+            hi = h[1];
         }
         DOS_REQUIRE(isfinite(lo) && isfinite(hi), "bounds are not finite (non-finite values?)");
         const double w = hi - lo;

@@ -281,6 +281,10 @@ void launch_column_sum(const double *part, int n_blocks, int ld, double *out, do
 void launch_lanczos_block_scale(int64_t n, int ld, const double *inv_beta, double *w, int num_sms,
                                 cudaStream_t s);
 void launch_unit_scale(int64_t n, int ld, int n_vec, double *q, int num_sms, cudaStream_t s);
+// Extreme-Ritz-value bounds of a k-step Lanczos run: out = {lo, hi, steps kept};
+// work: 3 k doubles.
+void launch_lanczos_bounds(const double *alpha, const double *beta, int k, double *work,
+                           double *out, cudaStream_t s);
 // work: 3 * n_vec * M doubles
 void launch_tridiag_ritz(const double *alpha, const double *beta, const int *m_used, int M, int ld,
                          int n_vec, double *work, double *theta, double *weight, cudaStream_t s);

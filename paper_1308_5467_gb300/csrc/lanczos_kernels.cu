@@ -95,23 +95,13 @@ __global__ void unit_scale_kernel(int64_t n, int ld, int n_vec, double *__restri
 // implicit QL with Wilkinson-style shifts (the classical tql1/tql2 iteration),
 // applying every plane rotation to the first row of the eigenvector matrix only.
 // One warp per run (its first lane works); work arrays in global scratch.
-__global__ void tridiag_ritz_kernel(const double *__restrict__ alpha,
-                                    const double *__restrict__ beta,  // [M][ld], beta[j] = ||f_{j+1}||
-                                    const int *__restrict__ m_used, int M, int ld, int n_vec,
-                                    double *__restrict__ d, double *__restrict__ e,
-                                    double *__restrict__ z, double *__restrict__ theta,
-                                    double *__restrict__ weight) {
-    // one run per warp (lane 0): runs deflate at different points, and runs sharing a
-    // warp would execute the union of their iteration paths
-    const int l = blockIdx.x;
-    if (threadIdx.x != 0 || l >= n_vec) return;
-    const int m = m_used[l];
-    double *dd = d + (size_t)l * M, *ee = e + (size_t)l * M, *zz = z + (size_t)l * M;
-    for (int i = 0; i < m; ++i) {
-        dd[i] = alpha[(size_t)i * ld + l];
-        ee[i] = i + 1 < m ? beta[(size_t)i * ld + l] : 0.0;
-        zz[i] = i == 0 ? 1.0 : 0.0;
-    }
+// Implicit QL with Wilkinson-style shifts (the classical tql1/tql2 iteration) on
+// the symmetric tridiagonal (dd: diagonal, ee: off-diagonal, ee[m-1] = 0),
+// applying every plane rotation to one row zz of the eigenvector matrix (start
+// from e_1 for first components, from e_m for last components).  On return
+// dd holds the eigenvalues (unsorted) and zz that row's entries.
+__device__ void ql_one_row(int m, double *__restrict__ dd, double *__restrict__ ee,
+                           double *__restrict__ zz) {
     for (int lo = 0; lo < m; ++lo) {
         for (int iter = 0; iter < 60; ++iter) {
             int mm = lo;
@@ -166,6 +156,26 @@ __global__ void tridiag_ritz_kernel(const double *__restrict__ alpha,
             ee[mm] = 0.0;
         }
     }
+}
+
+__global__ void tridiag_ritz_kernel(const double *__restrict__ alpha,
+                                    const double *__restrict__ beta,  // [M][ld], beta[j] = ||f_{j+1}||
+                                    const int *__restrict__ m_used, int M, int ld, int n_vec,
+                                    double *__restrict__ d, double *__restrict__ e,
+                                    double *__restrict__ z, double *__restrict__ theta,
+                                    double *__restrict__ weight) {
+    // one run per warp (lane 0): runs deflate at different points, and runs sharing a
+    // warp would execute the union of their iteration paths
+    const int l = blockIdx.x;
+    if (threadIdx.x != 0 || l >= n_vec) return;
+    const int m = m_used[l];
+    double *dd = d + (size_t)l * M, *ee = e + (size_t)l * M, *zz = z + (size_t)l * M;
+    for (int i = 0; i < m; ++i) {
+        dd[i] = alpha[(size_t)i * ld + l];
+        ee[i] = i + 1 < m ? beta[(size_t)i * ld + l] : 0.0;
+        zz[i] = i == 0 ? 1.0 : 0.0;
+    }
+    ql_one_row(m, dd, ee, zz);
     for (int i = 0; i < M; ++i) {
         theta[(size_t)l * M + i] = i < m ? dd[i] : 0.0;
         weight[(size_t)l * M + i] = i < m ? zz[i] * zz[i] : 0.0;
@@ -228,6 +238,49 @@ __global__ void weighted_lorentz_kernel(const double *__restrict__ pts,
 
 int block_threads_for(int ld) { return (kThreads / ld) * ld; }  // ld <= 256
 
+// Lanczos bounds (Section 3.1.1): the run stops at an invariant subspace
+// (beta_j <= 1e-12 times the running estimate max(|alpha_i| + beta_i + beta_{i-1})
+// of ||A||); the extreme Ritz values theta of the k-step tridiagonal widened by
+// ||f|| |y_last| (f the residual, y the unit Ritz vector).  One thread.
+// out: lo, hi, and the number of steps kept.
+__global__ void lanczos_bounds_kernel(const double *__restrict__ alpha,
+                                      const double *__restrict__ beta, int k,
+                                      double *__restrict__ work, double *__restrict__ out) {
+    if (blockIdx.x != 0 || threadIdx.x != 0) return;
+    int kk = k;
+    double scale = 0.0;
+    bool finite = true;
+    for (int j = 0; j < k; ++j) {
+        finite = finite && isfinite(alpha[j]) && isfinite(beta[j]);
+        scale = fmax(scale, fabs(alpha[j]) + beta[j] + (j ? beta[j - 1] : 0.0));
+        if (!(beta[j] > 1e-12 * scale)) {
+            kk = j + 1;
+            break;
+        }
+    }
+    if (!finite) {
+        out[0] = out[1] = NAN;
+        out[2] = kk;
+        return;
+    }
+    double *dd = work, *ee = work + kk, *zz = work + 2 * kk;
+    for (int i = 0; i < kk; ++i) {
+        dd[i] = alpha[i];
+        ee[i] = i + 1 < kk ? beta[i] : 0.0;
+        zz[i] = i == kk - 1 ? 1.0 : 0.0;
+    }
+    ql_one_row(kk, dd, ee, zz);
+    int jmin = 0, jmax = 0;
+    for (int i = 1; i < kk; ++i) {
+        if (dd[i] < dd[jmin]) jmin = i;
+        if (dd[i] > dd[jmax]) jmax = i;
+    }
+    const double f = beta[kk - 1];
+    out[0] = dd[jmin] - f * fabs(zz[jmin]);
+    out[1] = dd[jmax] + f * fabs(zz[jmax]);
+    out[2] = kk;
+}
+
 }  // namespace
 
 int lanczos_blocks(int num_sms, int64_t n, int ld) {
@@ -286,6 +339,12 @@ void launch_weighted_gauss(const double *pts, const double *w, int64_t n_pts, do
                            double *out, cudaStream_t s) {
     weighted_gauss_kernel<<<N_x < 65535 ? N_x : 65535, 256, 0, s>>>(pts, w, n_pts, scale, sigma, x,
                                                                     x0, h, N_x, out);
+    DOS_LAUNCHED();
+}
+
+void launch_lanczos_bounds(const double *alpha, const double *beta, int k, double *work,
+                           double *out, cudaStream_t s) {
+    lanczos_bounds_kernel<<<1, 32, 0, s>>>(alpha, beta, k, work, out);
     DOS_LAUNCHED();
 }
 
