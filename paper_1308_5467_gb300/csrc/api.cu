@@ -992,9 +992,13 @@ int dos_lanczos_ritz(dos_ctx *ctx, const dos_csr *Adesc, int M, int n_v, uint64_
             launch_lanczos_block_scale(A.n, ld, inv_beta, prev, ctx->num_sms, s);
             std::swap(cur, prev);
         }
-        std::vector<double> ha((size_t)M * ld), hb((size_t)M * ld);
-        DOS_CUDA_TRY(cudaMemcpyAsync(ha.data(), alpha, ha.size() * 8, cudaMemcpyDeviceToHost, s));
-        DOS_CUDA_TRY(cudaMemcpyAsync(hb.data(), beta, hb.size() * 8, cudaMemcpyDeviceToHost, s));
+        // steps kept per run (invariant-subspace rule) and the Ritz pairs, on the device
+        launch_lanczos_steps(alpha, beta, M, ld, n_v, mu_dev, s);
+        launch_tridiag_ritz(alpha, beta, mu_dev, M, ld, n_v, work, th, wt, s);
+        copy_out(theta, th, (size_t)n_v * M * sizeof(double), s);
+        copy_out(weight, wt, (size_t)n_v * M * sizeof(double), s);
+        std::vector<int> mus(n_v);
+        DOS_CUDA_TRY(cudaMemcpyAsync(mus.data(), mu_dev, n_v * sizeof(int), cudaMemcpyDeviceToHost, s));
         DOS_CUDA_TRY(cudaStreamSynchronize(s));
         if (profiling) {
             for (int j = 0; j < M; ++j) {
@@ -1006,26 +1010,8 @@ int dos_lanczos_ritz(dos_ctx *ctx, const dos_csr *Adesc, int M, int n_v, uint64_
             ctx->prof_step_launches += M;
             ctx->prof_sweeps += 1;
         }
-        // invariant subspace per run: beta_j <= 1e-12 * running norm estimate
-        std::vector<int> mus(n_v, M);
-        for (int l = 0; l < n_v; ++l) {
-            double scale = 0.0;
-            for (int j = 0; j < M; ++j) {
-                const double al = ha[(size_t)j * ld + l], be = hb[(size_t)j * ld + l];
-                const double bp = j ? hb[(size_t)(j - 1) * ld + l] : 0.0;
-                DOS_REQUIRE(isfinite(al) && isfinite(be), "Lanczos produced non-finite values");
-                scale = std::max(scale, fabs(al) + be + bp);
-                if (!(be > 1e-12 * scale)) {
-                    mus[l] = j + 1;
-                    break;
-                }
-            }
-        }
-        DOS_CUDA_TRY(cudaMemcpyAsync(mu_dev, mus.data(), n_v * sizeof(int), cudaMemcpyHostToDevice, s));
-        launch_tridiag_ritz(alpha, beta, mu_dev, M, ld, n_v, work, th, wt, s);
-        copy_out(theta, th, (size_t)n_v * M * sizeof(double), s);
-        copy_out(weight, wt, (size_t)n_v * M * sizeof(double), s);
-        DOS_CUDA_TRY(cudaStreamSynchronize(s));
+        for (int l = 0; l < n_v; ++l)
+            DOS_REQUIRE(mus[l] >= 1, "Lanczos produced non-finite values");
         if (m_used) memcpy(m_used, mus.data(), n_v * sizeof(int));
     });
 }
@@ -1082,13 +1068,6 @@ int dos_points_error(dos_ctx *ctx, const double *pts, const double *wts, int64_t
         DOS_REQUIRE(eig ? n_eig >= 1 : (ref_mu != nullptr && M_ref >= 0 && M_ref <= 100000),
                     "need eigenvalues or reference moments");
         cudaStream_t s = (cudaStream_t)stream;
-        // weights are normalised by their sum on the host
-        std::vector<double> hw((size_t)n_pts);
-        DOS_CUDA_TRY(cudaMemcpyAsync(hw.data(), wts, hw.size() * 8, cudaMemcpyDefault, s));
-        DOS_CUDA_TRY(cudaStreamSynchronize(s));
-        double wsum = 0.0;
-        for (double v : hw) wsum += v;
-        DOS_REQUIRE(wsum > 0.0 && isfinite(wsum), "weights must have a positive finite sum");
         const double d = 0.5 * (ub - lb);
         const int Mr = eig ? 0 : M_ref;
         const int64_t nq64 = std::max<int64_t>(4 * (int64_t)(Mr + 1), (int64_t)ceil(40.0 * d / sigma));
@@ -1097,14 +1076,15 @@ int dos_points_error(dos_ctx *ctx, const double *pts, const double *wts, int64_t
         const size_t n_ref = eig ? 0 : (size_t)M_ref + 1;
         const size_t neig = eig ? (size_t)n_eig : 0;
         const size_t nd = 2 * (size_t)n_pts + n_ref + (size_t)(Mr + 1) + 2 * (size_t)N_q +
-                          2 * (size_t)N_x + 2 + neig;
+                          2 * (size_t)N_x + 3 + neig;
         double *buf = (double *)ctx->err_buf.get(nd * sizeof(double));
         double *dp = buf, *dw = dp + n_pts, *dref = dw + n_pts, *poly = dref + n_ref;
         double *approx = poly + (Mr + 1) + 2 * (size_t)N_q, *ref = approx + N_x, *out = ref + N_x;
-        double *deig = out + 2;
+        double *wsum = out + 2, *deig = wsum + 1;
         DOS_CUDA_TRY(cudaMemcpyAsync(dp, pts, (size_t)n_pts * 8, cudaMemcpyDefault, s));
         DOS_CUDA_TRY(cudaMemcpyAsync(dw, wts, (size_t)n_pts * 8, cudaMemcpyDefault, s));
-        launch_weighted_gauss(dp, dw, n_pts, 1.0 / wsum, sigma, nullptr, x0, h, N_x, approx, s);
+        launch_normalize_weights(dw, n_pts, wsum, s);  // the weights as a probability measure
+        launch_weighted_gauss(dp, dw, n_pts, 1.0, sigma, nullptr, x0, h, N_x, approx, s);
         if (eig) {
             DOS_CUDA_TRY(cudaMemcpyAsync(deig, eig, neig * 8, cudaMemcpyDefault, s));
             launch_blur_eigs(deig, n_eig, sigma, x0, h, N_x, ref, s);
@@ -1113,9 +1093,10 @@ int dos_points_error(dos_ctx *ctx, const double *pts, const double *wts, int64_t
             launch_blur_kpm(dref, M_ref, ref_damping, lb, ub, sigma, N_q, x0, h, N_x, poly, ref, s);
         }
         launch_error_norms(approx, ref, N_x, h, out, s);
-        double hv[2];
+        double hv[3];
         DOS_CUDA_TRY(cudaMemcpyAsync(hv, out, sizeof(hv), cudaMemcpyDeviceToHost, s));
         DOS_CUDA_TRY(cudaStreamSynchronize(s));
+        DOS_REQUIRE(hv[2] > 0.0 && isfinite(hv[2]), "weights must have a positive finite sum");
         if (err_l1) *err_l1 = hv[0];
         if (err_inf) *err_inf = hv[1];
     });
@@ -1143,19 +1124,19 @@ int dos_heat_capacity(dos_ctx *ctx, const double *mu, int M, int damping, double
             copy_out(cv, dout, n_beta * 8, s);
         } else {
             DOS_REQUIRE(wts && n_pts >= 1, "weights / n_pts");
-            std::vector<double> hw((size_t)n_pts);
-            DOS_CUDA_TRY(cudaMemcpyAsync(hw.data(), wts, hw.size() * 8, cudaMemcpyDefault, s));
-            DOS_CUDA_TRY(cudaStreamSynchronize(s));
-            double wsum = 0.0;
-            for (double v : hw) wsum += v;
-            DOS_REQUIRE(wsum > 0.0 && isfinite(wsum), "weights must have a positive finite sum");
-            const size_t nd = 2 * (size_t)n_pts + 2 * (size_t)n_beta;
+            const size_t nd = 2 * (size_t)n_pts + 2 * (size_t)n_beta + 1;
             double *buf = (double *)ctx->err_buf.get(nd * sizeof(double));
             double *dp = buf, *dw = dp + n_pts, *db = dw + n_pts, *dout = db + n_beta;
+            double *wsum = dout + n_beta;
             DOS_CUDA_TRY(cudaMemcpyAsync(dp, pts, (size_t)n_pts * 8, cudaMemcpyDefault, s));
             DOS_CUDA_TRY(cudaMemcpyAsync(dw, wts, (size_t)n_pts * 8, cudaMemcpyDefault, s));
             DOS_CUDA_TRY(cudaMemcpyAsync(db, betas, n_beta * 8, cudaMemcpyDefault, s));
-            launch_heat_points(dp, dw, n_pts, 1.0 / wsum, db, n_beta, dout, s);
+            launch_normalize_weights(dw, n_pts, wsum, s);
+            launch_heat_points(dp, dw, n_pts, 1.0, db, n_beta, dout, s);
+            double hsum = 0.0;
+            DOS_CUDA_TRY(cudaMemcpyAsync(&hsum, wsum, sizeof(double), cudaMemcpyDeviceToHost, s));
+            DOS_CUDA_TRY(cudaStreamSynchronize(s));
+            DOS_REQUIRE(hsum > 0.0 && isfinite(hsum), "weights must have a positive finite sum");
             copy_out(cv, dout, n_beta * 8, s);
         }
         DOS_CUDA_TRY(cudaStreamSynchronize(s));

@@ -281,6 +281,11 @@ void launch_column_sum(const double *part, int n_blocks, int ld, double *out, do
 void launch_lanczos_block_scale(int64_t n, int ld, const double *inv_beta, double *w, int num_sms,
                                 cudaStream_t s);
 void launch_unit_scale(int64_t n, int ld, int n_vec, double *q, int num_sms, cudaStream_t s);
+// w <- w / sum(w) on the device; sum_out[0] receives the sum.
+void launch_normalize_weights(double *w, int64_t n, double *sum_out, cudaStream_t s);
+// m_used[l]: steps run l keeps (invariant-subspace rule), -1 for non-finite values.
+void launch_lanczos_steps(const double *alpha, const double *beta, int M, int ld, int n_vec,
+                          int *m_used, cudaStream_t s);
 // Extreme-Ritz-value bounds of a k-step Lanczos run: out = {lo, hi, steps kept};
 // work: 3 k doubles.
 void launch_lanczos_bounds(const double *alpha, const double *beta, int k, double *work,

@@ -281,6 +281,55 @@ __global__ void lanczos_bounds_kernel(const double *__restrict__ alpha,
     out[2] = kk;
 }
 
+// w <- w / sum(w) in place (one block: fixed-order partial sums, a fixed shuffle
+// tree, then the division); sum_out[0] = the sum, for the caller's check.
+__global__ void normalize_weights_kernel(double *__restrict__ w, int64_t n,
+                                         double *__restrict__ sum_out) {
+    __shared__ double sh[32];
+    __shared__ double total;
+    double s = 0.0;
+    for (int64_t j = threadIdx.x; j < n; j += blockDim.x) s += w[j];
+    for (int off = 16; off > 0; off >>= 1) s += __shfl_down_sync(0xffffffffu, s, off);
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int q = 0; q < (int)(blockDim.x >> 5); ++q) t += sh[q];
+        total = t;
+        sum_out[0] = t;
+    }
+    __syncthreads();
+    const double t = total;
+    if (t > 0.0 && isfinite(t))
+        for (int64_t j = threadIdx.x; j < n; j += blockDim.x) w[j] /= t;
+}
+
+// Steps each Lanczos run keeps: a run ends at an invariant subspace, beta_j <= 1e-12
+// times the running estimate max(|alpha_i| + beta_i + beta_{i-1}) of ||A|| (the
+// paper is silent on breakdown); -1 marks a run with a non-finite coefficient.
+__global__ void lanczos_steps_kernel(const double *__restrict__ alpha,
+                                     const double *__restrict__ beta, int M, int ld, int n_vec,
+                                     int *__restrict__ m_used) {
+    const int l = blockIdx.x * blockDim.x + threadIdx.x;
+    if (l >= n_vec) return;
+    double scale = 0.0;
+    int m = M;
+    for (int j = 0; j < M; ++j) {
+        const double al = alpha[(size_t)j * ld + l], be = beta[(size_t)j * ld + l];
+        const double bp = j ? beta[(size_t)(j - 1) * ld + l] : 0.0;
+        if (!isfinite(al) || !isfinite(be)) {
+            m = -1;
+            break;
+        }
+        scale = fmax(scale, fabs(al) + be + bp);
+        if (!(be > 1e-12 * scale)) {
+            m = j + 1;
+            break;
+        }
+    }
+    m_used[l] = m;
+}
+
 }  // namespace
 
 int lanczos_blocks(int num_sms, int64_t n, int ld) {
@@ -345,6 +394,17 @@ void launch_weighted_gauss(const double *pts, const double *w, int64_t n_pts, do
 void launch_lanczos_bounds(const double *alpha, const double *beta, int k, double *work,
                            double *out, cudaStream_t s) {
     lanczos_bounds_kernel<<<1, 32, 0, s>>>(alpha, beta, k, work, out);
+    DOS_LAUNCHED();
+}
+
+void launch_normalize_weights(double *w, int64_t n, double *sum_out, cudaStream_t s) {
+    normalize_weights_kernel<<<1, 1024, 0, s>>>(w, n, sum_out);
+    DOS_LAUNCHED();
+}
+
+void launch_lanczos_steps(const double *alpha, const double *beta, int M, int ld, int n_vec,
+                          int *m_used, cudaStream_t s) {
+    lanczos_steps_kernel<<<(n_vec + 63) / 64, 64, 0, s>>>(alpha, beta, M, ld, n_vec, m_used);
     DOS_LAUNCHED();
 }
 
