@@ -54,6 +54,10 @@ WORKLOADS = {
     "chunglu": dict(kind="chunglu", n=4194304, beta=2.5, mean_deg=20.0, seed=3, M=1000,
                     n_v=256, desc="normalized Laplacian of a Chung-Lu graph, n=4194304, "
                               "beta=2.5, mean degree 20, seed 3"),
+    "chunglu1m": dict(kind="chunglu", n=1048576, beta=2.5, mean_deg=20.0, seed=3, M=200,
+                      n_v=256, desc="normalized Laplacian of a Chung-Lu graph, n=1048576, "
+                                "beta=2.5, mean degree 20, seed 3 (a quarter of the 4M-row "
+                                "graph, small enough for counter captures)"),
     "batched": dict(kind="batched", count=512, seed=4, M=200, n_v=32,
                     desc="512 Anderson lattices, L ~ U{10..40}, W ~ U[1,16], seed 4"),
 }
