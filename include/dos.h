@@ -78,9 +78,11 @@ extern "C" {
                                        replaying a cached CUDA graph */
 #define DOS_OPT_AUTOTUNE 8u         /* time the candidate launch shapes on this matrix
                                        once and cache the fastest (see dos_tune) */
-#define DOS_OPT_TEST_STALL_WAIT 16u /* failure-detection tests only: the staged kernel
-                                       expects 16 bytes more than it copies, so its first
-                                       wait can never complete and must run out */
+#define DOS_OPT_TEST_STALL_WAIT 16u /* failure-detection tests only: the TMA kernels'
+                                       waits can never complete and must run out
+                                       (staged 2 expects 16 bytes more than it copies;
+                                       staged 3 arms its barrier without issuing the
+                                       gather) */
 #define DOS_OPT_NO_PDL 32u          /* launch consecutive sweep steps with plain stream
                                        order instead of programmatic dependent launch
                                        (the next step's blocks are scheduled while the
@@ -110,7 +112,10 @@ typedef struct {
     int32_t tiles;           /* row tiles = blocks per sweep step */
     int32_t staged;          /* 1: rows of X_k / X_{k-1} loaded by the threads;
                                 2: row panels of X_k and X_{k-1} staged in shared memory
-                                by bulk asynchronous (TMA) copies (0: choose) */
+                                by bulk asynchronous (TMA) copies;
+                                3: the gathered rows X_k[j] of each four nonzeros loaded
+                                by one TMA gather (tile::gather4) into shared memory
+                                (0: choose) */
     int32_t chunk_bytes;     /* bytes per chunk: 16, or 32 (256-bit loads and stores;
                                 with staged 1 only, and rows of whole 32-byte chunks)
                                 (0: 16, or the autotuned choice) */

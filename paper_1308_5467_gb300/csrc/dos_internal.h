@@ -82,7 +82,8 @@ struct PinnedBuffer {
 // Launch shape of the fused step kernel.
 struct Shape {
     int team = 0, chunks = 0, block = 0, tiles = 0;
-    int staged = 0;  // 0 direct loads, 1 TMA-staged row panels (step_staged_kernel)
+    int staged = 0;  // 0 direct loads, 1 TMA-staged row panels (step_staged_kernel),
+                     // 2 TMA gathers of the X_k rows (step_tmag_kernel)
     int cb = 16;     // bytes per chunk: 16, or 32 (direct loads only)
 };
 

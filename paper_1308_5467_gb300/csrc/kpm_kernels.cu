@@ -727,6 +727,223 @@ __global__ void __launch_bounds__(kBlock, 2) step_staged_kernel(const StepParams
     }
 }
 
+// The tensor-map type and cuTensorMapEncodeTiled's signature (driver API).
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
+// ---- TMA-gather variant -------------------------------------------------------------
+// The gathers X_k[j, :] of the SpMM are issued as tensor-memory-accelerator
+// gathers: one elected lane per team loads the rows of the next four nonzeros of
+// its row with a single cp.async.bulk.tensor ... tile::gather4 (a 2-D tensor map
+// of the vector block, boxes one row high) into a per-team shared-memory stage,
+// completing on that stage's mbarrier; two stages per team, so the next batch is
+// in flight while this one is consumed.  The gathered rows hold no registers and
+// no L1 miss slots.  X_k[i] and X_{k-1}[i] are thread loads as in the direct
+// kernel.  Used for steps k >= 1 (the first step runs the direct first-step
+// instance).  Every wait is bounded: past spin_cycles a team stops, sets status
+// bit 4 and waits (bounded again) for its gathers in flight before the block ends.
+// The wait test (stall_test) arms the barrier without issuing the gather.
+__device__ __forceinline__ void tma_gather4(void *dst, const CUtensorMap *tmap, int r0, int r1,
+                                            int r2, int r3, uint64_t *bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile::gather4.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3, %4, %5, %6}], [%7];" ::"r"(smem_addr(dst)),
+        "l"(tmap), "r"(0), "r"(r0), "r"(r1), "r"(r2), "r"(r3), "r"(smem_addr(bar))
+        : "memory");
+}
+__device__ __forceinline__ void fence_proxy_async_smem() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+// Shared memory: [2 barriers per team][pad to 128 B][2 stages per team, each the
+// 4 gathered rows packed (row u at u * ld), rounded up to 128 B][reduction scratch].
+__host__ __device__ inline size_t tmag_stage_bytes(int ld, int esz) {
+    return ((size_t)4 * ld * esz + 127) / 128 * 128;
+}
+__host__ __device__ inline size_t tmag_bar_bytes(int n_teams) {
+    return ((size_t)n_teams * 2 * sizeof(uint64_t) + 127) / 128 * 128;
+}
+size_t tmag_smem(int block, int team, int ld, int esz) {
+    const int n_teams = (block / 32) * (32 / team);
+    return tmag_bar_bytes(n_teams) + (size_t)n_teams * 2 * tmag_stage_bytes(ld, esz) +
+           (size_t)(block / 32) * ld * sizeof(double);
+}
+
+template <typename T, int G, int CPT, bool PV>
+__global__ void __launch_bounds__(kBlock, 2) step_tmag_kernel(const StepParams<T> p,
+                                                             const __grid_constant__ CUtensorMap tmap) {
+    constexpr int VPT = Traits<T>::VPT;
+    using Acc = typename Traits<T>::Acc;
+    constexpr int TPW = 32 / G;
+    extern __shared__ __align__(128) unsigned char smem[];
+
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+
+    const int ld = p.ld;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int g = lane % G;
+    const int n_teams = (blockDim.x >> 5) * TPW;
+    const int team = warp * TPW + lane / G;
+    const int team_base = (lane / G) * G;
+    const unsigned team_mask = G == 32 ? 0xffffffffu : (((1u << G) - 1u) << team_base);
+    const size_t stage_elems = tmag_stage_bytes(ld, (int)sizeof(T)) / sizeof(T);
+    uint64_t *bars = reinterpret_cast<uint64_t *>(smem);
+    T *stages = reinterpret_cast<T *>(smem + tmag_bar_bytes(n_teams));
+    double *red = reinterpret_cast<double *>(smem + tmag_bar_bytes(n_teams) +
+                                             (size_t)n_teams * 2 * stage_elems * sizeof(T));
+    uint64_t *tbar = bars + 2 * team;
+    T *tbuf = stages + (size_t)team * 2 * stage_elems;
+
+    const int4 tl = p.tiles[blockIdx.x];
+    const int rb = tl.x, re = tl.y, seg = tl.z;
+    const T c = (T)p.seg_c[seg];
+    const T inv_d = (T)p.seg_inv_d[seg];
+    const int row0 = p.seg_row0[seg];
+    const T *__restrict__ xc = p.xc;
+    const int32_t *__restrict__ row_ptr = p.row_ptr;
+    const int32_t *__restrict__ col_idx = p.col_idx;
+    const T *__restrict__ val = p.val;
+    T *xn = p.xn;
+    const uint32_t batch_bytes = 4u * (uint32_t)ld * (uint32_t)sizeof(T);
+
+    constexpr int NA = PV ? CPT : 1, NJ = PV ? VPT : 1;
+    Acc accR[NA][NJ], accS[NA][NJ];
+#pragma unroll
+    for (int cc = 0; cc < NA; ++cc)
+#pragma unroll
+        for (int j = 0; j < NJ; ++j) {
+            acc_zero(accR[cc][j]);
+            acc_zero(accS[cc][j]);
+        }
+    bool valid[CPT];
+#pragma unroll
+    for (int cc = 0; cc < CPT; ++cc) valid[cc] = (g + cc * G) < p.n_chunks;
+
+    if (g == 0) {
+        mbar_init(&tbar[0], 1);
+        mbar_init(&tbar[1], 1);
+        mbar_init_fence();
+    }
+    __syncthreads();
+
+    uint32_t issued[2] = {0u, 0u}, done[2] = {0u, 0u};
+    bool timed_out = false;
+    T a_st[2][4];
+    for (int row = rb + team; row < re && !timed_out; row += n_teams) {
+        const size_t roff = (size_t)row * ld;
+        T xk[CPT][VPT], xo[CPT][VPT];
+#pragma unroll
+        for (int cc = 0; cc < CPT; ++cc) {
+            if (valid[cc]) {
+                const int off = (g + cc * G) * VPT;
+                load16(xc + roff + off, xk[cc]);
+                load16(xn + roff + off, xo[cc]);
+            }
+        }
+        const int e0 = __ldg(row_ptr + row), e1 = __ldg(row_ptr + row + 1);
+        const int nb = (e1 - e0 + 3) >> 2;
+        T y[CPT][VPT];
+#pragma unroll
+        for (int cc = 0; cc < CPT; ++cc)
+#pragma unroll
+            for (int j = 0; j < VPT; ++j) y[cc][j] = T(0);
+        // batch b: entries e0 + 4b .. e0 + 4b + 3 (past e1: column 0, value 0)
+        auto issue = [&](int b) {
+            int col[4];
+            T a[4];
+            team_fetch<T, G, 4>(col_idx, val, e0 + 4 * b, e1, g, team_base, team_mask, col, a);
+            const int st = b & 1;
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                if (st == 0) a_st[0][u] = a[u];
+                else a_st[1][u] = a[u];
+            }
+            __syncwarp(team_mask);  // the stage's previous rows have been read by the team
+            if (g == 0) {
+                fence_proxy_async_smem();
+                mbar_expect_tx(&tbar[st], batch_bytes);
+                // tests only: the gather is left out, so the wait runs out with
+                // nothing in flight
+                if (!p.stall_test)
+                    tma_gather4(tbuf + (size_t)st * stage_elems, &tmap, row0 + col[0],
+                                row0 + col[1], row0 + col[2], row0 + col[3], &tbar[st]);
+            }
+            ++issued[st];
+        };
+        if (nb > 0) issue(0);
+        for (int b = 0; b < nb; ++b) {
+            if (b + 1 < nb) issue(b + 1);
+            const int st = b & 1;
+            const bool ok = mbar_wait_bounded(&tbar[st], done[st] & 1u, p.spin_cycles);
+            if (__any_sync(team_mask, !ok)) {  // the team leaves together
+                timed_out = true;
+                break;
+            }
+            ++done[st];
+            const T *buf = tbuf + (size_t)st * stage_elems;
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const T au = st == 0 ? a_st[0][u] : a_st[1][u];
+#pragma unroll
+                for (int cc = 0; cc < CPT; ++cc) {
+                    if (valid[cc]) {
+                        T xv[VPT];
+                        load16(buf + (size_t)u * ld + (g + cc * G) * VPT, xv);
+#pragma unroll
+                        for (int j = 0; j < VPT; ++j) y[cc][j] = fma(au, xv[j], y[cc][j]);
+                    }
+                }
+            }
+        }
+        if (timed_out) break;
+        T rr = T(0), ss = T(0);
+#pragma unroll
+        for (int cc = 0; cc < CPT; ++cc) {
+            if (!valid[cc]) continue;
+            const int off = (g + cc * G) * VPT;
+            T xnew[VPT];
+#pragma unroll
+            for (int j = 0; j < VPT; ++j)
+                xnew[j] = fma(T(2), fma(-c, xk[cc][j], y[cc][j]) * inv_d, -xo[cc][j]);
+            store16(xn + roff + off, xnew);
+#pragma unroll
+            for (int j = 0; j < VPT; ++j) {
+                if constexpr (PV) {
+                    acc_add_prod(accR[cc][j], xnew[j], xk[cc][j]);
+                    acc_add_prod(accS[cc][j], xnew[j], xnew[j]);
+                } else {
+                    rr = fma(xnew[j], xk[cc][j], rr);
+                    ss = fma(xnew[j], xnew[j], ss);
+                }
+            }
+        }
+        if constexpr (!PV) {
+            acc_add(accR[0][0], rr);
+            acc_add(accS[0][0], ss);
+        }
+    }
+    if (timed_out) {
+        // a wait ran out: record it and let the gathers still in flight land (bounded)
+        if (g == 0) atomicOr(p.status, 4);
+#pragma unroll
+        for (int st = 0; st < 2; ++st)
+            while (done[st] < issued[st]) {
+                if (!mbar_wait_bounded(&tbar[st], done[st] & 1u, p.spin_cycles)) break;
+                ++done[st];
+            }
+    }
+    if constexpr (PV) {
+        double *out = p.part + (size_t)blockIdx.x * 2 * p.pv;
+        block_reduce_store<Acc, G, CPT, VPT>(accR, out, ld, p.n_chunks, p.pv, red);
+        block_reduce_store<Acc, G, CPT, VPT>(accS, out + p.pv, ld, p.n_chunks, p.pv, red);
+    } else {
+        double *out = p.part + (size_t)blockIdx.x * 2;
+        block_reduce_scalar(accR[0][0], out, red);
+        block_reduce_scalar(accS[0][0], out + 1, red);
+    }
+}
+
 // ---- kernel table --------------------------------------------------------------
 template <typename T>
 using StepFn = void (*)(const StepParams<T>);
@@ -740,6 +957,55 @@ StepFn<T> pick_staged(int G, int CPT, bool per_vec) {
     DOS_CASE(8, 2) DOS_CASE(16, 2) DOS_CASE(32, 2) DOS_CASE(32, 4)
 #undef DOS_CASE
     return nullptr;
+}
+
+template <typename T>
+using TmagFn = void (*)(const StepParams<T>, const CUtensorMap);
+
+template <typename T>
+TmagFn<T> pick_tmag(int G, int CPT, bool per_vec) {
+#define DOS_CASE(GG, CC)                                                                     \
+    if (G == GG && CPT == CC)                                                                \
+        return per_vec ? step_tmag_kernel<T, GG, CC, true> : step_tmag_kernel<T, GG, CC, false>;
+    DOS_CASE(4, 1) DOS_CASE(8, 1) DOS_CASE(16, 1) DOS_CASE(32, 1)
+    DOS_CASE(8, 2) DOS_CASE(16, 2) DOS_CASE(32, 2) DOS_CASE(32, 4)
+#undef DOS_CASE
+    return nullptr;
+}
+
+// The tensor map of one vector block for the gathers: 2-D, n_rows x ld elements,
+// row pitch ld * size, boxes of one full row (the TMA box limit of 256 elements
+// per dimension holds: panels are at most 256 vectors wide).
+using EncodeTiledFn = PFN_cuTensorMapEncodeTiled_v12000;
+static EncodeTiledFn encode_tiled() {
+    static EncodeTiledFn fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void *ptr = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &ptr, 12000,
+                                             cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<EncodeTiledFn>(ptr);
+    });
+    return fn;
+}
+template <typename T>
+static CUtensorMap vector_block_map(const T *x, int64_t n_rows, int ld) {
+    EncodeTiledFn enc = encode_tiled();
+    if (!enc) throw Error{DOS_ECUDA, "cuTensorMapEncodeTiled is not available"};
+    CUtensorMap m;
+    const cuuint64_t dims[2] = {(cuuint64_t)ld, (cuuint64_t)n_rows};
+    const cuuint64_t strides[1] = {(cuuint64_t)ld * sizeof(T)};
+    const cuuint32_t box[2] = {(cuuint32_t)ld, 1u};
+    const cuuint32_t estr[2] = {1u, 1u};
+    const CUresult r = enc(&m, sizeof(T) == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
+                                             : CU_TENSOR_MAP_DATA_TYPE_FLOAT64,
+                           2, const_cast<T *>(x), dims, strides, box, estr,
+                           CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                           CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) throw Error{DOS_ECUDA, "cuTensorMapEncodeTiled rejected the vector block"};
+    return m;
 }
 
 // Rows per panel of the staged kernel: a multiple of the team count with the four
@@ -1009,7 +1275,7 @@ bool shape_supported(int precision, const Shape &sh, int ld) {
     if (sh.team < 1 || sh.team > 32 || (sh.team & (sh.team - 1))) return false;
     if (sh.chunks != 1 && sh.chunks != 2 && sh.chunks != 4) return false;
     if (sh.tiles < 1) return false;
-    if (sh.staged < 0 || sh.staged > 1) return false;
+    if (sh.staged < 0 || sh.staged > 2) return false;
     if (sh.cb != 16 && sh.cb != 32) return false;
     const int vpt = sh.cb / esz;
     if (sh.cb == 32) {  // 256-bit accesses: direct loads, rows of whole 32-byte chunks
@@ -1022,13 +1288,24 @@ bool shape_supported(int precision, const Shape &sh, int ld) {
         !(precision == DOS_PREC_F64 ? (void *)pick_staged<double>(sh.team, sh.chunks, false)
                                     : (void *)pick_staged<float>(sh.team, sh.chunks, false)))
         return false;
+    if (sh.staged == 2) {  // TMA gathers: 16-byte chunks, rows of at most 256 elements
+        if (sh.cb != 16 || ld > 256) return false;
+        if (!(precision == DOS_PREC_F64 ? (void *)pick_tmag<double>(sh.team, sh.chunks, false)
+                                        : (void *)pick_tmag<float>(sh.team, sh.chunks, false)))
+            return false;
+        if (tmag_smem(sh.block, sh.team, ld, esz) > (size_t)227 * 1024) return false;
+    }
     return sh.team * sh.chunks * vpt >= ld;
 }
 
 // Opt in to more than 48 KB of dynamic shared memory (per kernel, per device;
 // remembered so the driver is asked once per size).
+static void allow_smem_fn(const void *fn, size_t bytes);
 template <typename T>
 static void allow_smem(StepFn<T> fn, size_t bytes) {
+    allow_smem_fn((const void *)fn, bytes);
+}
+static void allow_smem_fn(const void *fn, size_t bytes) {
     static std::mutex mu;
     static std::map<std::tuple<const void *, int>, size_t> granted;
     int dev = 0;
@@ -1049,6 +1326,12 @@ static int occupancy_t(const Shape &sh, int ld) {
         if (!fn) return 0;
         const size_t sm = staged_smem(sh.block, sh.team, ld, sizeof(T));
         allow_smem<T>(fn, sm);
+        DOS_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, sh.block, sm));
+    } else if (sh.staged == 2) {
+        auto fn = pick_tmag<T>(sh.team, sh.chunks, false);
+        if (!fn) return 0;
+        const size_t sm = tmag_smem(sh.block, sh.team, ld, sizeof(T));
+        allow_smem_fn((const void *)fn, sm);
         DOS_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, sh.block, sm));
     } else {
         auto fn = pick<T>(sh.team, sh.chunks, false, sh.cb);
@@ -1131,7 +1414,26 @@ static void launch_step_t(const SweepArgs &a, int k, int slot, cudaStream_t s) {
         const size_t sm = staged_smem(a.shape.block, a.shape.team, a.ld, sizeof(T));
         allow_smem<T>(fn, sm);
         fn<<<a.n_tiles, a.shape.block, sm, s>>>(p);
+    } else if (a.shape.staged == 2 && k > 0) {
+        auto fn = pick_tmag<T>(a.shape.team, a.shape.chunks, a.per_vec != 0);
+        if (!fn) throw Error{DOS_EINVAL, "unsupported TMA-gather launch shape"};
+        p.panel_rows = 0;
+        const CUtensorMap tmap = vector_block_map<T>(p.xc, a.n_rows, a.ld);
+        const size_t sm = tmag_smem(a.shape.block, a.shape.team, a.ld, sizeof(T));
+        allow_smem_fn((const void *)fn, sm);
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3((unsigned)a.n_tiles);
+        cfg.blockDim = dim3((unsigned)a.shape.block);
+        cfg.dynamicSmemBytes = sm;
+        cfg.stream = s;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+        attr[0].val.programmaticStreamSerializationAllowed = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = a.pdl ? 1 : 0;
+        DOS_CUDA_TRY(cudaLaunchKernelEx(&cfg, fn, p, tmap));
     } else {
+        // direct loads; also the first step of the TMA-gather variant
         auto fn = k == 0 ? pick_first<T>(a.per_vec != 0)
                          : pick<T>(a.shape.team, a.shape.chunks, a.per_vec != 0, a.shape.cb);
         if (!fn) throw Error{DOS_EINVAL, "unsupported launch shape"};

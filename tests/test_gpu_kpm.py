@@ -11,6 +11,7 @@ oracle on the same seeded inputs.  Tolerances:
 import numpy as np
 import pytest
 
+from oracle import bounds as obounds
 from oracle import kpm as okpm
 from synthetic import anderson_3d, laplacian_2d, random_symmetric, diagonal
 
@@ -227,12 +228,62 @@ def test_wide_chunk_parity(ctx, precision, launch):
         assert np.all(np.abs(mu_tot - ref.mean(axis=0)) <= tol)
 
 
+@pytest.mark.parametrize("precision", ["f64", "f32"])
+@pytest.mark.parametrize("launch", [{"staged": 3}, {"team": 16, "chunks": 1, "staged": 3},
+                                    {"team": 8, "chunks": 2, "staged": 3, "tiles": 7},
+                                    {"team": 32, "chunks": 2, "staged": 3, "tiles": 500},
+                                    {"team": 32, "chunks": 4, "staged": 3}])
+def test_tma_gather_parity(ctx, precision, launch):
+    """Rows gathered by TMA (tile::gather4, four nonzeros per copy): a lattice, and a
+    random matrix with empty rows and one dense row (batches padded past the row's
+    end), per-vector and total moments, several tile counts and n_v."""
+    from paper_1308_5467_gb300 import dos
+    dtype = np.float64 if precision == "f64" else np.float32
+    per_chunk = 2 if precision == "f64" else 4
+    for A, lb, ub in ((anderson_3d(13, 6.0, seed=4), -9.6, 9.6),
+                      (random_symmetric(400, 0.02, 9, empty_rows=7, long_row=37), None, None)):
+        Aw = A.astype(dtype)
+        if lb is None:
+            lb, ub = obounds.bounds(A, "gershgorin", pad_frac=0.01)
+        for n_v in (64, 20):
+            if launch.get("team", 16) * launch.get("chunks", 1) * per_chunk < n_v:
+                with pytest.raises(dos.DosError):
+                    ctx.dos_kpm_moments(dev(Aw), lb, ub, 30, n_v, seed=5, precision=precision,
+                                        launch=launch)
+                continue
+            pv = np.empty((n_v, 71))
+            mu = ctx.dos_kpm_moments(dev(Aw), lb, ub, 70, n_v, seed=5, precision=precision,
+                                     launch=launch, mu_per_vec=pv)
+            mu_tot = ctx.dos_kpm_moments(dev(Aw), lb, ub, 70, n_v, seed=5, precision=precision,
+                                         launch=launch)
+            ref = okpm.kpm_moments_per_vector(Aw, lb, ub, 70, n_v, seed=5)
+            tol = TOL64 if precision == "f64" else tol32(70)
+            assert np.all(np.abs(pv - ref) <= tol)
+            assert np.all(np.abs(mu - ref.mean(axis=0)) <= tol)
+            assert np.all(np.abs(mu_tot - ref.mean(axis=0)) <= tol)
+
+
+def test_tma_gather_wait_timeout_is_reported(ctx):
+    """The TMA-gather kernel's bounded wait made to run out (the barrier is armed
+    and no gather issued): DOS_ETIMEOUT, and the context still works."""
+    from paper_1308_5467_gb300 import dos
+    A = dev(anderson_3d(8, 6.0, seed=4))
+    with pytest.raises(dos.DosError) as ei:
+        ctx.dos_kpm_moments(A, -9.6, 9.6, 10, 16, seed=5, precision="f64",
+                            launch={"staged": 3}, flags=dos.DOS_OPT_TEST_STALL_WAIT,
+                            wait_limit_cycles=2_000_000)
+    assert ei.value.status == dos.DOS_ETIMEOUT
+    mu = ctx.dos_kpm_moments(A, -9.6, 9.6, 10, 16, seed=5, precision="f64", launch={"staged": 3})
+    ref = okpm.kpm_moments(anderson_3d(8, 6.0, seed=4), -9.6, 9.6, 10, 16, seed=5)
+    assert np.abs(mu - ref).max() < TOL64
+
+
 def test_unknown_variant_is_rejected(ctx):
     from paper_1308_5467_gb300 import dos
     A = anderson_3d(6, 6.0, seed=4)
     with pytest.raises(dos.DosError):
         ctx.dos_kpm_moments(dev(A), -9.6, 9.6, 10, 16, seed=5, precision="f64",
-                            launch={"staged": 3})
+                            launch={"staged": 4})
 
 
 def test_wide_chunks_need_whole_32_byte_rows(ctx):
