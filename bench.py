@@ -609,7 +609,8 @@ def main():
     ap.add_argument("--no-pdl", action="store_true",
                     help="plain stream order between sweep steps (no programmatic dependent launch)")
     ap.add_argument("--launch", default=None,
-                    help="fixed launch shape team,chunks,staged(1|2|3)[,chunk_bytes(16|32)] "
+                    help="fixed launch shape team,chunks,staged(1|2|3)[,chunk_bytes(16|32)"
+                         "[,depth(2|4|8)]] "
                          "instead of the autotuner "
                          "(used when profiling one known kernel instance)")
     args = ap.parse_args()
@@ -648,7 +649,7 @@ def main():
     # launch shape of the fused step chosen by the library's autotuner (cached in ctx)
     fixed = None
     if args.launch:
-        fixed = dict(zip(("team", "chunks", "staged", "chunk_bytes"),
+        fixed = dict(zip(("team", "chunks", "staged", "chunk_bytes", "depth"),
                          (int(v) for v in args.launch.split(","))))
         tuned_shape, tuned64 = fixed, None
     else:

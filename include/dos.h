@@ -119,6 +119,9 @@ typedef struct {
     int32_t chunk_bytes;     /* bytes per chunk: 16, or 32 (256-bit loads and stores;
                                 with staged 1 only, and rows of whole 32-byte chunks)
                                 (0: 16, or the autotuned choice) */
+    int32_t depth;           /* staged 3 only: batches of four gathers each team keeps in
+                                flight (2, 4 or 8); 0: the deepest of 8, 4, 2 whose
+                                stages leave room for two blocks per SM */
 } dos_launch;
 
 /* Optional arguments of the _ex / _batched entry points (NULL = defaults). */

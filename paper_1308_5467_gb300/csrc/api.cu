@@ -186,7 +186,7 @@ Shape tune_shape(dos_ctx *ctx, const dos_csr *A, int B, const int64_t *seg_rows,
 Shape choose_shape(dos_ctx *ctx, const SweepRequest &r, const dos_csr *Adesc, int ld,
                    int64_t n_rows, int64_t nnz, cudaStream_t s) {
     const dos_launch &o = r.opts.launch;
-    if (o.team || o.chunks || o.block || o.tiles || o.staged || o.chunk_bytes) {
+    if (o.team || o.chunks || o.block || o.tiles || o.staged || o.chunk_bytes || o.depth) {
         Shape d = default_shape(r.precision, ld, ctx->num_sms, n_rows);
         Shape sh;
         sh.team = o.team ? o.team : d.team;
@@ -197,6 +197,9 @@ Shape choose_shape(dos_ctx *ctx, const SweepRequest &r, const dos_csr *Adesc, in
         DOS_REQUIRE(o.chunk_bytes == 0 || o.chunk_bytes == 16 || o.chunk_bytes == 32,
                     "launch.chunk_bytes must be 0, 16 or 32");
         sh.cb = o.chunk_bytes ? o.chunk_bytes : 16;
+        DOS_REQUIRE(o.depth == 0 || ((o.depth == 2 || o.depth == 4 || o.depth == 8) && o.staged == 3),
+                    "launch.depth must be 0, or 2, 4 or 8 with staged 3");
+        sh.depth = o.depth;
         sh.tiles = 1;
         DOS_REQUIRE(shape_supported(r.precision, sh, ld),
                     "launch override does not cover the vector block (team*chunks*chunk_bytes >= row) "
@@ -403,7 +406,7 @@ void run_sweep(dos_ctx *ctx, const dos_csr *Adesc, SweepRequest &r, cudaStream_t
         (uint64_t)(uintptr_t)val, (uint64_t)A.n, (uint64_t)A.nnz, (uint64_t)B, (uint64_t)ld,
         (uint64_t)r.n_v, (uint64_t)r.M, r.seed, (uint64_t)r.opts.vec_offset, r.opts.batch_index,
         (uint64_t)sh.team, (uint64_t)sh.chunks, (uint64_t)sh.block, (uint64_t)plan.n_tiles,
-        (uint64_t)sh.staged, (uint64_t)sh.cb,
+        (uint64_t)sh.staged, (uint64_t)sh.cb, (uint64_t)sh.depth,
         (uint64_t)per_vec, (uint64_t)slots, (uint64_t)(uintptr_t)xb, (uint64_t)(uintptr_t)partial,
         (uint64_t)(uintptr_t)dotsum, (uint64_t)(uintptr_t)mu_dev, (uint64_t)(uintptr_t)mupv_dev,
         (uint64_t)(uintptr_t)tiles, (uint64_t)(uintptr_t)seg.row0, (uint64_t)(uintptr_t)status,
@@ -496,16 +499,21 @@ dos_kpm_opts default_opts() {
 // sweeps of 16 and 48 Chebyshev steps with CUDA events; the difference / 32 is
 // the per-step time (fixed per-call costs cancel).  Best of three runs (one when
 // a step takes more than 2 ms).
+// Row length (elements) of one vector panel of an n_v-vector sweep.
+static int panel_ld(int n_v, int precision) {
+    const int vpt = precision == DOS_PREC_F64 ? 2 : 4;
+    const int n_panels = (n_v + kPanelMax - 1) / kPanelMax;
+    const int panel_nv = (n_v + n_panels - 1) / n_panels;
+    return (panel_nv + vpt - 1) / vpt * vpt;
+}
+
 Shape tune_shape(dos_ctx *ctx, const dos_csr *A, int B, const int64_t *seg_rows, int n_v,
                  int precision, double *best_ms, cudaStream_t s) {
     DOS_REQUIRE(n_v >= 1 && n_v <= 4096, "n_v must be in [1, 4096]");
     DOS_REQUIRE(precision == DOS_PREC_F64 || precision == DOS_PREC_F32_ACC64, "bad precision");
-    const int vpt = precision == DOS_PREC_F64 ? 2 : 4;
     const int esz = precision == DOS_PREC_F64 ? 8 : 4;
     const int pw = std::min(n_v, kPanelMax);
-    const int n_panels = (n_v + kPanelMax - 1) / kPanelMax;
-    const int panel_nv = (n_v + n_panels - 1) / n_panels;
-    const int ld = (panel_nv + vpt - 1) / vpt * vpt;
+    const int ld = panel_ld(n_v, precision);
     std::vector<int64_t> rows;
     if (B == 1) rows = {0, A->n};
     else rows.assign(seg_rows, seg_rows + B + 1);
@@ -567,6 +575,7 @@ Shape tune_shape(dos_ctx *ctx, const dos_csr *A, int B, const int64_t *seg_rows,
                         r.opts.launch.tiles = sh.tiles;
                         r.opts.launch.staged = sh.staged + 1;
                         r.opts.launch.chunk_bytes = sh.cb;
+                        r.opts.launch.depth = sh.depth;
                         DOS_CUDA_TRY(cudaEventRecord(e0, s));
                         run_sweep(ctx, A, r, s);
                         DOS_CUDA_TRY(cudaEventRecord(e1, s));
@@ -796,6 +805,9 @@ int dos_tune(dos_ctx *ctx, const dos_csr *A, int B, const int64_t *seg_rows, int
             best->tiles = sh.tiles;
             best->staged = sh.staged + 1;
             best->chunk_bytes = sh.cb;
+            best->depth = sh.staged == 2 ? tmag_depth(sh.block, sh.team, panel_ld(n_v, precision),
+                                                      precision == DOS_PREC_F64 ? 8 : 4, sh.depth)
+                                         : 0;
         }
     });
 }

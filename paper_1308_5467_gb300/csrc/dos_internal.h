@@ -85,6 +85,7 @@ struct Shape {
     int staged = 0;  // 0 direct loads, 1 TMA-staged row panels (step_staged_kernel),
                      // 2 TMA gathers of the X_k rows (step_tmag_kernel)
     int cb = 16;     // bytes per chunk: 16, or 32 (direct loads only)
+    int depth = 0;   // TMA gathers: batches in flight per team (2, 4, 8; 0: by shared memory)
 };
 
 // Cached CUDA graph for one sweep configuration.
@@ -184,6 +185,8 @@ struct SweepArgs {
 Shape default_shape(int precision, int ld, int num_sms, int64_t n_rows);
 bool shape_supported(int precision, const Shape &sh, int ld);
 int max_active_blocks(int precision, const Shape &sh, int ld);
+// Ring depth of the TMA-gather kernel for this shape (asked: 0 = by shared memory).
+int tmag_depth(int block, int team, int ld, int esz, int asked);
 
 void launch_init_vectors(const SweepArgs &a, cudaStream_t s);
 // Step k (0-based): reads x_cur = blocks[k%2], writes blocks[(k+1)%2]; partial slice `slot`.

@@ -727,22 +727,25 @@ __global__ void __launch_bounds__(kBlock, 2) step_staged_kernel(const StepParams
     }
 }
 
+// ---- TMA-gather variant -------------------------------------------------------------
+// The gathers X_k[j, :] of the SpMM are issued as tensor-memory-accelerator
+// gathers: one elected lane per team loads the rows of four nonzeros with a single
+// cp.async.bulk.tensor ... tile::gather4 (a 2-D tensor map of the vector block,
+// boxes one row high) into a per-team shared-memory stage, completing on that
+// stage's mbarrier.  Each team owns a ring of `depth` stages and walks its rows as
+// one stream of batches (four nonzeros each, padded with column 0 / value 0 past a
+// row's end): the producer side runs up to depth batches ahead of the consumer,
+// across row boundaries, so the gathers of the next rows are in flight while this
+// row is summed.  The gathered rows hold no registers and no L1 miss slots.
+// X_k[i] and X_{k-1}[i] are thread loads as in the direct kernel.  Used for steps
+// k >= 1 (the first step runs the direct first-step instance).  Every wait is
+// bounded: past spin_cycles a team stops, sets status bit 4 and waits (bounded
+// again) for its gathers in flight before the block ends.  The wait test
+// (stall_test) arms the barrier without issuing the gather.
 // The tensor-map type and cuTensorMapEncodeTiled's signature (driver API).
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
-// ---- TMA-gather variant -------------------------------------------------------------
-// The gathers X_k[j, :] of the SpMM are issued as tensor-memory-accelerator
-// gathers: one elected lane per team loads the rows of the next four nonzeros of
-// its row with a single cp.async.bulk.tensor ... tile::gather4 (a 2-D tensor map
-// of the vector block, boxes one row high) into a per-team shared-memory stage,
-// completing on that stage's mbarrier; two stages per team, so the next batch is
-// in flight while this one is consumed.  The gathered rows hold no registers and
-// no L1 miss slots.  X_k[i] and X_{k-1}[i] are thread loads as in the direct
-// kernel.  Used for steps k >= 1 (the first step runs the direct first-step
-// instance).  Every wait is bounded: past spin_cycles a team stops, sets status
-// bit 4 and waits (bounded again) for its gathers in flight before the block ends.
-// The wait test (stall_test) arms the barrier without issuing the gather.
 __device__ __forceinline__ void tma_gather4(void *dst, const CUtensorMap *tmap, int r0, int r1,
                                             int r2, int r3, uint64_t *bar) {
     asm volatile(
@@ -755,23 +758,34 @@ __device__ __forceinline__ void fence_proxy_async_smem() {
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 }
 
-// Shared memory: [2 barriers per team][pad to 128 B][2 stages per team, each the
-// 4 gathered rows packed (row u at u * ld), rounded up to 128 B][reduction scratch].
+// Shared memory: [depth barriers per team][4 values per stage][pad to 128 B]
+// [depth stages per team, each the 4 gathered rows packed (row u at u * ld), rounded
+// up to 128 B][reduction scratch].
 __host__ __device__ inline size_t tmag_stage_bytes(int ld, int esz) {
     return ((size_t)4 * ld * esz + 127) / 128 * 128;
 }
-__host__ __device__ inline size_t tmag_bar_bytes(int n_teams) {
-    return ((size_t)n_teams * 2 * sizeof(uint64_t) + 127) / 128 * 128;
+__host__ __device__ inline size_t tmag_head_bytes(int n_teams, int depth, int esz) {
+    return ((size_t)n_teams * depth * (sizeof(uint64_t) + 4 * esz) + 127) / 128 * 128;
 }
-size_t tmag_smem(int block, int team, int ld, int esz) {
+size_t tmag_smem(int block, int team, int ld, int esz, int depth) {
     const int n_teams = (block / 32) * (32 / team);
-    return tmag_bar_bytes(n_teams) + (size_t)n_teams * 2 * tmag_stage_bytes(ld, esz) +
+    return tmag_head_bytes(n_teams, depth, esz) +
+           (size_t)n_teams * depth * tmag_stage_bytes(ld, esz) +
            (size_t)(block / 32) * ld * sizeof(double);
+}
+// Ring depth: the one asked for, else the deepest of 8, 4, 2 that leaves room for
+// two blocks per SM.
+int tmag_ring_depth(int block, int team, int ld, int esz, int asked) {
+    if (asked) return asked;
+    for (int d = 8; d > 2; d >>= 1)
+        if (tmag_smem(block, team, ld, esz, d) <= (size_t)112 * 1024) return d;
+    return 2;
 }
 
 template <typename T, int G, int CPT, bool PV>
 __global__ void __launch_bounds__(kBlock, 2) step_tmag_kernel(const StepParams<T> p,
-                                                             const __grid_constant__ CUtensorMap tmap) {
+                                                             const __grid_constant__ CUtensorMap tmap,
+                                                             const int log2_depth) {
     constexpr int VPT = Traits<T>::VPT;
     using Acc = typename Traits<T>::Acc;
     constexpr int TPW = 32 / G;
@@ -781,6 +795,8 @@ __global__ void __launch_bounds__(kBlock, 2) step_tmag_kernel(const StepParams<T
     asm volatile("griddepcontrol.wait;" ::: "memory");
 
     const int ld = p.ld;
+    const int depth = 1 << log2_depth;
+    const uint32_t ring_mask = (uint32_t)depth - 1u;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int g = lane % G;
     const int n_teams = (blockDim.x >> 5) * TPW;
@@ -788,12 +804,13 @@ __global__ void __launch_bounds__(kBlock, 2) step_tmag_kernel(const StepParams<T
     const int team_base = (lane / G) * G;
     const unsigned team_mask = G == 32 ? 0xffffffffu : (((1u << G) - 1u) << team_base);
     const size_t stage_elems = tmag_stage_bytes(ld, (int)sizeof(T)) / sizeof(T);
-    uint64_t *bars = reinterpret_cast<uint64_t *>(smem);
-    T *stages = reinterpret_cast<T *>(smem + tmag_bar_bytes(n_teams));
-    double *red = reinterpret_cast<double *>(smem + tmag_bar_bytes(n_teams) +
-                                             (size_t)n_teams * 2 * stage_elems * sizeof(T));
-    uint64_t *tbar = bars + 2 * team;
-    T *tbuf = stages + (size_t)team * 2 * stage_elems;
+    const size_t head = tmag_head_bytes(n_teams, depth, (int)sizeof(T));
+    uint64_t *tbar = reinterpret_cast<uint64_t *>(smem) + (size_t)team * depth;
+    T *tval = reinterpret_cast<T *>(smem + (size_t)n_teams * depth * sizeof(uint64_t)) +
+              (size_t)team * depth * 4;
+    T *tbuf = reinterpret_cast<T *>(smem + head) + (size_t)team * depth * stage_elems;
+    double *red = reinterpret_cast<double *>(smem + head +
+                                             (size_t)n_teams * depth * stage_elems * sizeof(T));
 
     const int4 tl = p.tiles[blockIdx.x];
     const int rb = tl.x, re = tl.y, seg = tl.z;
@@ -821,16 +838,52 @@ __global__ void __launch_bounds__(kBlock, 2) step_tmag_kernel(const StepParams<T
     for (int cc = 0; cc < CPT; ++cc) valid[cc] = (g + cc * G) < p.n_chunks;
 
     if (g == 0) {
-        mbar_init(&tbar[0], 1);
-        mbar_init(&tbar[1], 1);
+        for (int st = 0; st < depth; ++st) mbar_init(&tbar[st], 1);
         mbar_init_fence();
     }
     __syncthreads();
 
-    uint32_t issued[2] = {0u, 0u}, done[2] = {0u, 0u};
+    // Producer position: row p_row, its entries [p_e, p_e1); all team-uniform.
+    int p_row = rb + team, p_e = 0, p_e1 = 0;
+    if (p_row < re) {
+        p_e = __ldg(row_ptr + p_row);
+        p_e1 = __ldg(row_ptr + p_row + 1);
+    }
+    uint32_t n_issued = 0, n_done = 0;
+    // Issue batches until the ring is full or the team's rows are exhausted.
+    auto produce = [&]() {
+        while (n_issued - n_done <= ring_mask) {
+            while (p_row < re && p_e >= p_e1) {
+                p_row += n_teams;
+                if (p_row < re) {
+                    p_e = __ldg(row_ptr + p_row);
+                    p_e1 = __ldg(row_ptr + p_row + 1);
+                }
+            }
+            if (p_row >= re) return;
+            int col[4];
+            T a[4];
+            team_fetch<T, G, 4>(col_idx, val, p_e, p_e1, g, team_base, team_mask, col, a);
+            const uint32_t st = n_issued & ring_mask;
+            __syncwarp(team_mask);  // the stage's previous batch has been read by the team
+            if (g == 0) {
+#pragma unroll
+                for (int u = 0; u < 4; ++u) tval[st * 4 + u] = a[u];
+                fence_proxy_async_smem();
+                mbar_expect_tx(&tbar[st], batch_bytes);
+                // tests only: the gather is left out, so the wait runs out with
+                // nothing in flight
+                if (!p.stall_test)
+                    tma_gather4(tbuf + (size_t)st * stage_elems, &tmap, row0 + col[0],
+                                row0 + col[1], row0 + col[2], row0 + col[3], &tbar[st]);
+            }
+            ++n_issued;
+            p_e += 4;
+        }
+    };
+
     bool timed_out = false;
-    T a_st[2][4];
-    for (int row = rb + team; row < re && !timed_out; row += n_teams) {
+    for (int row = rb + team; row < re; row += n_teams) {
         const size_t roff = (size_t)row * ld;
         T xk[CPT][VPT], xo[CPT][VPT];
 #pragma unroll
@@ -848,43 +901,19 @@ __global__ void __launch_bounds__(kBlock, 2) step_tmag_kernel(const StepParams<T
         for (int cc = 0; cc < CPT; ++cc)
 #pragma unroll
             for (int j = 0; j < VPT; ++j) y[cc][j] = T(0);
-        // batch b: entries e0 + 4b .. e0 + 4b + 3 (past e1: column 0, value 0)
-        auto issue = [&](int b) {
-            int col[4];
-            T a[4];
-            team_fetch<T, G, 4>(col_idx, val, e0 + 4 * b, e1, g, team_base, team_mask, col, a);
-            const int st = b & 1;
-#pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                if (st == 0) a_st[0][u] = a[u];
-                else a_st[1][u] = a[u];
-            }
-            __syncwarp(team_mask);  // the stage's previous rows have been read by the team
-            if (g == 0) {
-                fence_proxy_async_smem();
-                mbar_expect_tx(&tbar[st], batch_bytes);
-                // tests only: the gather is left out, so the wait runs out with
-                // nothing in flight
-                if (!p.stall_test)
-                    tma_gather4(tbuf + (size_t)st * stage_elems, &tmap, row0 + col[0],
-                                row0 + col[1], row0 + col[2], row0 + col[3], &tbar[st]);
-            }
-            ++issued[st];
-        };
-        if (nb > 0) issue(0);
         for (int b = 0; b < nb; ++b) {
-            if (b + 1 < nb) issue(b + 1);
-            const int st = b & 1;
-            const bool ok = mbar_wait_bounded(&tbar[st], done[st] & 1u, p.spin_cycles);
+            produce();
+            const uint32_t st = n_done & ring_mask;
+            const bool ok = mbar_wait_bounded(&tbar[st], (n_done >> log2_depth) & 1u,
+                                              p.spin_cycles);
             if (__any_sync(team_mask, !ok)) {  // the team leaves together
                 timed_out = true;
                 break;
             }
-            ++done[st];
             const T *buf = tbuf + (size_t)st * stage_elems;
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
-                const T au = st == 0 ? a_st[0][u] : a_st[1][u];
+                const T au = tval[st * 4 + u];
 #pragma unroll
                 for (int cc = 0; cc < CPT; ++cc) {
                     if (valid[cc]) {
@@ -895,6 +924,7 @@ __global__ void __launch_bounds__(kBlock, 2) step_tmag_kernel(const StepParams<T
                     }
                 }
             }
+            ++n_done;
         }
         if (timed_out) break;
         T rr = T(0), ss = T(0);
@@ -926,12 +956,12 @@ __global__ void __launch_bounds__(kBlock, 2) step_tmag_kernel(const StepParams<T
     if (timed_out) {
         // a wait ran out: record it and let the gathers still in flight land (bounded)
         if (g == 0) atomicOr(p.status, 4);
-#pragma unroll
-        for (int st = 0; st < 2; ++st)
-            while (done[st] < issued[st]) {
-                if (!mbar_wait_bounded(&tbar[st], done[st] & 1u, p.spin_cycles)) break;
-                ++done[st];
-            }
+        while (n_done < n_issued) {
+            if (!mbar_wait_bounded(&tbar[n_done & ring_mask], (n_done >> log2_depth) & 1u,
+                                   p.spin_cycles))
+                break;
+            ++n_done;
+        }
     }
     if constexpr (PV) {
         double *out = p.part + (size_t)blockIdx.x * 2 * p.pv;
@@ -960,7 +990,7 @@ StepFn<T> pick_staged(int G, int CPT, bool per_vec) {
 }
 
 template <typename T>
-using TmagFn = void (*)(const StepParams<T>, const CUtensorMap);
+using TmagFn = void (*)(const StepParams<T>, const CUtensorMap, int);
 
 template <typename T>
 TmagFn<T> pick_tmag(int G, int CPT, bool per_vec) {
@@ -1247,6 +1277,10 @@ int grid_for(int64_t work, int block, int cap) {
 
 }  // namespace
 
+int tmag_depth(int block, int team, int ld, int esz, int asked) {
+    return tmag_ring_depth(block, team, ld, esz, asked);
+}
+
 // ---- launchers -------------------------------------------------------------------
 void launch_validate_csr(int64_t n_rows, int64_t nnz, const int32_t *row_ptr,
                          const int32_t *col_idx, int B, const int32_t *seg_row0, int *flag,
@@ -1293,7 +1327,11 @@ bool shape_supported(int precision, const Shape &sh, int ld) {
         if (!(precision == DOS_PREC_F64 ? (void *)pick_tmag<double>(sh.team, sh.chunks, false)
                                         : (void *)pick_tmag<float>(sh.team, sh.chunks, false)))
             return false;
-        if (tmag_smem(sh.block, sh.team, ld, esz) > (size_t)227 * 1024) return false;
+        if (sh.depth != 0 && sh.depth != 2 && sh.depth != 4 && sh.depth != 8) return false;
+        const int depth = tmag_ring_depth(sh.block, sh.team, ld, esz, sh.depth);
+        if (tmag_smem(sh.block, sh.team, ld, esz, depth) > (size_t)227 * 1024) return false;
+    } else if (sh.depth != 0) {
+        return false;  // the ring depth belongs to the TMA-gather variant
     }
     return sh.team * sh.chunks * vpt >= ld;
 }
@@ -1330,7 +1368,9 @@ static int occupancy_t(const Shape &sh, int ld) {
     } else if (sh.staged == 2) {
         auto fn = pick_tmag<T>(sh.team, sh.chunks, false);
         if (!fn) return 0;
-        const size_t sm = tmag_smem(sh.block, sh.team, ld, sizeof(T));
+        const int esz = (int)sizeof(T);
+        const size_t sm = tmag_smem(sh.block, sh.team, ld, esz,
+                                    tmag_ring_depth(sh.block, sh.team, ld, esz, sh.depth));
         allow_smem_fn((const void *)fn, sm);
         DOS_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, sh.block, sm));
     } else {
@@ -1419,7 +1459,10 @@ static void launch_step_t(const SweepArgs &a, int k, int slot, cudaStream_t s) {
         if (!fn) throw Error{DOS_EINVAL, "unsupported TMA-gather launch shape"};
         p.panel_rows = 0;
         const CUtensorMap tmap = vector_block_map<T>(p.xc, a.n_rows, a.ld);
-        const size_t sm = tmag_smem(a.shape.block, a.shape.team, a.ld, sizeof(T));
+        const int esz = (int)sizeof(T);
+        const int depth = tmag_ring_depth(a.shape.block, a.shape.team, a.ld, esz, a.shape.depth);
+        const int log2_depth = depth == 8 ? 3 : depth == 4 ? 2 : 1;
+        const size_t sm = tmag_smem(a.shape.block, a.shape.team, a.ld, esz, depth);
         allow_smem_fn((const void *)fn, sm);
         cudaLaunchConfig_t cfg = {};
         cfg.gridDim = dim3((unsigned)a.n_tiles);
@@ -1431,7 +1474,7 @@ static void launch_step_t(const SweepArgs &a, int k, int slot, cudaStream_t s) {
         attr[0].val.programmaticStreamSerializationAllowed = 1;
         cfg.attrs = attr;
         cfg.numAttrs = a.pdl ? 1 : 0;
-        DOS_CUDA_TRY(cudaLaunchKernelEx(&cfg, fn, p, tmap));
+        DOS_CUDA_TRY(cudaLaunchKernelEx(&cfg, fn, p, tmap, log2_depth));
     } else {
         // direct loads; also the first step of the TMA-gather variant
         auto fn = k == 0 ? pick_first<T>(a.per_vec != 0)

@@ -48,7 +48,8 @@ class dos_csr(C.Structure):
 
 class dos_launch(C.Structure):
     _fields_ = [("team", C.c_int32), ("chunks", C.c_int32), ("block", C.c_int32),
-                ("tiles", C.c_int32), ("staged", C.c_int32), ("chunk_bytes", C.c_int32)]
+                ("tiles", C.c_int32), ("staged", C.c_int32), ("chunk_bytes", C.c_int32),
+                ("depth", C.c_int32)]
 
 
 class dos_kpm_opts(C.Structure):
@@ -266,7 +267,7 @@ class Context:
         if launch:
             o.launch = dos_launch(*[int(launch.get(k, 0))
                                     for k in ("team", "chunks", "block", "tiles", "staged",
-                                              "chunk_bytes")])
+                                              "chunk_bytes", "depth")])
         return o
 
     def dos_kpm_moments(self, A: CSRArrays, lb: float, ub: float, M: int, n_v: int, seed: int,
@@ -312,7 +313,7 @@ class Context:
                                   C.byref(best), C.byref(ms), _stream_of(A.row_ptr)))
         return {"team": best.team, "chunks": best.chunks, "block": best.block,
                 "tiles": best.tiles, "staged": best.staged,
-                "chunk_bytes": best.chunk_bytes}, ms.value
+                "chunk_bytes": best.chunk_bytes, "depth": best.depth}, ms.value
 
     def dos_reconstruct(self, mu, M: int, damping="jackson", lb: float = -1.0, ub: float = 1.0,
                         t=None, N_t: int = 1000, phi_hat=None, phi_lambda=None,

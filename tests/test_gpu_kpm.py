@@ -232,11 +232,15 @@ def test_wide_chunk_parity(ctx, precision, launch):
 @pytest.mark.parametrize("launch", [{"staged": 3}, {"team": 16, "chunks": 1, "staged": 3},
                                     {"team": 8, "chunks": 2, "staged": 3, "tiles": 7},
                                     {"team": 32, "chunks": 2, "staged": 3, "tiles": 500},
-                                    {"team": 32, "chunks": 4, "staged": 3}])
+                                    {"team": 32, "chunks": 4, "staged": 3},
+                                    {"team": 16, "chunks": 1, "staged": 3, "depth": 8},
+                                    {"team": 16, "chunks": 2, "staged": 3, "depth": 2,
+                                     "tiles": 3}])
 def test_tma_gather_parity(ctx, precision, launch):
-    """Rows gathered by TMA (tile::gather4, four nonzeros per copy): a lattice, and a
-    random matrix with empty rows and one dense row (batches padded past the row's
-    end), per-vector and total moments, several tile counts and n_v."""
+    """Rows gathered by TMA (tile::gather4, four nonzeros per copy, a ring of 2, 4 or
+    8 batches per team running ahead across rows): a lattice, and a random matrix with
+    empty rows and one dense row (batches padded past the row's end), per-vector and
+    total moments, several tile counts and n_v."""
     from paper_1308_5467_gb300 import dos
     dtype = np.float64 if precision == "f64" else np.float32
     per_chunk = 2 if precision == "f64" else 4
@@ -246,7 +250,7 @@ def test_tma_gather_parity(ctx, precision, launch):
         if lb is None:
             lb, ub = obounds.bounds(A, "gershgorin", pad_frac=0.01)
         for n_v in (64, 20):
-            if launch.get("team", 16) * launch.get("chunks", 1) * per_chunk < n_v:
+            if "team" in launch and launch["team"] * launch.get("chunks", 1) * per_chunk < n_v:
                 with pytest.raises(dos.DosError):
                     ctx.dos_kpm_moments(dev(Aw), lb, ub, 30, n_v, seed=5, precision=precision,
                                         launch=launch)
@@ -281,9 +285,11 @@ def test_tma_gather_wait_timeout_is_reported(ctx):
 def test_unknown_variant_is_rejected(ctx):
     from paper_1308_5467_gb300 import dos
     A = anderson_3d(6, 6.0, seed=4)
-    with pytest.raises(dos.DosError):
-        ctx.dos_kpm_moments(dev(A), -9.6, 9.6, 10, 16, seed=5, precision="f64",
-                            launch={"staged": 4})
+    for launch in ({"staged": 4}, {"staged": 3, "depth": 3}, {"staged": 3, "depth": 16},
+                   {"staged": 1, "depth": 4}, {"depth": 4}):
+        with pytest.raises(dos.DosError):
+            ctx.dos_kpm_moments(dev(A), -9.6, 9.6, 10, 16, seed=5, precision="f64",
+                                launch=launch)
 
 
 def test_wide_chunks_need_whole_32_byte_rows(ctx):
