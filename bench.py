@@ -86,6 +86,15 @@ def make_matrix(w):
     raise ValueError(w["kind"])
 
 
+def step_kernel_name(shape, precision):
+    """Name of the fused step kernel a launch shape runs (public staged values:
+    1 direct loads, 2 TMA row panels, 3 TMA gathers; 0 / absent: direct)."""
+    t = "double" if precision == "f64" else "float"
+    staged = (shape or {}).get("staged", 1)
+    base = {2: "step_staged_kernel", 3: "step_tmag_kernel"}.get(staged, "step_kernel")
+    return f"{base}<{t}>"
+
+
 def algorithmic_bytes_per_step(n, nnz, n_v, precision):
     """Compulsory bytes of one fused step: CSR once (col_idx 4 B + value) plus
     row_ptr, X_k read once, X_{k-1} read and X_{k+1} written."""
@@ -556,7 +565,7 @@ def run_method(args, w, world, rank, local, device):
         achieved = alg / (launch_ms * 1e-3) / 1e9
         roofline = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"],
                     "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"], "traffic": None,
-                    "peak_source": peak_kind, "kernel": "step_kernel",
+                    "peak_source": peak_kind, "kernel": step_kernel_name(tuned_shape, prec),
                     "algorithmic_bytes_per_launch": alg, "launch_ms": launch_ms}
         metric, unit = "Legendre moments/sec (nnz*n_v*M/s)", "moments/s"
 
@@ -722,7 +731,7 @@ def main():
         traffic = tr["bytes"] if tr and tr["src"] == kernel_source_hash() and same_launch else None
         roofline = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"],
                     "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"], "traffic": traffic,
-                    "peak_source": peak_kind, "kernel": "step_kernel<float>",
+                    "peak_source": peak_kind, "kernel": step_kernel_name(tuned_shape, prec),
                     "algorithmic_bytes_per_launch": alg, "launch_ms": launch_ms}
     else:
         flops = 2 * fma_per_step(A.n, A.nnz, n_v)
@@ -730,7 +739,7 @@ def main():
         roofline = {"bound": "alu", "achieved": achieved, "peak": 1.25, "unit": "TFLOP/s",
                     "frac": achieved / 1.25, "traffic": None,
                     "peak_source": "nominal FP64 rate of GB300 (1.25 TFLOP/s)",
-                    "kernel": "step_kernel<double>", "flops_per_launch": flops,
+                    "kernel": step_kernel_name(tuned_shape, prec), "flops_per_launch": flops,
                     "launch_ms": launch_ms}
 
     forms = {prec: {"ms_per_step": ms, "value": value, "e1": e1, "einf": einf}}
@@ -744,6 +753,7 @@ def main():
                         "roofline": {"bound": "alu", "achieved": fl / (l64 * 1e-3) / 1e12,
                                      "peak": 1.25, "unit": "TFLOP/s",
                                      "frac": fl / (l64 * 1e-3) / 1e12 / 1.25,
+                                     "kernel": step_kernel_name(tuned64, "f64"),
                                      "launch_ms": l64},
                         "max_abs_diff_vs_f32": float(np.abs(out64[0] - mu).max())}
 

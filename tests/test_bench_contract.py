@@ -37,3 +37,12 @@ def test_algorithmic_bytes_formula():
     # Anderson 64^3, n_v = 64: CSR 1,835,008 x (4 + 4) + 4 (n + 1), three blocks of n x 64 floats
     assert bench.algorithmic_bytes_per_step(262144, 1835008, 64, "f32") == 217055236
     assert bench.fma_per_step(262144, 1835008, 64) == 1835008 * 64 + 4 * 262144 * 64
+
+
+def test_roofline_names_the_variant_that_ran():
+    sys.path.insert(0, ROOT)
+    import bench
+    assert bench.step_kernel_name({"staged": 1, "chunk_bytes": 32}, "f32") == "step_kernel<float>"
+    assert bench.step_kernel_name({"staged": 2}, "f64") == "step_staged_kernel<double>"
+    assert bench.step_kernel_name({"staged": 3, "depth": 2}, "f32") == "step_tmag_kernel<float>"
+    assert bench.step_kernel_name(None, "f64") == "step_kernel<double>"
