@@ -213,9 +213,18 @@ def cpu_baseline(A, lb, ub, M, n_v_full, seed, target_s=12.0):
     t = time.perf_counter() - t0
     value = A.nnz * nv * Ms / t
     scaled = "" if Ms == M else f", timed at M={Ms} and scaled linearly to M={M}"
+    # the same oracle on one thread, for reference: a few vectors, ~target_s / 3
+    per_vec_1 = t * min(cores, nv) / nv
+    n1 = int(max(1, min(nv, (target_s / 3) / max(per_vec_1, 1e-6))))
+    t0 = time.perf_counter()
+    okpm.kpm_moments_per_vector(A, lb, ub, Ms, n1, seed, nthreads=1)
+    t1 = time.perf_counter() - t0
+    single = {"value": A.nnz * n1 * Ms / t1, "cores": 1,
+              "sample": f"{n1} start vectors, {t1:.1f} s wall on 1 thread{scaled}"}
     return {"value": value, "unit": "moments/s", "cores": min(cores, nv), "kind": "oracle",
             "sample": f"{nv} start vectors of the same workload (M={Ms}, doubling mode, FP64), "
-                      f"{t:.1f} s wall on {min(cores, nv)} threads{scaled}"}
+                      f"{t:.1f} s wall on {min(cores, nv)} threads{scaled}",
+            "single_thread": single}
 
 
 def run_reference(args):
