@@ -960,14 +960,14 @@ int dos_lanczos_ritz(dos_ctx *ctx, const dos_csr *Adesc, int M, int n_v, uint64_
         const int nb_axpy = lanczos_blocks(ctx->num_sms, A.n, ld);
         const int nb_spmm = lanczos_team_blocks(ctx->num_sms, A.n, ld);
         const int nb = std::max(nb_axpy, nb_spmm);  // rows of the partial-sum buffer
-        // scratch: two vector blocks | partials | alpha, beta [M][ld] | m_used | QL work | out
+        // scratch: two vector blocks | partials | alpha, beta [M][ld] | out | 1/beta | m_used
         const size_t nvec = (size_t)A.n * ld;
         const size_t n_dbl = 2 * nvec + (size_t)nb * ld + 2 * (size_t)M * ld +
-                             3 * (size_t)n_v * M + 2 * (size_t)n_v * M + n_v + ld;
+                             2 * (size_t)n_v * M + n_v + ld;
         double *buf = (double *)ctx->lz_buf.get(n_dbl * sizeof(double));
         double *q0 = buf, *q1 = q0 + nvec, *part = q1 + nvec, *alpha = part + (size_t)nb * ld;
-        double *beta = alpha + (size_t)M * ld, *work = beta + (size_t)M * ld;
-        double *th = work + 3 * (size_t)n_v * M, *wt = th + (size_t)n_v * M;
+        double *beta = alpha + (size_t)M * ld;
+        double *th = beta + (size_t)M * ld, *wt = th + (size_t)n_v * M;
         double *inv_beta = wt + (size_t)n_v * M;
         int *mu_dev = (int *)(inv_beta + ld);
         SweepArgs a{};
@@ -1006,7 +1006,7 @@ int dos_lanczos_ritz(dos_ctx *ctx, const dos_csr *Adesc, int M, int n_v, uint64_
         }
         // steps kept per run (invariant-subspace rule) and the Ritz pairs, on the device
         launch_lanczos_steps(alpha, beta, M, ld, n_v, mu_dev, s);
-        launch_tridiag_ritz(alpha, beta, mu_dev, M, ld, n_v, work, th, wt, s);
+        launch_tridiag_ritz(alpha, beta, mu_dev, M, ld, n_v, th, wt, s);
         copy_out(theta, th, (size_t)n_v * M * sizeof(double), s);
         copy_out(weight, wt, (size_t)n_v * M * sizeof(double), s);
         std::vector<int> mus(n_v);

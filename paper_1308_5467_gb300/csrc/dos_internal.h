@@ -296,7 +296,7 @@ void launch_lanczos_bounds(const double *alpha, const double *beta, int k, doubl
                            double *out, cudaStream_t s);
 // work: 3 * n_vec * M doubles
 void launch_tridiag_ritz(const double *alpha, const double *beta, const int *m_used, int M, int ld,
-                         int n_vec, double *work, double *theta, double *weight, cudaStream_t s);
+                         int n_vec, double *theta, double *weight, cudaStream_t s);
 void launch_weighted_gauss(const double *pts, const double *w, int64_t n_pts, double scale,
                            double sigma, const double *x, double x0, double h, int N_x,
                            double *out, cudaStream_t s);

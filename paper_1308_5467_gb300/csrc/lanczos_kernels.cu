@@ -161,22 +161,26 @@ __device__ void ql_one_row(int m, double *__restrict__ dd, double *__restrict__ 
 __global__ void tridiag_ritz_kernel(const double *__restrict__ alpha,
                                     const double *__restrict__ beta,  // [M][ld], beta[j] = ||f_{j+1}||
                                     const int *__restrict__ m_used, int M, int ld, int n_vec,
-                                    double *__restrict__ d, double *__restrict__ e,
-                                    double *__restrict__ z, double *__restrict__ theta,
-                                    double *__restrict__ weight) {
-    // one run per warp (lane 0): runs deflate at different points, and runs sharing a
-    // warp would execute the union of their iteration paths
+                                    double *__restrict__ theta, double *__restrict__ weight) {
+    // One run per block; lane 0 runs the QL sweep.  Runs deflate at different
+    // points, and runs sharing a warp would execute the union of their iteration
+    // paths.  The run's d, e, z live in shared memory (3 M doubles): the sweep
+    // reads e[i] at the head of each rotation's dependent FP64 chain, and a
+    // shared-memory load is far shorter than a trip to L2.
+    extern __shared__ double tri_sm[];
     const int l = blockIdx.x;
-    if (threadIdx.x != 0 || l >= n_vec) return;
+    if (l >= n_vec) return;
     const int m = m_used[l];
-    double *dd = d + (size_t)l * M, *ee = e + (size_t)l * M, *zz = z + (size_t)l * M;
-    for (int i = 0; i < m; ++i) {
+    double *dd = tri_sm, *ee = tri_sm + M, *zz = tri_sm + 2 * (size_t)M;
+    for (int i = threadIdx.x; i < m; i += blockDim.x) {
         dd[i] = alpha[(size_t)i * ld + l];
         ee[i] = i + 1 < m ? beta[(size_t)i * ld + l] : 0.0;
         zz[i] = i == 0 ? 1.0 : 0.0;
     }
-    ql_one_row(m, dd, ee, zz);
-    for (int i = 0; i < M; ++i) {
+    __syncthreads();
+    if (threadIdx.x == 0) ql_one_row(m, dd, ee, zz);
+    __syncthreads();
+    for (int i = threadIdx.x; i < M; i += blockDim.x) {
         theta[(size_t)l * M + i] = i < m ? dd[i] : 0.0;
         weight[(size_t)l * M + i] = i < m ? zz[i] * zz[i] : 0.0;
     }
@@ -369,10 +373,12 @@ void launch_unit_scale(int64_t n, int ld, int n_vec, double *q, int num_sms, cud
 }
 
 void launch_tridiag_ritz(const double *alpha, const double *beta, const int *m_used, int M, int ld,
-                         int n_vec, double *work, double *theta, double *weight, cudaStream_t s) {
-    double *d = work, *e = work + (size_t)n_vec * M, *z = work + 2 * (size_t)n_vec * M;
-    tridiag_ritz_kernel<<<n_vec, 32, 0, s>>>(alpha, beta, m_used, M, ld, n_vec, d, e, z, theta,
-                                             weight);
+                         int n_vec, double *theta, double *weight, cudaStream_t s) {
+    const size_t smem = 3 * (size_t)M * sizeof(double);  // M <= 4096: at most 96 KB
+    if (smem > 48 * 1024)
+        DOS_CUDA_TRY(cudaFuncSetAttribute((const void *)tridiag_ritz_kernel,
+                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    tridiag_ritz_kernel<<<n_vec, 32, smem, s>>>(alpha, beta, m_used, M, ld, n_vec, theta, weight);
     DOS_LAUNCHED();
 }
 
