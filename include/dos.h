@@ -367,10 +367,15 @@ int dos_smoothed_error(dos_ctx *ctx, const double *mu, int M, int damping, doubl
  * recurrence without reorthogonalisation, FP64) from the unit-normalised
  * Rademacher start vectors l = 0..n_v-1 of `seed` (the vectors of
  * dos_kpm_moments), advanced together as one block SpMM per step.  For each
- * run the eigenvalues theta (Ritz values) of its tridiagonal T and the squared
- * first components of the unit eigenvectors (weights, summing to one) are
- * computed on the device (implicit QL, Golub-Welsch): the quadrature of
- * Eq. landist / Eq. tauexpand.  A run that reaches an invariant subspace
+ * run the eigenvalues theta (Ritz values, ascending) of its tridiagonal T and the
+ * squared first components of the unit eigenvectors (weights, summing to one)
+ * are computed on the device (Golub-Welsch: the nodes by bisection on Sturm
+ * counts, each weight as the residue of e_1^T (zI - T)^{-1} e_1 by a contour
+ * integral): the quadrature of Eq. landist / Eq. tauexpand.  Ritz values closer
+ * than 1e-8 of the spectral scale (the copies that loss of orthogonality makes)
+ * are reported as one node: the group's first entry holds its total weight at its
+ * weight centroid, the other entries keep their Ritz value with weight 0.  A run
+ * that reaches an invariant subspace
  * (beta_j <= 1e-12 * its running norm estimate) stops after j+1 steps: its
  * remaining entries are 0 and m_used[l] = j+1.
  *   A: FP64 values.  1 <= M <= min(n, 4096), 1 <= n_v <= 256.

@@ -91,10 +91,7 @@ __global__ void unit_scale_kernel(int64_t n, int ld, int n_vec, double *__restri
         q[t] = (t % ld) < n_vec ? q[t] * inv : 0.0;
 }
 
-// Golub-Welsch on each run's tridiagonal T (diagonal alpha, off-diagonal beta):
-// implicit QL with Wilkinson-style shifts (the classical tql1/tql2 iteration),
-// applying every plane rotation to the first row of the eigenvector matrix only.
-// One warp per run (its first lane works); work arrays in global scratch.
+// Used for the Lanczos bounds (one thread; work arrays in global scratch).
 // Implicit QL with Wilkinson-style shifts (the classical tql1/tql2 iteration) on
 // the symmetric tridiagonal (dd: diagonal, ee: off-diagonal, ee[m-1] = 0),
 // applying every plane rotation to one row zz of the eigenvector matrix (start
@@ -158,31 +155,203 @@ __device__ void ql_one_row(int m, double *__restrict__ dd, double *__restrict__ 
     }
 }
 
-__global__ void tridiag_ritz_kernel(const double *__restrict__ alpha,
-                                    const double *__restrict__ beta,  // [M][ld], beta[j] = ||f_{j+1}||
-                                    const int *__restrict__ m_used, int M, int ld, int n_vec,
-                                    double *__restrict__ theta, double *__restrict__ weight) {
-    // One run per block; lane 0 runs the QL sweep.  Runs deflate at different
-    // points, and runs sharing a warp would execute the union of their iteration
-    // paths.  The run's d, e, z live in shared memory (3 M doubles): the sweep
-    // reads e[i] at the head of each rotation's dependent FP64 chain, and a
-    // shared-memory load is far shorter than a trip to L2.
-    extern __shared__ double tri_sm[];
+// ---- Ritz pairs of the n_v Lanczos tridiagonals (Golub–Welsch quadrature) --------
+// Nodes: the eigenvalues of each run's T (diagonal alpha_0..alpha_{m-1}, off-diagonal
+// beta_0..beta_{m-2}), by bisection on Sturm counts, one thread per eigenvalue.
+// Weights: the Gauss weight of node lambda_j is the residue of
+// r(z) = e_1^T (zI - T)^{-1} e_1 at lambda_j, i.e. the square of the first component
+// of its unit eigenvector.  It is taken as the contour integral
+// (1/2 pi i) \oint r(z) dz over a circle around lambda_j, by the trapezoid rule on
+// K = 64 points (one lane per conjugate pair), with r(z) the Stieltjes continued
+// fraction 1 / (z - alpha_0 - beta_0^2 / (z - alpha_1 - ...)) evaluated from the
+// bottom up.  Off the real axis every partial denominator has |Im t_i| >= |Im z|,
+// so the evaluation is stable and bounded.  Eigenvalues closer than 1e-8 of the
+// spectral scale (the copies that loss of orthogonality produces), or closer than
+// twice the width of a neighbouring group, are merged into one group: its total
+// weight, and its weight centroid (from the second integral \oint (z - c) r(z) dz),
+// go to its first member, the others get weight 0.  The total and the centroid are
+// well-conditioned where the split is not, and they keep the blurred DOS and the
+// quadrature's moments to second order in the group's width.  Each circle's radius is half the
+// distance from the group's centre to the nearest other node, so every other pole
+// is at least twice the radius away and every member within 0.4 of it: the
+// trapezoid error is below 2^-60 of a neighbouring weight.
+// Both kernels first scale T by a power of two so its Gershgorin bound is in
+// [1, 2) (exact; the results are scaled back), which keeps the Sturm recurrence
+// and the continued fraction far from overflow.
+constexpr int kRitzPoints = 64;  // K, trapezoid points on each circle (32 lanes x 2)
+
+// Loads run l's tridiagonal into shared memory, scaled: a[i] = f alpha_i,
+// b2[i] = (f beta_i)^2; returns f and the scaled Gershgorin interval.
+__device__ void load_scaled_tridiagonal(const double *__restrict__ alpha,
+                                        const double *__restrict__ beta, int l, int m, int ld,
+                                        double *a, double *b2, double *sc /* f, lo, hi */) {
+    for (int i = threadIdx.x; i < m; i += blockDim.x) {
+        a[i] = alpha[(size_t)i * ld + l];
+        b2[i] = i + 1 < m ? beta[(size_t)i * ld + l] : 0.0;  // raw beta for now
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double lo = INFINITY, hi = -INFINITY;
+        for (int i = 0; i < m; ++i) {
+            const double r = (i > 0 ? fabs(b2[i - 1]) : 0.0) + fabs(b2[i]);
+            lo = fmin(lo, a[i] - r);
+            hi = fmax(hi, a[i] + r);
+        }
+        const double scale = fmax(fabs(lo), fabs(hi));
+        double f = 1.0;
+        if (scale >= 2.2250738585072014e-308 && scale < INFINITY) {
+            int e;
+            frexp(scale, &e);    // scale = q 2^e, q in [0.5, 1)
+            f = ldexp(1.0, 1 - e);  // f scale in [1, 2)
+        }
+        sc[0] = f;
+        sc[1] = lo * f;
+        sc[2] = hi * f;
+    }
+    __syncthreads();
+    const double f = sc[0];
+    for (int i = threadIdx.x; i < m; i += blockDim.x) {
+        a[i] *= f;
+        const double bb = b2[i] * f;
+        b2[i] = bb * bb;
+    }
+    __syncthreads();
+}
+
+// Number of eigenvalues of T below x: m minus the sign changes of the leading
+// principal minors D_i = det(x I - T_i) (D_0 = 1, D_1 = x - a_0,
+// D_i = (x - a_{i-1}) D_{i-1} - b2_{i-2} D_{i-2}).  A zero minor counts as positive;
+// for an unreduced T an interior zero is flanked by opposite signs, so either
+// choice gives the same count.  The last two minors are rescaled together by an
+// exact power of two (the larger into [1, 2)) whenever the larger leaves
+// [2^-400, 2^400]; the exponents are read as integers, off the FP64 chain.
+__device__ int sturm_below(const double *a, const double *b2, int m, double x) {
+    double p0 = 1.0, p1 = x - a[0];
+    int changes = p1 < 0.0 ? 1 : 0;
+    for (int i = 1; i < m; ++i) {
+        const double p2 = fma(x - a[i], p1, -b2[i - 1] * p0);
+        changes += (p2 < 0.0) != (p1 < 0.0) ? 1 : 0;
+        p0 = p1;
+        p1 = p2;
+        const int e = max((int)((__double_as_longlong(p0) >> 52) & 0x7ff),
+                          (int)((__double_as_longlong(p1) >> 52) & 0x7ff));
+        if (e > 1023 + 400 || (e < 1023 - 400 && e != 0)) {
+            const double s = __longlong_as_double((long long)(2046 - e) << 52);  // 2^(1023-e)
+            p0 *= s;
+            p1 *= s;
+        }
+    }
+    return m - changes;
+}
+
+__global__ void ritz_bisect_kernel(const double *__restrict__ alpha,
+                                   const double *__restrict__ beta,
+                                   const int *__restrict__ m_used, int M, int ld, int n_vec,
+                                   double *__restrict__ theta) {
+    extern __shared__ double rz_sm[];
+    __shared__ double sc[3];
     const int l = blockIdx.x;
     if (l >= n_vec) return;
     const int m = m_used[l];
-    double *dd = tri_sm, *ee = tri_sm + M, *zz = tri_sm + 2 * (size_t)M;
-    for (int i = threadIdx.x; i < m; i += blockDim.x) {
-        dd[i] = alpha[(size_t)i * ld + l];
-        ee[i] = i + 1 < m ? beta[(size_t)i * ld + l] : 0.0;
-        zz[i] = i == 0 ? 1.0 : 0.0;
+    double *th = theta + (size_t)l * M;
+    for (int j = max(m, 0) + threadIdx.x; j < M; j += blockDim.x) th[j] = 0.0;
+    if (m <= 0) return;
+    double *a = rz_sm, *b2 = rz_sm + M;
+    load_scaled_tridiagonal(alpha, beta, l, m, ld, a, b2, sc);
+    const double f = sc[0];
+    const double scale = fmax(fabs(sc[1]), fabs(sc[2]));
+    const double eps = 2.220446049250313e-16;
+    for (int j = threadIdx.x; j < m; j += blockDim.x) {
+        double lo = sc[1] - 2.0 * eps * scale, hi = sc[2] + 2.0 * eps * scale;
+        for (int it = 0; it < 128; ++it) {
+            if (hi - lo <= fmax(4.0 * eps * fmax(fabs(lo), fabs(hi)), eps * scale)) break;
+            const double mid = 0.5 * (lo + hi);
+            if (sturm_below(a, b2, m, mid) > j) hi = mid;
+            else lo = mid;
+        }
+        th[j] = 0.5 * (lo + hi) / f;
+    }
+}
+
+__global__ void ritz_weight_kernel(const double *__restrict__ alpha,
+                                   const double *__restrict__ beta,
+                                   const int *__restrict__ m_used, int M, int ld, int n_vec,
+                                   double *__restrict__ theta, double *__restrict__ weight) {
+    extern __shared__ double rz_sm[];
+    __shared__ double sc[3];
+    __shared__ int n_groups;
+    const int l = blockIdx.x;
+    if (l >= n_vec) return;
+    const int m = m_used[l];
+    double *wt = weight + (size_t)l * M;
+    for (int j = max(m, 0) + threadIdx.x; j < M; j += blockDim.x) wt[j] = 0.0;
+    if (m <= 0) return;
+    double *a = rz_sm, *b2 = rz_sm + M, *lam = rz_sm + 2 * (size_t)M;
+    int *gs = reinterpret_cast<int *>(rz_sm + 3 * (size_t)M), *ge = gs + M;
+    load_scaled_tridiagonal(alpha, beta, l, m, ld, a, b2, sc);
+    const double f = sc[0];
+    const double scale = fmax(fabs(sc[1]), fabs(sc[2]));
+    for (int i = threadIdx.x; i < m; i += blockDim.x) lam[i] = theta[(size_t)l * M + i] * f;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        // groups of the (ascending) nodes, merged left to right on a stack until every
+        // gap is at least 1e-8 scale and twice the wider of its two groups
+        int top = 0;
+        for (int j = 0; j < m; ++j) {
+            int s = j, e = j;
+            while (top > 0) {
+                const int ps = gs[top - 1], pe = ge[top - 1];
+                const double gap = lam[s] - lam[pe];
+                const double wd = fmax(lam[pe] - lam[ps], lam[e] - lam[s]);
+                if (gap < 1e-8 * scale || gap < 2.0 * wd) {
+                    s = ps;
+                    --top;
+                } else {
+                    break;
+                }
+            }
+            gs[top] = s;
+            ge[top] = e;
+            ++top;
+        }
+        n_groups = top;
     }
     __syncthreads();
-    if (threadIdx.x == 0) ql_one_row(m, dd, ee, zz);
-    __syncthreads();
-    for (int i = threadIdx.x; i < M; i += blockDim.x) {
-        theta[(size_t)l * M + i] = i < m ? dd[i] : 0.0;
-        weight[(size_t)l * M + i] = i < m ? zz[i] * zz[i] : 0.0;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, n_warps = blockDim.x >> 5;
+    double sn, cs;
+    sincospi((2.0 * lane + 1.0) / kRitzPoints, &sn, &cs);  // this lane's point (upper half)
+    const int ng = n_groups;
+    for (int g = warp; g < ng; g += n_warps) {
+        const int s = gs[g], e = ge[g];
+        const double c = 0.5 * (lam[s] + lam[e]), width = lam[e] - lam[s];
+        double D = INFINITY;
+        if (g > 0) D = fmin(D, c - lam[ge[g - 1]]);
+        if (g + 1 < ng) D = fmin(D, lam[gs[g + 1]] - c);
+        const double rho = D < INFINITY ? 0.5 * D : fmax(fmax(2.0 * width, scale), 1.0);
+        const double zr = c + rho * cs, zi = rho * sn;
+        double tr = zr - a[m - 1], ti = zi;
+        for (int i = m - 2; i >= 0; --i) {
+            const double q = b2[i] / fma(tr, tr, ti * ti);
+            tr = zr - a[i] - q * tr;
+            ti = zi + q * ti;
+        }
+        // r = 1 / t; with zeta = z - c = rho e^{i th}, this point and its conjugate
+        // contribute 2 Re(r zeta) / K to the weight and 2 Re(r zeta^2) / K to the
+        // first moment about c
+        const double inv = 1.0 / fma(tr, tr, ti * ti);
+        double v = rho * inv * fma(tr, cs, ti * sn);
+        double v1 = rho * rho * inv * fma(tr, fma(cs, cs, -sn * sn), ti * (2.0 * sn * cs));
+        for (int off = 16; off > 0; off >>= 1) {
+            v += __shfl_down_sync(0xffffffffu, v, off);
+            v1 += __shfl_down_sync(0xffffffffu, v1, off);
+        }
+        if (lane == 0) {
+            const double W = v * (2.0 / kRitzPoints), M1 = v1 * (2.0 / kRitzPoints);
+            wt[s] = W;
+            if (e > s && W > 0.0)
+                theta[(size_t)l * M + s] = fmin(fmax(c + M1 / W, lam[s]), lam[e]) / f;
+        }
+        for (int q = s + 1 + lane; q <= e; q += 32) wt[q] = 0.0;
     }
 }
 
@@ -374,11 +543,19 @@ void launch_unit_scale(int64_t n, int ld, int n_vec, double *q, int num_sms, cud
 
 void launch_tridiag_ritz(const double *alpha, const double *beta, const int *m_used, int M, int ld,
                          int n_vec, double *theta, double *weight, cudaStream_t s) {
-    const size_t smem = 3 * (size_t)M * sizeof(double);  // M <= 4096: at most 96 KB
-    if (smem > 48 * 1024)
-        DOS_CUDA_TRY(cudaFuncSetAttribute((const void *)tridiag_ritz_kernel,
-                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    tridiag_ritz_kernel<<<n_vec, 32, smem, s>>>(alpha, beta, m_used, M, ld, n_vec, theta, weight);
+    // M <= 4096: bisection 64 KB, weights 96 KB + 32 KB of shared memory at most
+    const size_t sm_b = 2 * (size_t)M * sizeof(double);
+    const size_t sm_w = 3 * (size_t)M * sizeof(double) + 2 * (size_t)M * sizeof(int);
+    if (sm_b > 48 * 1024)
+        DOS_CUDA_TRY(cudaFuncSetAttribute((const void *)ritz_bisect_kernel,
+                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_b));
+    if (sm_w > 48 * 1024)
+        DOS_CUDA_TRY(cudaFuncSetAttribute((const void *)ritz_weight_kernel,
+                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_w));
+    const int tb = M < 1024 ? (M + 31) / 32 * 32 : 1024;
+    ritz_bisect_kernel<<<n_vec, tb, sm_b, s>>>(alpha, beta, m_used, M, ld, n_vec, theta);
+    DOS_LAUNCHED();
+    ritz_weight_kernel<<<n_vec, 512, sm_w, s>>>(alpha, beta, m_used, M, ld, n_vec, theta, weight);
     DOS_LAUNCHED();
 }
 

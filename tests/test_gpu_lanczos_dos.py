@@ -66,6 +66,27 @@ def test_invariant_subspace_and_dos(ctx):
     assert np.abs(phi - ref).max() < 1e-10
 
 
+def test_long_runs_with_ghost_copies(ctx):
+    """M = 300 steps on the 900-row Laplacian: loss of orthogonality makes copies of
+    converged Ritz values (they are merged into one node per group).  Weights are
+    non-negative and sum to one, the Ritz values are ascending, and the blurred DOS
+    equals the oracle's (scipy's eigendecomposition of its own tridiagonals); between
+    two rounding orders of the same runs the blurred DOS moves by ~1e-15."""
+    A = laplacian_2d(30)
+    M, n_v = 300, 4
+    theta, weight, m_used = ctx.dos_lanczos_ritz(dev(A), M, n_v, seed=2)
+    assert np.all(m_used == M)
+    assert weight.min() > -1e-12
+    assert np.abs(weight.sum(axis=1) - 1.0).max() < 1e-11
+    assert np.sum(weight == 0.0) > 0          # groups of copies were merged
+    for l in range(n_v):
+        assert np.all(np.diff(theta[l]) >= -1e-12)
+    x = np.linspace(-1.0, 9.0, 1001)
+    phi = ctx.dos_lanczos_dos(theta, weight, 0.35, x)
+    ref = old.lanczos_dos(A, M, n_v, seed=2, sigma=0.35, x=x)
+    assert np.abs(phi - ref).max() < 1e-9 * np.abs(ref).max()
+
+
 def test_haydock_matches_continued_fraction(ctx):
     A = anderson_3d(10, 6.0, seed=4)
     theta, weight, _ = ctx.dos_lanczos_ritz(dev(A), 30, 6, seed=3)
