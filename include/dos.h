@@ -373,8 +373,9 @@ int dos_smoothed_error(dos_ctx *ctx, const double *mu, int M, int damping, doubl
  * counts, each weight as the residue of e_1^T (zI - T)^{-1} e_1 by a contour
  * integral): the quadrature of Eq. landist / Eq. tauexpand.  Ritz values closer
  * than 1e-8 of the spectral scale (the copies that loss of orthogonality makes)
- * are reported as one node: the group's first entry holds its total weight at its
- * weight centroid, the other entries keep their Ritz value with weight 0.  A run
+ * are reported as one node: the entry just below the group's weight centroid
+ * holds the group's total weight at that centroid, the other entries keep their
+ * Ritz value with weight 0 (theta stays ascending).  A run
  * that reaches an invariant subspace
  * (beta_j <= 1e-12 * its running norm estimate) stops after j+1 steps: its
  * remaining entries are 0 and m_used[l] = j+1.

@@ -168,8 +168,8 @@ __device__ void ql_one_row(int m, double *__restrict__ dd, double *__restrict__ 
 // so the evaluation is stable and bounded.  Eigenvalues closer than 1e-8 of the
 // spectral scale (the copies that loss of orthogonality produces), or closer than
 // twice the width of a neighbouring group, are merged into one group: its total
-// weight, and its weight centroid (from the second integral \oint (z - c) r(z) dz),
-// go to its first member, the others get weight 0.  The total and the centroid are
+// weight, at its weight centroid (from the second integral \oint (z - c) r(z) dz),
+// goes to the member just below the centroid, the others get weight 0.  The total and the centroid are
 // well-conditioned where the split is not, and they keep the blurred DOS and the
 // quadrature's moments to second order in the group's width.  Each circle's radius is half the
 // distance from the group's centre to the nearest other node, so every other pole
@@ -345,13 +345,18 @@ __global__ void ritz_weight_kernel(const double *__restrict__ alpha,
             v += __shfl_down_sync(0xffffffffu, v, off);
             v1 += __shfl_down_sync(0xffffffffu, v1, off);
         }
-        if (lane == 0) {
-            const double W = v * (2.0 / kRitzPoints), M1 = v1 * (2.0 / kRitzPoints);
-            wt[s] = W;
-            if (e > s && W > 0.0)
-                theta[(size_t)l * M + s] = fmin(fmax(c + M1 / W, lam[s]), lam[e]) / f;
+        // lane 0 holds the sums; the group's node goes to the member just below its
+        // centroid, which keeps the Ritz values ascending
+        const double W = __shfl_sync(0xffffffffu, v, 0) * (2.0 / kRitzPoints);
+        const double M1 = __shfl_sync(0xffffffffu, v1, 0) * (2.0 / kRitzPoints);
+        int k = s;
+        double cc = lam[s];
+        if (e > s && W > 0.0) {
+            cc = fmin(fmax(c + M1 / W, lam[s]), lam[e]);
+            while (k < e && lam[k + 1] <= cc) ++k;
         }
-        for (int q = s + 1 + lane; q <= e; q += 32) wt[q] = 0.0;
+        for (int q = s + lane; q <= e; q += 32) wt[q] = q == k ? W : 0.0;
+        if (lane == 0 && e > s) theta[(size_t)l * M + k] = cc / f;
     }
 }
 
