@@ -2,12 +2,14 @@
 // advanced together as a block, Ritz values and Gauss weights per run, and the
 // Gaussian-blurred DOS from them.  FP64 throughout.
 //
-// Block layout as in the moment sweep: Q[i*ld + l].  Step j (per vector l):
+// Block layout as in the moment sweep: Q[i*ld + l].  The Lanczos vectors are kept
+// unnormalised, q_j = s_j u_j with s_j = 1 / beta_{j-1} per column (s_0 = 1), and
+// every pass applies the factors, so no pass rescales a block.  Step j:
 //   w = A q_j - beta_{j-1} q_{j-1}          (SpMM pass, lanczos_team_spmm_kernel in
-//                                            kpm_kernels.cu; w overwrites q_{j-1})
+//                                            kpm_kernels.cu; w overwrites u_{j-1})
 //   alpha_j = q_j . w                        (per-vector partials, fixed-order reduce)
-//   w -= alpha_j q_j;  beta_j = ||w||        (vector pass + reduce)
-//   q_{j+1} = w / beta_j                     (scale pass, in place)
+//   w -= alpha_j q_j;  beta_j = ||w||        (vector pass + reduce; w is u_{j+1},
+//                                             1 / beta_j is s_{j+1})
 // A run whose beta_j falls to 1e-12 times its running norm estimate has reached
 // an invariant subspace; the host keeps its first j+1 coefficients only.
 #include <cuda_runtime.h>
@@ -23,13 +25,14 @@ constexpr int kThreads = 256;
 
 // w -= alpha q (per column), partial ||w||^2 per column
 __global__ void lanczos_axpy_kernel(int64_t n, int ld, const double *__restrict__ alpha,
+                                    const double *__restrict__ s_q,
                                     const double *__restrict__ q, double *__restrict__ w,
                                     double *__restrict__ part, int n_vec) {
     extern __shared__ double sh[];
     const int cols = ld;
     const int rows_per_block = blockDim.x / cols;
     const int rloc = threadIdx.x / cols, l = threadIdx.x % cols;
-    const double a = alpha[l];
+    const double a = alpha[l] * (s_q ? s_q[l] : 1.0);  // q_j = s_j u_j
     double acc = 0.0;
     for (int64_t i = (int64_t)blockIdx.x * rows_per_block + rloc; i < n;
          i += (int64_t)gridDim.x * rows_per_block) {
@@ -47,13 +50,15 @@ __global__ void lanczos_axpy_kernel(int64_t n, int ld, const double *__restrict_
     }
 }
 
-// out[l] = sum over blocks of part[b][l], optionally sqrt; inv (if given) gets
-// 1 / out[l] (0 for a zero sum).  One block per column: each thread sums a
+// v = sum over blocks of part[b][l], optionally sqrt; out[l] = v * scale[l] (scale
+// NULL: 1); inv (if given) gets 1 / v (0 for a zero sum); prod (if given) gets
+// v * prod_by[l] (prod_by NULL: 1).  One block per column: each thread sums a
 // strided slice in order, then a fixed shuffle tree and a fixed warp order, so
 // the result is reproducible.
 __global__ void column_sum_kernel(const double *__restrict__ part, int n_blocks, int ld,
                                   double *__restrict__ out, double *__restrict__ inv,
-                                  int take_sqrt) {
+                                  int take_sqrt, const double *__restrict__ scale,
+                                  double *__restrict__ prod, const double *__restrict__ prod_by) {
     __shared__ double sh[32];
     const int l = blockIdx.x;
     double s = 0.0;
@@ -65,20 +70,9 @@ __global__ void column_sum_kernel(const double *__restrict__ part, int n_blocks,
         double t = 0.0;
         for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += sh[w];
         const double v = take_sqrt ? sqrt(t) : t;
-        out[l] = v;
+        out[l] = scale ? v * scale[l] : v;
         if (inv) inv[l] = v > 0.0 ? 1.0 / v : 0.0;
-    }
-}
-
-// q <- w * (1 / beta) per column (a zero beta leaves the column at zero); the
-// reciprocal comes from column_sum_kernel, so the pass has no FP64 division.
-__global__ void lanczos_scale_kernel(int64_t n, int ld, const double *__restrict__ inv_beta,
-                                     double *__restrict__ w) {
-    const int64_t total = n * ld;
-    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
-         t += (int64_t)gridDim.x * blockDim.x) {
-        const int l = (int)(t % ld);
-        w[t] *= inv_beta[l];
+        if (prod) prod[l] = prod_by ? v * prod_by[l] : v;
     }
 }
 
@@ -518,24 +512,20 @@ int lanczos_blocks(int num_sms, int64_t n, int ld) {
     return (int)std::max<int64_t>(1, std::min(b, cap));
 }
 
-void launch_lanczos_block_axpy(int64_t n, int ld, int n_vec, const double *alpha, const double *q,
-                               double *w, double *part, int n_blocks, cudaStream_t s) {
+void launch_lanczos_block_axpy(int64_t n, int ld, int n_vec, const double *alpha,
+                               const double *s_q, const double *q, double *w, double *part,
+                               int n_blocks, cudaStream_t s) {
     const int bt = block_threads_for(ld);
-    lanczos_axpy_kernel<<<n_blocks, bt, bt * sizeof(double), s>>>(n, ld, alpha, q, w, part, n_vec);
+    lanczos_axpy_kernel<<<n_blocks, bt, bt * sizeof(double), s>>>(n, ld, alpha, s_q, q, w, part,
+                                                                   n_vec);
     DOS_LAUNCHED();
 }
 
 void launch_column_sum(const double *part, int n_blocks, int ld, double *out, double *inv,
-                       int take_sqrt, cudaStream_t s) {
-    column_sum_kernel<<<ld, 256, 0, s>>>(part, n_blocks, ld, out, inv, take_sqrt);
-    DOS_LAUNCHED();
-}
-
-void launch_lanczos_block_scale(int64_t n, int ld, const double *inv_beta, double *w, int num_sms,
-                                cudaStream_t s) {
-    int64_t g = (n * ld + kThreads - 1) / kThreads;
-    if (g > (int64_t)num_sms * 16) g = (int64_t)num_sms * 16;
-    lanczos_scale_kernel<<<(int)std::max<int64_t>(g, 1), kThreads, 0, s>>>(n, ld, inv_beta, w);
+                       int take_sqrt, const double *scale, double *prod, const double *prod_by,
+                       cudaStream_t s) {
+    column_sum_kernel<<<ld, 256, 0, s>>>(part, n_blocks, ld, out, inv, take_sqrt, scale, prod,
+                                         prod_by);
     DOS_LAUNCHED();
 }
 
