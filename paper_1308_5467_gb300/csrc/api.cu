@@ -960,18 +960,17 @@ int dos_lanczos_ritz(dos_ctx *ctx, const dos_csr *Adesc, int M, int n_v, uint64_
         const int nb_axpy = lanczos_blocks(ctx->num_sms, A.n, ld);
         const int nb_spmm = lanczos_team_blocks(ctx->num_sms, A.n, ld);
         const int nb = std::max(nb_axpy, nb_spmm);  // rows of the partial-sum buffer
-        // scratch: two vector blocks | partials | alpha, beta [M][ld] | out | 1/beta [M][ld]
-        // | c [ld] | m_used
+        // scratch: two vector blocks | partials | alpha, beta [M][ld] | out | s, c, t [ld]
+        // | m_used
         const size_t nvec = (size_t)A.n * ld;
-        const size_t n_dbl = 2 * nvec + (size_t)nb * ld + 3 * (size_t)M * ld + ld +
+        const size_t n_dbl = 2 * nvec + (size_t)nb * ld + 2 * (size_t)M * ld + 3 * (size_t)ld +
                              2 * (size_t)n_v * M + n_v;
         double *buf = (double *)ctx->lz_buf.get(n_dbl * sizeof(double));
         double *q0 = buf, *q1 = q0 + nvec, *part = q1 + nvec, *alpha = part + (size_t)nb * ld;
         double *beta = alpha + (size_t)M * ld;
         double *th = beta + (size_t)M * ld, *wt = th + (size_t)n_v * M;
-        double *inv_beta = wt + (size_t)n_v * M;
-        double *c_coef = inv_beta + (size_t)M * ld;
-        int *mu_dev = (int *)(c_coef + ld);
+        double *s_fac = wt + (size_t)n_v * M, *c_fac = s_fac + ld, *t_fac = c_fac + ld;
+        int *mu_dev = (int *)(t_fac + ld);
         SweepArgs a{};
         a.precision = DOS_PREC_F64;
         a.n_rows = A.n;
@@ -996,19 +995,19 @@ int dos_lanczos_ritz(dos_ctx *ctx, const dos_csr *Adesc, int M, int n_v, uint64_
         }
         for (int j = 0; j < M; ++j) {
             if (profiling) DOS_CUDA_TRY(cudaEventRecord(ctx->prof_events[2 * j], s));
-            // cur = u_j, prev = u_{j-1}; q_j = s_j u_j with s_j = 1 / beta_{j-1} (s_0 = 1);
-            // c_j = beta_{j-1} s_{j-1}, written by the previous step's beta reduction
-            const double *s_cur = j >= 1 ? inv_beta + (size_t)(j - 1) * ld : nullptr;
-            launch_lanczos_team_spmm(A.n, ld, A.row_ptr, A.col_idx, val, cur, prev, s_cur,
-                                     j ? c_coef : nullptr, part, nb_spmm, s);
+            // cur = u_j, prev = u_{j-1} of q_j = s_j u_j; the factors s_j, c_j, t_j
+            // (per column, written by the previous step's beta kernel) are 1 / absent
+            // at j = 0
+            const double *sj = j ? s_fac : nullptr;
+            launch_lanczos_team_spmm(A.n, ld, A.row_ptr, A.col_idx, val, cur, prev,
+                                     j ? c_fac : nullptr, part, nb_spmm, s);
             if (profiling) DOS_CUDA_TRY(cudaEventRecord(ctx->prof_events[2 * j + 1], s));
-            launch_column_sum(part, nb_spmm, ld, alpha + (size_t)j * ld, nullptr, 0, s_cur,
-                              nullptr, nullptr, s);
-            launch_lanczos_block_axpy(A.n, ld, n_v, alpha + (size_t)j * ld, s_cur, cur, prev, part,
-                                      nb_axpy, s);
-            launch_column_sum(part, nb_axpy, ld, beta + (size_t)j * ld,
-                              inv_beta + (size_t)j * ld, 1, nullptr, c_coef, s_cur, s);
-            std::swap(cur, prev);  // cur now holds u_{j+1} = w, prev u_j
+            launch_lanczos_alpha(part, nb_spmm, ld, sj, alpha + (size_t)j * ld, s);
+            launch_lanczos_block_axpy(A.n, ld, n_v, alpha + (size_t)j * ld, j ? t_fac : nullptr,
+                                      cur, prev, part, nb_axpy, s);
+            launch_lanczos_beta(part, nb_axpy, ld, sj, j ? beta + (size_t)(j - 1) * ld : nullptr,
+                                beta + (size_t)j * ld, s_fac, c_fac, t_fac, s);
+            std::swap(cur, prev);  // cur now holds u_{j+1}, prev u_j
         }
         // steps kept per run (invariant-subspace rule) and the Ritz pairs, on the device
         launch_lanczos_steps(alpha, beta, M, ld, n_v, mu_dev, s);

@@ -273,20 +273,21 @@ void launch_dgl(const double *nu, int M, double c, double d, double sigma, doubl
 // Block product with the fused step's team mapping (kpm_kernels.cu): w = A q -
 // beta_prev q_prev over q_prev, per-block alpha partials [n_blocks][ld].
 int lanczos_team_blocks(int num_sms, int64_t n, int ld);
-// q and qprev_w hold u_j and u_{j-1} of q_j = s_j u_j; s_cur: s_j per column (NULL
-// for 1); c_prev: beta_{j-1} s_{j-1} per column (NULL: no previous term); part gets
-// the partial sums of u_j . w
+// W = A u_j - c_j u_{j-1} over u_{j-1} (c_prev: c_j per column, NULL: no previous
+// term); part gets the partial sums of u_j . W
 void launch_lanczos_team_spmm(int64_t n, int ld, const int32_t *row_ptr, const int32_t *col_idx,
                               const double *val, const double *q, double *qprev_w,
-                              const double *s_cur, const double *c_prev, double *part,
-                              int n_blocks, cudaStream_t s);
+                              const double *c_prev, double *part, int n_blocks,
+                              cudaStream_t s);
 int lanczos_blocks(int num_sms, int64_t n, int ld);
 void launch_lanczos_block_axpy(int64_t n, int ld, int n_vec, const double *alpha,
-                               const double *s_q, const double *q, double *w, double *part,
+                               const double *t_fac, const double *q, double *w, double *part,
                                int n_blocks, cudaStream_t s);
-void launch_column_sum(const double *part, int n_blocks, int ld, double *out, double *inv,
-                       int take_sqrt, const double *scale, double *prod, const double *prod_by,
-                       cudaStream_t s);
+void launch_lanczos_alpha(const double *part, int n_blocks, int ld, const double *s_fac,
+                          double *alpha, cudaStream_t s);
+void launch_lanczos_beta(const double *part, int n_blocks, int ld, const double *s_fac,
+                         const double *beta_prev, double *beta, double *s_next, double *c_next,
+                         double *t_next, cudaStream_t s);
 void launch_unit_scale(int64_t n, int ld, int n_vec, double *q, int num_sms, cudaStream_t s);
 // w <- w / sum(w) on the device; sum_out[0] receives the sum.
 void launch_normalize_weights(double *w, int64_t n, double *sum_out, cudaStream_t s);

@@ -1502,20 +1502,18 @@ static void launch_step_t(const SweepArgs &a, int k, int slot, cudaStream_t s) {
 }
 
 // ---- block Lanczos product (Section 3.2.1) with the fused step's data mapping -----
-// w = A q_j - beta_{j-1} q_{j-1} for n_vec runs at once (FP64), written over
-// q_{j-1}, and per-block partial sums of u_j . w per column (alpha_j = s_j u_j . w).
-// The Lanczos vectors are stored unnormalised, q_j = s_j u_j with one factor per
-// column (s_j = 1 / beta_{j-1}, or 1 where the pointer is null), so no pass
-// rescales them: w = s_j (A u_j) - c_j u_{j-1} with c_j = beta_{j-1} s_{j-1}
-// (null: no previous term), the same FP64 work per element as with stored q.  A team
+// w = A u_j - c_j u_{j-1} for n_vec runs at once (FP64), written over u_{j-1}, and
+// per-block partial sums of u_j . w per column (c_prev: c_j per column, NULL for
+// no previous term).  The Lanczos loop keeps its vectors unnormalised
+// (q_j = s_j u_j), so with the right c_j this is q_j's product divided by s_j:
+// one FMA per element after the gathers, as for normalised vectors.  A team
 // of G threads shares a matrix row, each thread owning CPT chunks of CB bytes of
 // the row of Q; CSR entries are fetched once per team and shared by shuffles.
 template <int G, int CPT, int CB>
 __global__ void __launch_bounds__(kBlock, 3) lanczos_team_spmm_kernel(
     int64_t n, int ld, const int32_t *__restrict__ row_ptr, const int32_t *__restrict__ col_idx,
     const double *__restrict__ val, const double *__restrict__ q, double *__restrict__ qprev_w,
-    const double *__restrict__ s_cur, const double *__restrict__ c_prev,
-    double *__restrict__ part) {
+    const double *__restrict__ c_prev, double *__restrict__ part) {
     constexpr int VPT = CB / 8;
     constexpr int TPW = 32 / G;
     constexpr int U = CPT * CB >= 64 ? 4 : 8;
@@ -1527,20 +1525,16 @@ __global__ void __launch_bounds__(kBlock, 3) lanczos_team_spmm_kernel(
     const int team_base = (lane / G) * G;
     const unsigned team_mask = G == 32 ? 0xffffffffu : (((1u << G) - 1u) << team_base);
     const int n_chunks = ld / VPT;
-    // per-column factors, read in the epilogue from shared memory (ld <= 256)
-    __shared__ __align__(16) double fac_s[256], fac_c[256];
-    for (int c = threadIdx.x; c < ld; c += blockDim.x) {
-        fac_s[c] = s_cur ? s_cur[c] : 1.0;
-        fac_c[c] = c_prev ? c_prev[c] : 0.0;
-    }
-    __syncthreads();
     bool valid[CPT];
-    double acc[CPT][VPT];
+    double bp[CPT][VPT], acc[CPT][VPT];
 #pragma unroll
     for (int cc = 0; cc < CPT; ++cc) {
         valid[cc] = (g + cc * G) < n_chunks;
 #pragma unroll
-        for (int j = 0; j < VPT; ++j) acc[cc][j] = 0.0;
+        for (int j = 0; j < VPT; ++j) {
+            bp[cc][j] = (c_prev && valid[cc]) ? c_prev[(g + cc * G) * VPT + j] : 0.0;
+            acc[cc][j] = 0.0;
+        }
     }
     for (int64_t row = (int64_t)blockIdx.x * n_teams + team; row < n;
          row += (int64_t)gridDim.x * n_teams) {
@@ -1580,14 +1574,13 @@ __global__ void __launch_bounds__(kBlock, 3) lanczos_team_spmm_kernel(
 #pragma unroll
         for (int cc = 0; cc < CPT; ++cc) {
             if (!valid[cc]) continue;
-            const int c0 = (g + cc * G) * VPT;
             double w[VPT];
 #pragma unroll
             for (int j = 0; j < VPT; ++j) {
-                w[j] = fma(fac_s[c0 + j], y[cc][j], -fac_c[c0 + j] * xo[cc][j]);
-                acc[cc][j] = fma(xk[cc][j], w[j], acc[cc][j]);  // u_j . w; s_j applied later
+                w[j] = y[cc][j] - bp[cc][j] * xo[cc][j];
+                acc[cc][j] = fma(xk[cc][j], w[j], acc[cc][j]);
             }
-            store_chunk(qprev_w + roff + c0, w);
+            store_chunk(qprev_w + roff + (g + cc * G) * VPT, w);
         }
     }
     block_reduce_store<double, G, CPT, VPT>(acc, part + (size_t)blockIdx.x * ld, ld, n_chunks, ld,
@@ -1595,7 +1588,7 @@ __global__ void __launch_bounds__(kBlock, 3) lanczos_team_spmm_kernel(
 }
 
 using LanczosFn = void (*)(int64_t, int, const int32_t *, const int32_t *, const double *,
-                           const double *, double *, const double *, const double *, double *);
+                           const double *, double *, const double *, double *);
 static LanczosFn pick_lanczos(int G, int CPT, int CB) {
 #define DOS_LZ(GG, CC, BB) \
     if (G == GG && CPT == CC && CB == BB) return lanczos_team_spmm_kernel<GG, CC, BB>;
@@ -1630,14 +1623,14 @@ int lanczos_team_blocks(int num_sms, int64_t n, int ld) {
 
 void launch_lanczos_team_spmm(int64_t n, int ld, const int32_t *row_ptr, const int32_t *col_idx,
                               const double *val, const double *q, double *qprev_w,
-                              const double *s_cur, const double *c_prev, double *part,
-                              int n_blocks, cudaStream_t s) {
+                              const double *c_prev, double *part, int n_blocks,
+                              cudaStream_t s) {
     int G, CPT, CB;
     lanczos_shape(ld, &G, &CPT, &CB);
     LanczosFn fn = pick_lanczos(G, CPT, CB);
     if (!fn) throw Error{DOS_EINVAL, "no Lanczos product kernel for this vector block"};
     fn<<<n_blocks, kBlock, step_smem(kBlock, ld), s>>>(n, ld, row_ptr, col_idx, val, q, qprev_w,
-                                                       s_cur, c_prev, part);
+                                                       c_prev, part);
     DOS_LAUNCHED();
 }
 

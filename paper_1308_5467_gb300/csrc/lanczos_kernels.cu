@@ -3,13 +3,16 @@
 // Gaussian-blurred DOS from them.  FP64 throughout.
 //
 // Block layout as in the moment sweep: Q[i*ld + l].  The Lanczos vectors are kept
-// unnormalised, q_j = s_j u_j with s_j = 1 / beta_{j-1} per column (s_0 = 1), and
-// every pass applies the factors, so no pass rescales a block.  Step j:
-//   w = A q_j - beta_{j-1} q_{j-1}          (SpMM pass, lanczos_team_spmm_kernel in
-//                                            kpm_kernels.cu; w overwrites u_{j-1})
-//   alpha_j = q_j . w                        (per-vector partials, fixed-order reduce)
-//   w -= alpha_j q_j;  beta_j = ||w||        (vector pass + reduce; w is u_{j+1},
-//                                             1 / beta_j is s_{j+1})
+// unnormalised, q_j = s_j u_j with one factor per column, so that no pass has to
+// rescale a block.  With w_j = A q_j - beta_{j-1} q_{j-1} and W = w_j / s_j, step j:
+//   W = A u_j - c_j u_{j-1}                 (SpMM pass, lanczos_team_spmm_kernel in
+//                                            kpm_kernels.cu; W overwrites u_{j-1})
+//   alpha_j = q_j . w_j = s_j^2 u_j . W      (per-vector partials, fixed-order reduce)
+//   u_{j+1} = t_j (W - alpha_j u_j)          (vector pass, partial ||u_{j+1}||^2)
+//   beta_j = ||w_j - alpha_j q_j|| = s_j ||u_{j+1}|| / t_j
+// with t_j = 1 / beta_{j-1}, s_{j+1} = s_j / (t_j beta_j), c_{j+1} = beta_j s_j / s_{j+1}
+// (s_0 = t_0 = 1).  t_j keeps |u_j| of the order of beta_j / beta_0, and every
+// per-element pass does the work it did with normalised vectors.
 // A run whose beta_j falls to 1e-12 times its running norm estimate has reached
 // an invariant subspace; the host keeps its first j+1 coefficients only.
 #include <cuda_runtime.h>
@@ -23,21 +26,22 @@ namespace {
 
 constexpr int kThreads = 256;
 
-// w -= alpha q (per column), partial ||w||^2 per column
+// w <- t (w - alpha u) per column, partial ||w||^2 per column (t NULL: 1)
 __global__ void lanczos_axpy_kernel(int64_t n, int ld, const double *__restrict__ alpha,
-                                    const double *__restrict__ s_q,
+                                    const double *__restrict__ t_fac,
                                     const double *__restrict__ q, double *__restrict__ w,
                                     double *__restrict__ part, int n_vec) {
     extern __shared__ double sh[];
     const int cols = ld;
     const int rows_per_block = blockDim.x / cols;
     const int rloc = threadIdx.x / cols, l = threadIdx.x % cols;
-    const double a = alpha[l] * (s_q ? s_q[l] : 1.0);  // q_j = s_j u_j
+    const double a = alpha[l];
+    const double t = t_fac ? t_fac[l] : 1.0;
     double acc = 0.0;
     for (int64_t i = (int64_t)blockIdx.x * rows_per_block + rloc; i < n;
          i += (int64_t)gridDim.x * rows_per_block) {
         const size_t o = (size_t)i * ld + l;
-        const double v = w[o] - a * q[o];
+        const double v = (w[o] - a * q[o]) * t;
         w[o] = v;
         if (l < n_vec) acc = fma(v, v, acc);
     }
@@ -50,29 +54,54 @@ __global__ void lanczos_axpy_kernel(int64_t n, int ld, const double *__restrict_
     }
 }
 
-// v = sum over blocks of part[b][l], optionally sqrt; out[l] = v * scale[l] (scale
-// NULL: 1); inv (if given) gets 1 / v (0 for a zero sum); prod (if given) gets
-// v * prod_by[l] (prod_by NULL: 1).  One block per column: each thread sums a
+// Sum over blocks of part[b][l] for column l = blockIdx.x: each thread sums a
 // strided slice in order, then a fixed shuffle tree and a fixed warp order, so
-// the result is reproducible.
-__global__ void column_sum_kernel(const double *__restrict__ part, int n_blocks, int ld,
-                                  double *__restrict__ out, double *__restrict__ inv,
-                                  int take_sqrt, const double *__restrict__ scale,
-                                  double *__restrict__ prod, const double *__restrict__ prod_by) {
+// the result is reproducible.  Thread 0 returns the total.
+__device__ double column_total(const double *__restrict__ part, int n_blocks, int ld, int l) {
     __shared__ double sh[32];
-    const int l = blockIdx.x;
     double s = 0.0;
     for (int b = threadIdx.x; b < n_blocks; b += blockDim.x) s += part[(size_t)b * ld + l];
     for (int off = 16; off > 0; off >>= 1) s += __shfl_down_sync(0xffffffffu, s, off);
     if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = s;
     __syncthreads();
-    if (threadIdx.x == 0) {
-        double t = 0.0;
+    double t = 0.0;
+    if (threadIdx.x == 0)
         for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += sh[w];
-        const double v = take_sqrt ? sqrt(t) : t;
-        out[l] = scale ? v * scale[l] : v;
-        if (inv) inv[l] = v > 0.0 ? 1.0 / v : 0.0;
-        if (prod) prod[l] = prod_by ? v * prod_by[l] : v;
+    return t;
+}
+
+// alpha_j = s_j^2 (u_j . w) per column (s NULL: 1).  One block per column.
+__global__ void lanczos_alpha_kernel(const double *__restrict__ part, int n_blocks, int ld,
+                                     const double *__restrict__ s_fac,
+                                     double *__restrict__ alpha) {
+    const int l = blockIdx.x;
+    const double t = column_total(part, n_blocks, ld, l);
+    if (threadIdx.x == 0) {
+        const double sj = s_fac ? s_fac[l] : 1.0;
+        alpha[l] = t * sj * sj;
+    }
+}
+
+// From v^2 = ||u_{j+1}||^2 (partials) per column, with s = s_j and bp = beta_{j-1}
+// (both NULL at j = 0: 1):  beta_j = s bp v, and the factors of the next step,
+// s_{j+1} = s bp / beta_j, c_{j+1} = beta_j^2 / bp (the SpMM's coefficient of u_j)
+// and t_{j+1} = 1 / beta_j (the axpy's rescale).  A zero beta_j leaves the run's
+// later vectors at zero.  One block per column; s may be s_next (in place).
+__global__ void lanczos_beta_kernel(const double *__restrict__ part, int n_blocks, int ld,
+                                    const double *s_fac, const double *__restrict__ beta_prev,
+                                    double *__restrict__ beta, double *s_next,
+                                    double *__restrict__ c_next, double *__restrict__ t_next) {
+    const int l = blockIdx.x;
+    const double t = column_total(part, n_blocks, ld, l);
+    if (threadIdx.x == 0) {
+        const double sj = s_fac ? s_fac[l] : 1.0;
+        const double bp = beta_prev ? beta_prev[l] : 1.0;
+        const double b = sj * bp * sqrt(t);
+        beta[l] = b;
+        const double ib = b > 0.0 ? 1.0 / b : 0.0;
+        s_next[l] = sj * bp * ib;
+        c_next[l] = bp > 0.0 ? b * b / bp : 0.0;
+        t_next[l] = ib;
     }
 }
 
@@ -513,19 +542,25 @@ int lanczos_blocks(int num_sms, int64_t n, int ld) {
 }
 
 void launch_lanczos_block_axpy(int64_t n, int ld, int n_vec, const double *alpha,
-                               const double *s_q, const double *q, double *w, double *part,
+                               const double *t_fac, const double *q, double *w, double *part,
                                int n_blocks, cudaStream_t s) {
     const int bt = block_threads_for(ld);
-    lanczos_axpy_kernel<<<n_blocks, bt, bt * sizeof(double), s>>>(n, ld, alpha, s_q, q, w, part,
-                                                                   n_vec);
+    lanczos_axpy_kernel<<<n_blocks, bt, bt * sizeof(double), s>>>(n, ld, alpha, t_fac, q, w,
+                                                                   part, n_vec);
     DOS_LAUNCHED();
 }
 
-void launch_column_sum(const double *part, int n_blocks, int ld, double *out, double *inv,
-                       int take_sqrt, const double *scale, double *prod, const double *prod_by,
-                       cudaStream_t s) {
-    column_sum_kernel<<<ld, 256, 0, s>>>(part, n_blocks, ld, out, inv, take_sqrt, scale, prod,
-                                         prod_by);
+void launch_lanczos_alpha(const double *part, int n_blocks, int ld, const double *s_fac,
+                          double *alpha, cudaStream_t s) {
+    lanczos_alpha_kernel<<<ld, 256, 0, s>>>(part, n_blocks, ld, s_fac, alpha);
+    DOS_LAUNCHED();
+}
+
+void launch_lanczos_beta(const double *part, int n_blocks, int ld, const double *s_fac,
+                         const double *beta_prev, double *beta, double *s_next, double *c_next,
+                         double *t_next, cudaStream_t s) {
+    lanczos_beta_kernel<<<ld, 256, 0, s>>>(part, n_blocks, ld, s_fac, beta_prev, beta, s_next,
+                                           c_next, t_next);
     DOS_LAUNCHED();
 }
 
