@@ -521,9 +521,17 @@ Shape tune_shape(dos_ctx *ctx, const dos_csr *A, int B, const int64_t *seg_rows,
     // any bounds do (values may grow; the kernels' speed does not depend on them).
     std::vector<double> lb(B, -1.0), ub(B, 1.0);
     double *mu_scratch = (double *)ctx->rec_out.get((size_t)B * 97 * sizeof(double));
-    cudaEvent_t e0, e1;
-    DOS_CUDA_TRY(cudaEventCreate(&e0));
-    DOS_CUDA_TRY(cudaEventCreate(&e1));
+    // timing events, released on every exit path (a failing candidate throws)
+    struct EventPair {
+        cudaEvent_t a = nullptr, b = nullptr;
+        ~EventPair() {
+            if (a) cudaEventDestroy(a);
+            if (b) cudaEventDestroy(b);
+        }
+    } ev;
+    DOS_CUDA_TRY(cudaEventCreate(&ev.a));
+    DOS_CUDA_TRY(cudaEventCreate(&ev.b));
+    cudaEvent_t e0 = ev.a, e1 = ev.b;
     Shape best;
     double best_t = INFINITY;
     bool first = true;
@@ -599,8 +607,6 @@ Shape tune_shape(dos_ctx *ctx, const dos_csr *A, int B, const int64_t *seg_rows,
             }
         }
     }
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
     DOS_REQUIRE(best.team > 0, "no launch shape fits this vector block");
     int64_t nnz = A->nnz;
     ctx->tuned[std::make_tuple((int64_t)A->n, nnz, B, pw, precision)] = best;
