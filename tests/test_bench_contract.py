@@ -46,3 +46,15 @@ def test_roofline_names_the_variant_that_ran():
     assert bench.step_kernel_name({"staged": 2}, "f64") == "step_staged_kernel<double>"
     assert bench.step_kernel_name({"staged": 3, "depth": 2}, "f32") == "step_tmag_kernel<float>"
     assert bench.step_kernel_name(None, "f64") == "step_kernel<double>"
+
+
+def test_cpu_baseline_reports_all_cores_and_one():
+    """The oracle's rate on the host cores and on one thread, over bounded samples."""
+    sys.path.insert(0, ROOT)
+    import bench
+    from synthetic import laplacian_2d
+    cb = bench.cpu_baseline(laplacian_2d(40), -0.1, 8.1, 100, 20, 1, target_s=0.5)
+    assert cb["kind"] == "oracle" and cb["unit"] == "moments/s" and cb["value"] > 0
+    assert cb["cores"] >= 1 and "start vectors" in cb["sample"]
+    st = cb["single_thread"]
+    assert st["cores"] == 1 and st["value"] > 0 and "1 thread" in st["sample"]
