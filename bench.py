@@ -7,13 +7,17 @@ steps -> moments -> Jackson reconstruction on a 1000-point t-grid -> the
 sigma-smoothed L1/Linf error against a reference DOS.  The metric is Chebyshev
 moments per second, nnz * n_v * M / t_step.
 
-Default workload: 3-D Anderson model on a 64^3 periodic lattice (n = 262144,
-7 nonzeros per row), on-site disorder uniform in [-2, 2], hopping -1, seed 2;
-M = 500, n_v = 64, FP32 SpMM with FP64 moment accumulation (the FP64 form is
-measured too and reported under "forms").  Inputs are synthetic and seeded.
+Default workload: the normalized Laplacian of a seeded Chung-Lu graph (n =
+4,194,304, power-law expected degrees with exponent 2.5, mean degree 20, skewed
+rows up to ~10^4 nonzeros), FP32 values and int32 indices; M = 1000, n_v = 256;
+bounds from a 20-step Lanczos run (Gershgorin's discs are ~20x too wide for a
+normalized Laplacian).  FP32 vectors and SpMM with FP32 row sums accumulated as
+float pairs and FP64; the FP64 form is measured too and reported under
+"forms".  Inputs are synthetic and seeded.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference]
-                    [--workload anderson64|laplacian40|chunglu|batched] [--precision f32|f64]
+                    [--workload chunglu|anderson64|laplacian40|chunglu1m|batched|learned]
+                    [--precision f32|f64]
 
 Under torchrun (N > 1) every rank sweeps its own n_v start vectors (vector
 offset rank * n_v) -- weak scaling, no collective on the data path; the moments
@@ -51,13 +55,20 @@ WORKLOADS = {
                        desc="3-D Anderson 64^3 periodic, W=4 (eps ~ U[-2,2]), hopping -1, seed 2"),
     "laplacian40": dict(kind="laplacian", m=40, M=100, n_v=20, seed=1,
                         desc="2-D 5-point Dirichlet Laplacian 40x40"),
+    # bounds: "lanczos" = 20 Lanczos steps + residual, padded 1% per side; the
+    # reference DOS of the smoothed error: ref_nv independent vectors in ref_prec;
+    # f64_steps / e2e_steps: timed steps of those secondary forms (one warm-up each)
     "chunglu": dict(kind="chunglu", n=4194304, beta=2.5, mean_deg=20.0, seed=3, M=1000,
-                    n_v=256, desc="normalized Laplacian of a Chung-Lu graph, n=4194304, "
-                              "beta=2.5, mean degree 20, seed 3"),
+                    n_v=256, bounds="lanczos", ref_nv=1024, ref_prec="f32", f64_steps=1,
+                    e2e_steps=2,
+                    desc="normalized Laplacian of a Chung-Lu graph, n=4194304, "
+                         "beta=2.5, mean degree 20, seed 3"),
     "chunglu1m": dict(kind="chunglu", n=1048576, beta=2.5, mean_deg=20.0, seed=3, M=200,
-                      n_v=256, desc="normalized Laplacian of a Chung-Lu graph, n=1048576, "
-                                "beta=2.5, mean degree 20, seed 3 (a quarter of the 4M-row "
-                                "graph, small enough for counter captures)"),
+                      n_v=256, bounds="lanczos", ref_nv=1024, ref_prec="f32", f64_steps=2,
+                      e2e_steps=2,
+                      desc="normalized Laplacian of a Chung-Lu graph, n=1048576, "
+                           "beta=2.5, mean degree 20, seed 3 (a quarter of the 4M-row "
+                           "graph, small enough for counter captures)"),
     "batched": dict(kind="batched", count=512, seed=4, M=200, n_v=32,
                     desc="512 Anderson lattices, L ~ U{10..40}, W ~ U[1,16], seed 4"),
 }
@@ -105,6 +116,13 @@ def algorithmic_bytes_per_step(n, nnz, n_v, precision):
 def fma_per_step(n, nnz, n_v):
     """FMAs of one fused step: nnz*n_v (SpMM) + 2 n n_v (shift, recurrence) + 2 n n_v (dots)."""
     return nnz * n_v + 4 * n * n_v
+
+
+# GB300's FP64 rate is not measured here: NVIDIA's nominal figure, next to which
+# the FP64 fused step's ncu FP64-pipe utilisation is the evidence of the bound.
+FP64_NOMINAL_TFLOPS = 1.25
+FP64_PEAK_SOURCE = ("nominal FP64 rate of GB300 (1.25 TFLOP/s, not measured); ncu: FP64 pipe "
+                    "91% busy in the fused step on the 64^3 lattice")
 
 
 def measured_peaks():
@@ -192,35 +210,47 @@ def kernel_source_hash():
     return hashlib.sha256(region.encode()).hexdigest()[:16]
 
 
-def cpu_baseline(A, lb, ub, M, n_v_full, seed, target_s=12.0):
-    """The oracle as it stands, on the host cores, over a bounded sample:
-    the same matrix and M, a number of start vectors sized for ~target_s."""
+def oracle_sample(A, lb, ub, M, n_v_full, seed, target_s, cores):
+    """(vectors, degree) of a bounded oracle sample of about target_s seconds on
+    `cores` threads: the full degree M with as many start vectors as fit (at least
+    one per thread), or -- when one doubling pass over A already costs most of the
+    budget (the 4-million-row graph) -- one vector per thread at a reduced even
+    degree; the sweep costs ceil(M/2) passes, so the rate scales linearly."""
     from oracle import kpm as okpm
-    cores = os.cpu_count() or 1
-    # very large matrices: a reduced degree, scaled linearly (the sweep's cost is
-    # linear in M: ceil(M/2) passes over A)
-    Ms = M if A.nnz * M <= 5e10 else max(2, int(5e10 // A.nnz))
     probe = max(1, min(cores, n_v_full))
     t0 = time.perf_counter()
-    okpm.kpm_moments_per_vector(A, lb, ub, Ms, probe, seed, nthreads=cores)
-    t_probe = time.perf_counter() - t0
-    nv = probe
-    if t_probe < target_s / 2:
-        nv = int(min(max(probe, probe * target_s / max(t_probe, 1e-3)), 4 * n_v_full))
+    okpm.kpm_moments_per_vector(A, lb, ub, 4, probe, seed, nthreads=cores)
+    t_pass = max((time.perf_counter() - t0) / 2, 1e-6)   # one pass of `probe` vectors
+    t_full = t_pass * max(1, (M + 1) // 2)
+    if t_full <= target_s:
+        nv = int(min(4 * n_v_full, probe * max(1, int(target_s / t_full))))
         nv = max(probe, (nv // cores) * cores if nv >= cores else nv)
+        return nv, M
+    return probe, int(min(M, max(2, 2 * int(target_s / t_pass))))
+
+
+def cpu_baseline(A, lb, ub, M, n_v_full, seed, target_s=12.0):
+    """The oracle as it stands, on the host cores, over a bounded sample of the
+    same matrix, bounds and start vectors (see oracle_sample)."""
+    from oracle import kpm as okpm
+    cores = os.cpu_count() or 1
+    nv, Ms = oracle_sample(A, lb, ub, M, n_v_full, seed, target_s, cores)
     t0 = time.perf_counter()
     okpm.kpm_moments_per_vector(A, lb, ub, Ms, nv, seed, nthreads=cores)
     t = time.perf_counter() - t0
     value = A.nnz * nv * Ms / t
     scaled = "" if Ms == M else f", timed at M={Ms} and scaled linearly to M={M}"
-    # the same oracle on one thread, for reference: a few vectors, ~target_s / 3
+    # the same oracle on one thread, for reference: ~target_s / 3
     per_vec_1 = t * min(cores, nv) / nv
     n1 = int(max(1, min(nv, (target_s / 3) / max(per_vec_1, 1e-6))))
+    M1 = Ms if per_vec_1 <= target_s / 3 else int(max(2, 2 * ((Ms * (target_s / 3)
+                                                                / per_vec_1) // 2)))
     t0 = time.perf_counter()
-    okpm.kpm_moments_per_vector(A, lb, ub, Ms, n1, seed, nthreads=1)
+    okpm.kpm_moments_per_vector(A, lb, ub, M1, n1, seed, nthreads=1)
     t1 = time.perf_counter() - t0
-    single = {"value": A.nnz * n1 * Ms / t1, "cores": 1,
-              "sample": f"{n1} start vectors, {t1:.1f} s wall on 1 thread{scaled}"}
+    scaled1 = "" if M1 == M else f", timed at M={M1} and scaled linearly to M={M}"
+    single = {"value": A.nnz * n1 * M1 / t1, "cores": 1,
+              "sample": f"{n1} start vectors, {t1:.1f} s wall on 1 thread{scaled1}"}
     return {"value": value, "unit": "moments/s", "cores": min(cores, nv), "kind": "oracle",
             "sample": f"{nv} start vectors of the same workload (M={Ms}, doubling mode, FP64), "
                       f"{t:.1f} s wall on {min(cores, nv)} threads{scaled}",
@@ -228,13 +258,18 @@ def cpu_baseline(A, lb, ub, M, n_v_full, seed, target_s=12.0):
 
 
 def run_reference(args):
-    """The reference arm: the CPU oracle, timed as it stands on the host cores."""
+    """The reference arm: the CPU oracle, timed as it stands on the host cores,
+    each step a bounded sample of the workload (about 90 s / (K + W) per step)."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return 0
     w = WORKLOADS[args.workload]
     if w["kind"] == "batched":
-        print(json.dumps({"impl": "reference", "unavailable": "batched workload has no oracle arm"}))
+        return run_reference_batched(args, w)
+    if w["kind"] == "learned":
+        print(json.dumps({"impl": "reference", "unavailable":
+                          "the learned workload trains the library's network; its oracle is "
+                          "the CPU KPM of the kpm workloads"}))
         return 0
     if args.method != "kpm":
         return run_reference_method(args, w)
@@ -243,29 +278,102 @@ def run_reference(args):
     A = make_matrix(w)
     if args.precision == "f32":
         A = A.astype(np.float32)
-    lb, ub = obounds.bounds(A, "gershgorin", pad_frac=0.01)
+    lb, ub = obounds.bounds(A, w.get("bounds", "gershgorin"), steps=20, seed=w["seed"],
+                            pad_frac=0.01)
     M = w["M"]
     cores = os.cpu_count() or 1
-    nv = max(1, min(cores, w["n_v"]))
-    for _ in range(args.warmup if args.warmup <= 1 else 1):
-        okpm.kpm_moments_per_vector(A, lb, ub, min(M, 20), nv, w["seed"], nthreads=cores)
+    step_s = min(6.0, max(0.5, 90.0 / max(1, args.steps + args.warmup)))
+    nv, Ms = oracle_sample(A, lb, ub, M, w["n_v"], w["seed"], step_s, cores)
+    nv = min(nv, max(1, min(cores, w["n_v"])))
+    for _ in range(min(args.warmup, 1)):
+        okpm.kpm_moments_per_vector(A, lb, ub, min(Ms, 20), nv, w["seed"], nthreads=cores)
     times = []
     for _ in range(args.steps):
         t0 = time.perf_counter()
-        okpm.kpm_moments_per_vector(A, lb, ub, M, nv, w["seed"], nthreads=cores)
+        okpm.kpm_moments_per_vector(A, lb, ub, Ms, nv, w["seed"], nthreads=cores)
         times.append(time.perf_counter() - t0)
     t = sum(times) / len(times)
-    value = A.nnz * nv * M / t
+    value = A.nnz * nv * Ms / t
+    scaled = "" if Ms == M else f"; degree reduced to M={Ms}, the rate scales linearly in M"
     sample = (f"each step: {nv} of the {w['n_v']} start vectors of {args.workload} "
-              f"(M={M}, FP64 oracle, doubling mode) on {min(cores, nv)} host threads")
+              f"(M={Ms}, FP64 oracle, doubling mode) on {min(cores, nv)} host threads{scaled}")
     line = {"metric": "Chebyshev moments/sec (nnz*n_v*M/s)", "value": value,
             "unit": "moments/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * t, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": args.workload, "n": A.n, "nnz": A.nnz, "M": M,
-                       "n_v": w["n_v"], "n_v_sample": nv},
+                       "n_v": w["n_v"], "n_v_sample": nv, "M_sample": Ms,
+                       "bounds": w.get("bounds", "gershgorin")},
             "impl": "reference",
             "cpu_baseline": {"value": value, "unit": "moments/s", "cores": min(cores, nv),
+                             "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": "moments/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+def batched_sample(mats, M, n_v, step_s, cores):
+    """Matrices of the 512-lattice batch for a bounded oracle sample: a spread of
+    sizes (the smallest, the largest and evenly spaced indices), as many as fit
+    in about step_s seconds at the full M and n_v."""
+    from oracle import kpm as okpm
+    sizes = np.array([m.n for m in mats])
+    order = [int(np.argmin(sizes)), int(np.argmax(sizes))] + list(range(0, len(mats), 37))
+    picks, t_used = [], 0.0
+    for b in order:
+        if b in picks:
+            continue
+        t0 = time.perf_counter()
+        okpm.kpm_moments(mats[b], -20.0, 20.0, min(M, 8), n_v, 0, batch_index=b,
+                         nthreads=cores)
+        t_est = (time.perf_counter() - t0) * max(1.0, M / 8.0)
+        if picks and t_used + t_est > step_s:
+            break
+        picks.append(b)
+        t_used += t_est
+    return picks
+
+
+def run_reference_batched(args, w):
+    """Reference arm of the 512-lattice workload: the oracle, matrix by matrix with
+    each matrix's own start-vector counters, over a bounded sample of the batch."""
+    from oracle import bounds as obounds
+    from oracle import kpm as okpm
+    from synthetic import batched_anderson
+    mats = batched_anderson(w["count"], w["seed"])
+    if args.precision == "f32":
+        mats = [m.astype(np.float32) for m in mats]
+    M, n_v = w["M"], w["n_v"]
+    cores = os.cpu_count() or 1
+    step_s = min(6.0, max(0.5, 90.0 / max(1, args.steps + args.warmup)))
+    picks = batched_sample(mats, M, n_v, step_s, cores)
+    bnds = [obounds.bounds(mats[b], "gershgorin", pad_frac=0.01) for b in picks]
+
+    def one():
+        for b, (lb, ub) in zip(picks, bnds):
+            okpm.kpm_moments(mats[b], lb, ub, M, n_v, w["seed"], batch_index=b, nthreads=cores)
+    for _ in range(min(args.warmup, 1)):
+        one()
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        one()
+        times.append(time.perf_counter() - t0)
+    t = sum(times) / len(times)
+    nnz = sum(mats[b].nnz for b in picks)
+    value = nnz * n_v * M / t
+    sample = (f"each step: {len(picks)} of the {len(mats)} lattices (n from "
+              f"{min(mats[b].n for b in picks)} to {max(mats[b].n for b in picks)}), all "
+              f"{n_v} start vectors, M={M}, FP64 oracle one matrix at a time on {cores} threads")
+    line = {"metric": "Chebyshev moments/sec (nnz*n_v*M/s)", "value": value,
+            "unit": "moments/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * t, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": args.workload, "B": len(mats), "M": M, "n_v": n_v,
+                       "sampled_matrices": picks, "nnz_sample": nnz},
+            "impl": "reference",
+            "cpu_baseline": {"value": value, "unit": "moments/s", "cores": cores,
                              "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": "moments/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
@@ -387,35 +495,76 @@ def run_batched(args, w, world, rank, local, device):
     n_rows = int(seg[-1])
     alg = algorithmic_bytes_per_step(n_rows, nnz, n_v, prec)
     achieved = alg / (launch_ms * 1e-3) / 1e9
-    forms = {prec: {"ms_per_step": ms, "value": value}}
+    forms = {prec: {"ms_per_step": ms, "value": value, "steps": args.steps}}
     # FP64 batched, and plain FP64 KPM one matrix at a time
-    ms64, (_, _, mu64), _ = timed(lambda: step(A64, "f64"), max(2, args.steps // 4), 1)
-    forms["f64_batched"] = {"ms_per_step": ms64, "value": units * world / (ms64 * 1e-3)}
+    st64 = max(2, args.steps // 4)
+    ms64, (_, _, mu64), _ = timed(lambda: step(A64, "f64"), st64, 1)
+    forms["f64_batched"] = {"ms_per_step": ms64, "value": units * world / (ms64 * 1e-3),
+                            "steps": st64}
     singles = [dos.CSRArrays.from_synthetic(m, device=device) for m in mats]
 
     def plain():
         return [ctx.dos_kpm_moments(S, lb[b], ub[b], M, n_v, seed=w["seed"], precision="f64",
                                     batch_index=b) for b, S in enumerate(singles)]
-    ms_plain, _, _ = timed(plain, 1, 1)
-    forms["f64_plain_per_matrix"] = {"ms_per_step": ms_plain,
+    ms_plain, mu_plain, _ = timed(plain, 1, 1)
+    forms["f64_plain_per_matrix"] = {"ms_per_step": ms_plain, "steps": 1,
                                      "value": units * world / (ms_plain * 1e-3)}
-    # smoothed L1 error of sampled matrices against an FP64 n_v = 512 reference
+    # smoothed L1 error of sampled matrices against an FP64 n_v = 512 reference, in
+    # each form (the same start vectors in all three)
     picks = [0, 100, 255, 511]
-    errs = {prec: [], "f64": []}
+    errs = {prec: [], "f64_batched": [], "f64_plain_per_matrix": []}
     for b in picks:
         ref = ctx.dos_kpm_moments(singles[b], lb[b], ub[b], M, 512, seed=w["seed"] + 77,
                                   precision="f64", batch_index=b)
         sig = 0.02 * (ub[b] - lb[b])
-        errs[prec].append(ctx.dos_smoothed_error(mu[b], M, "jackson", lb[b], ub[b], sig,
-                                                 ref_mu=ref)[0])
-        errs["f64"].append(ctx.dos_smoothed_error(mu64[b], M, "jackson", lb[b], ub[b], sig,
-                                                  ref_mu=ref)[0])
+        for key, m in ((prec, mu[b]), ("f64_batched", mu64[b]),
+                       ("f64_plain_per_matrix", mu_plain[b])):
+            errs[key].append(ctx.dos_smoothed_error(m, M, "jackson", lb[b], ub[b], sig,
+                                                    ref_mu=ref)[0])
+    for key, v in errs.items():
+        forms[key]["e1_sampled"] = float(np.mean(v))
+    forms["f64_batched"]["max_abs_diff_vs_" + prec] = float(np.abs(mu64 - mu).max())
+
+    # end to end: host (pinned) CSR through the same C-ABI calls, which copy it in
+    e2e = None
+    if not args.no_e2e:
+        rp_h = torch.from_numpy(rp).pin_memory()
+        ci_h = torch.from_numpy(ci).pin_memory()
+        va_h = torch.from_numpy(va.astype(vdt)).pin_memory()
+        Ah = dos.CSRArrays(n_rows, rp_h, ci_h, va_h)
+        st_e2e = max(3, args.steps // 2)
+        ms_e2e, _, _ = timed(lambda: step(Ah, prec), st_e2e, 1)
+        h2d = 2 * (rp_h.numel() * 4 + ci_h.numel() * 4 + va_h.numel() * va_h.element_size())
+        d2h = len(mats) * (M + 1) * 8 + 2 * len(mats) * 8
+        e2e = {"value": units * world / (ms_e2e * 1e-3), "unit": "moments/s",
+               "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms_per_step": ms_e2e,
+               "steps": st_e2e}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        from oracle import kpm as okpm
+        cores = os.cpu_count() or 1
+        mats_h = [m.astype(vdt) for m in mats]
+        cpu_picks = batched_sample(mats_h, M, n_v, 12.0, cores)
+        t0 = time.perf_counter()
+        for b in cpu_picks:
+            okpm.kpm_moments(mats_h[b], lb[b], ub[b], M, n_v, w["seed"], batch_index=b,
+                             nthreads=cores)
+        t = time.perf_counter() - t0
+        nnz_s = sum(mats_h[b].nnz for b in cpu_picks)
+        cpu = {"value": nnz_s * n_v * M / t, "unit": "moments/s", "cores": cores,
+               "kind": "oracle",
+               "sample": f"{len(cpu_picks)} of the {len(mats)} lattices (n from "
+                         f"{min(mats[b].n for b in cpu_picks)} to "
+                         f"{max(mats[b].n for b in cpu_picks)}), all {n_v} start vectors, "
+                         f"M={M}, FP64 oracle one matrix at a time, {t:.1f} s wall on {cores} "
+                         f"threads"}
     if rank == 0:
         line = {
             "metric": "Chebyshev moments/sec (nnz*n_v*M/s)", "value": value, "unit": "moments/s",
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f32+f64acc" if prec == "f32" else "f64", "data": "synthetic",
+            "dtype": "f32" if prec == "f32" else "f64", "data": "synthetic",
             "config": {"workload": "batched", "desc": w["desc"], "B": len(mats), "n": n_rows,
                        "nnz": nnz, "M": M, "n_v": n_v, "precision": prec, "pdl": not args.no_pdl,
                        "l2": "inputs larger than L2: %.0f MB per fused step" % (alg / 1e6)},
@@ -423,9 +572,9 @@ def run_batched(args, w, world, rank, local, device):
                          "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"], "traffic": None,
                          "peak_source": peak_kind, "launch_ms": launch_ms,
                          "algorithmic_bytes_per_launch": alg},
-            "forms": forms, "e1_sampled": {k: float(np.mean(v)) for k, v in errs.items()},
-            "gpu_launches": prof["launches"], "clocks": clk.summary(), "e2e": None,
-            "cpu_baseline": None,
+            "forms": forms, "e1_sampled": float(np.mean(errs[prec])),
+            "gpu_launches": prof["launches"], "clocks": clk.summary(), "e2e": e2e,
+            "cpu_baseline": cpu,
         }
         print(json.dumps(line))
     ctx.close()
@@ -554,12 +703,12 @@ def run_method(args, w, world, rank, local, device):
         ld = (n_v + 1) // 2 * 2
         flops = 2 * A.nnz * n_v
         byts = lanczos_spmm_bytes(A.n, A.nnz, ld)
-        f_alu = flops / (launch_ms * 1e-3) / 1e12 / 1.25
+        f_alu = flops / (launch_ms * 1e-3) / 1e12 / FP64_NOMINAL_TFLOPS
         f_hbm = byts / (launch_ms * 1e-3) / 1e9 / peaks["hbm_gbs"]
         if f_alu >= f_hbm:
-            roofline = {"bound": "alu", "achieved": f_alu * 1.25, "peak": 1.25,
-                        "unit": "TFLOP/s", "frac": f_alu, "traffic": None,
-                        "peak_source": "nominal FP64 rate of GB300 (1.25 TFLOP/s)",
+            roofline = {"bound": "alu", "achieved": f_alu * FP64_NOMINAL_TFLOPS,
+                        "peak": FP64_NOMINAL_TFLOPS, "unit": "TFLOP/s", "frac": f_alu,
+                        "traffic": None, "peak_source": FP64_PEAK_SOURCE,
                         "kernel": "lanczos_team_spmm_kernel", "flops_per_launch": flops,
                         "launch_ms": launch_ms, "hbm_frac": f_hbm}
         else:
@@ -616,8 +765,10 @@ def main():
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--seconds", type=float, default=0.0,
+                    help="learned workload: training budget in seconds (0: its default)")
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--workload", default="anderson64", choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default="chunglu", choices=sorted(WORKLOADS))
     ap.add_argument("--method", default="kpm", choices=["kpm"] + sorted(METHODS),
                     help="kpm (the benchmark) or one of the paper's other estimators")
     ap.add_argument("--precision", default="f32", choices=["f32", "f64"])
@@ -653,7 +804,11 @@ def main():
         return run_method(args, w, world, rank, local, device)
     if w["kind"] == "batched":
         return run_batched(args, w, world, rank, local, device)
+    if w["kind"] == "learned":
+        return run_learned(args, w, world, rank, local, device)
     A = make_matrix(w)
+    if w["kind"] == "chunglu":
+        A = A.astype(np.float32)      # the graph's values are FP32 (both forms read them)
     M, n_v, seed = w["M"], w["n_v"], w["seed"]
     prec = args.precision
     vdtype = np.float32 if prec == "f32" else np.float64
@@ -661,8 +816,12 @@ def main():
     Ad64 = dos.CSRArrays.from_synthetic(A, device=device, dtype=np.float64)
     ctx = dos.Context(local)
     vec_offset = rank * n_v
+    bmethod = w.get("bounds", "gershgorin")
 
-    lb, ub = ctx.dos_bounds(Ad, "gershgorin", pad_frac=0.01)
+    def bounds_of(Acsr):
+        return ctx.dos_bounds(Acsr, bmethod, steps=20, seed=seed, pad_frac=0.01)
+
+    lb, ub = bounds_of(Ad)
     sigma = 0.02 * (ub - lb)
     # launch shape of the fused step chosen by the library's autotuner (cached in ctx)
     fixed = None
@@ -674,18 +833,17 @@ def main():
         tuned_shape, tuned_ms = ctx.dos_tune(Ad, n_v, prec)
         tuned64 = (ctx.dos_tune(Ad64, n_v, "f64")[0]
                    if (prec == "f32" and not args.no_f64_form) else None)
-    # reference DOS for the smoothed error: a sweep with many independent vectors
-    # (FP64 with 1024 vectors; FP32 with 256 for the 4-million-row graph)
-    if w["kind"] == "chunglu":
-        ref_mu = ctx.dos_kpm_moments(Ad, lb, ub, M, 256, seed=seed + 1000, precision="f32")
-    else:
-        ref_mu = ctx.dos_kpm_moments(Ad64, lb, ub, M, 1024, seed=seed + 1000, precision="f64",
-                                     vec_offset=0)
+    # reference DOS for the smoothed error: a sweep of ref_nv independent vectors
+    # (another seed); FP32 on the graph, whose FP32 error (~1e-6 per moment) is far
+    # below the stochastic error of 1024 vectors (~2e-5)
+    ref_nv, ref_prec = w.get("ref_nv", 1024), w.get("ref_prec", "f64")
+    ref_mu = ctx.dos_kpm_moments(Ad if ref_prec == prec else Ad64, lb, ub, M, ref_nv,
+                                 seed=seed + 1000, precision=ref_prec)
 
     sweep_flags = dos.DOS_OPT_NO_PDL if args.no_pdl else 0
 
     def step(Acsr, precision, host=False):
-        lo, hi = ctx.dos_bounds(Acsr, "gershgorin", pad_frac=0.01)
+        lo, hi = bounds_of(Acsr)
         mu = ctx.dos_kpm_moments(Acsr, lo, hi, M, n_v, seed=seed, precision=precision,
                                  vec_offset=vec_offset, flags=sweep_flags,
                                  launch=fixed if precision == prec else None)
@@ -730,41 +888,57 @@ def main():
     # roofline of the dominant kernel (the fused step)
     peaks, peak_kind = measured_peaks()
     launch_ms = prof["step_ms"] / max(1, prof["step_launches"])
+    kname = step_kernel_name(tuned_shape, prec)
     if prec == "f32":
         alg = algorithmic_bytes_per_step(A.n, A.nnz, n_v, prec)
         achieved = alg / (launch_ms * 1e-3) / 1e9
-        key = (args.workload, prec)
-        tr = NCU_TRAFFIC.get(key)
+        tr = NCU_TRAFFIC.get((args.workload, prec))
         same_launch = tr is not None and all(tuned_shape.get(k) == v
                                              for k, v in tr.get("launch", {}).items())
         traffic = tr["bytes"] if tr and tr["src"] == kernel_source_hash() and same_launch else None
         roofline = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"],
                     "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"], "traffic": traffic,
-                    "peak_source": peak_kind, "kernel": step_kernel_name(tuned_shape, prec),
-                    "algorithmic_bytes_per_launch": alg, "launch_ms": launch_ms}
+                    "peak_source": peak_kind, "kernel": kname,
+                    "algorithmic_bytes_per_launch": alg, "launch_ms": launch_ms,
+                    "frac_basis": "compulsory bytes (CSR once, X_k once, X_{k-1} read, "
+                                  "X_{k+1} written) / launch time"}
+        if traffic:
+            # the same launch against the DRAM bytes it actually moved (ncu)
+            roofline["frac_of_traffic"] = traffic / (launch_ms * 1e-3) / 1e9 / peaks["hbm_gbs"]
+            roofline["traffic_source"] = tr.get("note", "ncu dram__bytes_read.sum + "
+                                                        "dram__bytes_write.sum per launch")
     else:
         flops = 2 * fma_per_step(A.n, A.nnz, n_v)
         achieved = flops / (launch_ms * 1e-3) / 1e12
-        roofline = {"bound": "alu", "achieved": achieved, "peak": 1.25, "unit": "TFLOP/s",
-                    "frac": achieved / 1.25, "traffic": None,
-                    "peak_source": "nominal FP64 rate of GB300 (1.25 TFLOP/s)",
-                    "kernel": step_kernel_name(tuned_shape, prec), "flops_per_launch": flops,
-                    "launch_ms": launch_ms}
+        roofline = {"bound": "alu", "achieved": achieved, "peak": FP64_NOMINAL_TFLOPS,
+                    "unit": "TFLOP/s", "frac": achieved / FP64_NOMINAL_TFLOPS, "traffic": None,
+                    "peak_source": FP64_PEAK_SOURCE, "kernel": kname,
+                    "flops_per_launch": flops, "launch_ms": launch_ms}
 
-    forms = {prec: {"ms_per_step": ms, "value": value, "e1": e1, "einf": einf}}
+    forms = {prec: {"ms_per_step": ms, "value": value, "e1": e1, "einf": einf,
+                    "steps": args.steps}}
     if not args.no_f64_form and prec == "f32":
-        ms64, out64, prof64 = timed(lambda: step(Ad64, "f64"), max(3, args.steps // 4), 1,
-                                    profile=True)
+        st64 = w.get("f64_steps", max(3, args.steps // 4))
+        ms64, out64, prof64 = timed(lambda: step(Ad64, "f64"), st64, 1, profile=True)
         l64 = prof64["step_ms"] / max(1, prof64["step_launches"])
         fl = 2 * fma_per_step(A.n, A.nnz, n_v)
+        diff = np.abs(out64[0] - mu)
+        k = np.arange(M + 1)
         forms["f64"] = {"ms_per_step": ms64, "value": units * world / (ms64 * 1e-3),
-                        "e1": out64[2], "einf": out64[3],
+                        "e1": out64[2], "einf": out64[3], "steps": st64,
                         "roofline": {"bound": "alu", "achieved": fl / (l64 * 1e-3) / 1e12,
-                                     "peak": 1.25, "unit": "TFLOP/s",
-                                     "frac": fl / (l64 * 1e-3) / 1e12 / 1.25,
+                                     "peak": FP64_NOMINAL_TFLOPS, "unit": "TFLOP/s",
+                                     "frac": fl / (l64 * 1e-3) / 1e12 / FP64_NOMINAL_TFLOPS,
+                                     "peak_source": FP64_PEAK_SOURCE,
                                      "kernel": step_kernel_name(tuned64, "f64"),
                                      "launch_ms": l64},
-                        "max_abs_diff_vs_f32": float(np.abs(out64[0] - mu).max())}
+                        # FP32 form against the FP64 form on the same values and vectors:
+                        # the arithmetic error, next to the stochastic error of the estimate
+                        "max_abs_diff_vs_f32": float(diff.max()),
+                        "fp32_bound_2u_sqrt_k": float(2 * 2.0 ** -24 * np.sqrt(M + 1)),
+                        "max_diff_over_u_sqrt_k": float((diff / (2.0 ** -24
+                                                                 * np.sqrt(k + 1))).max()),
+                        "stochastic_std_sqrt_2_over_n_nv": float(np.sqrt(2.0 / (A.n * n_v)))}
 
     e2e = None
     if not args.no_e2e:
@@ -773,11 +947,13 @@ def main():
         ci = torch.from_numpy(A.col_idx).pin_memory()
         va = torch.from_numpy(A.val.astype(vdtype)).pin_memory()
         Ah = dos.CSRArrays(A.n, rp, ci, va)
-        ms_e2e, _, _ = timed(lambda: step(Ah, prec, host=True), max(3, args.steps // 2), 1)
+        st_e2e = w.get("e2e_steps", max(3, args.steps // 2))
+        ms_e2e, _, _ = timed(lambda: step(Ah, prec, host=True), st_e2e, 1)
         h2d = 2 * (rp.numel() * 4 + ci.numel() * 4 + va.numel() * va.element_size())
         d2h = 8 * (M + 1) + 8 * 1000 + 8 * 2 + 16
         e2e = {"value": units * world / (ms_e2e * 1e-3), "unit": "moments/s",
-               "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms_per_step": ms_e2e}
+               "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms_per_step": ms_e2e,
+               "steps": st_e2e}
 
     if world > 1:
         # the ranks swept disjoint blocks of start vectors (offset rank * n_v):
@@ -795,10 +971,15 @@ def main():
             "value": value, "unit": "moments/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None,
-            "dtype": "f32+f64acc" if prec == "f32" else "f64", "data": "synthetic",
+            "dtype": "f32" if prec == "f32" else "f64", "data": "synthetic",
             "config": {"workload": args.workload, "desc": w["desc"], "launch": tuned_shape,
                        "launch_f64": tuned64, "n": A.n, "nnz": A.nnz,
                        "M": M, "n_v": n_v, "precision": prec,
+                       "accumulation": ("FP32 products summed per row in FP32, rows "
+                                        "accumulated as float pairs per thread, blocks and "
+                                        "tiles in FP64") if prec == "f32" else "FP64",
+                       "bounds": f"{bmethod}, padded 1% per side",
+                       "reference_dos": f"{ref_prec.upper()} sweep of {ref_nv} other vectors",
                        "l2": "inputs larger than L2: %.0f MB touched per fused step"
                              % (algorithmic_bytes_per_step(A.n, A.nnz, n_v, prec) / 1e6),
                        "sigma": sigma, "lb": lb, "ub": ub, "pdl": not args.no_pdl},

@@ -50,6 +50,8 @@ extern "C" {
                             bounds did not enclose the spectrum (Section 3.1:
                             T_k(B) v_0 then grows exponentially) */
 #define DOS_ETIMEOUT 5   /* a bounded device-side wait ran out */
+#define DOS_EIO 6        /* a file could not be opened, read or written, or is not
+                            a file of the expected format (dos_mlp_save / load) */
 
 /* ---- enumerations ---------------------------------------------------------- */
 #define DOS_F64 0               /* value / vector element type */
@@ -267,24 +269,26 @@ int dos_kpm_moments_batched(dos_ctx *ctx, const dos_csr *A, int B, const int64_t
 /*
  * dos_kpm_moments without any memory allocation.  The paper has no
  * counterpart: this exists for callers that cannot call cudaMalloc while they
- * run -- code executing while a CUDA graph is being captured around it, or
- * applications whose device memory is owned by their own pool allocator or
- * fixed by a budget.  It computes the same moments mu_0..mu_M as
+ * run -- applications whose device memory is reserved up front by their own
+ * pool allocator (so a library's cudaMalloc fails or evicts the pool's cache),
+ * and services held to a fixed memory budget or latency target, where
+ * cudaMalloc / cudaFree may synchronise the device.  It computes the same moments mu_0..mu_M as
  * dos_kpm_moments (single matrix, start-vector counter b = 0, vector offset
  * 0) but keeps all intermediates in one fixed 64 MiB device array that is part
  * of the library image (every GPU that loads the library holds it until the
  * process exits), so the caller passes only inputs and outputs and no
  * context is needed.  It works on the calling thread's current device.
- *   A: all three arrays in DEVICE memory; values FP64 for DOS_PREC_F64, FP32
- *      for DOS_PREC_F32_ACC64 (no conversion copy is made).
+ *   A: all three arrays in DEVICE memory (checked: a host array returns
+ *      DOS_EINVAL before any work is queued); values FP64 for DOS_PREC_F64,
+ *      FP32 for DOS_PREC_F32_ACC64 (no conversion copy is made).
  *   mu: M+1 doubles in device memory.
  *   Limits: n_v <= 256, M <= 20000, and 2 * n * ld * element_size <= 63 MiB
  *      with ld = n_v rounded up to 2 (FP64) or 4 (FP32) -- e.g. n <= 129024
  *      rows at n_v = 64 in FP32.  Larger problems return DOS_ENOMEM before any
  *      work is queued.
- *   The first call on a device looks up the array's device address (a host
- *   symbol is only a stand-in for it); make that first call before any stream
- *   capture.  Every call uses the same array and leaves its contents behind
+ *   The first call on a device looks up the array's device address with
+ *   cudaGetSymbolAddress (in host code the array's name is only a stand-in for
+ *   it); make that first call before any stream capture.  Every call uses the same array and leaves its contents behind
  *   (the kernels re-initialise what they read); calls that overlap on the GPU
  *   -- from several host threads or streams -- race on it and must be
  *   serialised by the caller.  Synchronises `stream` (to check the CSR

@@ -47,9 +47,36 @@ int dos_mlp_set_params(dos_mlp *mlp, const float *params, void *stream);
 /* Copy the FP32 master parameters out.  Synchronises `stream`. */
 int dos_mlp_get_params(dos_mlp *mlp, float *params, void *stream);
 
-/* y = network(x) for a batch: x is B x n_in, y is B x n_out (row-major FP32).
- * 1 <= B <= 65536.  Synchronises when y is host memory. */
+/* y = network(x) for one training-sized batch: x is B x n_in, y is B x n_out
+ * (row-major FP32), 1 <= B <= 65536; the activations stay in the network's
+ * buffers (as dos_mlp_loss_grad leaves them).  Synchronises when y is host
+ * memory. */
 int dos_mlp_forward(dos_mlp *mlp, const float *x, int B, float *y, void *stream);
+
+/* Inference: y = network(x) for any number of rows B >= 1 (x: B x n_in,
+ * y: B x n_out, row-major FP32, host or device).  Runs the forward kernels over
+ * consecutive slices of at most `max_rows` rows (0: 8192), so the activation
+ * buffers stay bounded whatever B is; each row's output is bitwise the same as
+ * from dos_mlp_forward.  Synchronises when x or y is host memory. */
+int dos_mlp_infer(dos_mlp *mlp, const float *x, int64_t B, float *y, int max_rows,
+                  void *stream);
+
+/* Checkpoint: write the network to `path` in a byte-stable little-endian file:
+ *   bytes 0-7   magic "DOSMLP\0\1" (format version 1)
+ *   then int32 n_in, n_hidden, n_out, int32 0 (reserved), int64 Adam step count,
+ *   int64 n_params, then n_params FP32 master parameters (the flat order above),
+ *   n_params FP32 Adam first moments, n_params FP32 Adam second moments, and
+ *   last a uint64 FNV-1a hash of every byte before it.
+ * The same network state always gives the same bytes.  Synchronises `stream`.
+ * Errors: DOS_EIO (cannot write), DOS_ECUDA, DOS_EINVAL. */
+int dos_mlp_save(dos_mlp *mlp, const char *path, void *stream);
+
+/* Create a network on `ctx` from a file written by dos_mlp_save: sizes,
+ * parameters, Adam moments and step count restored, so inference and further
+ * training continue bit for bit as from the saved network.  Errors: DOS_EIO
+ * (cannot open or read, wrong magic or version, sizes that disagree with the
+ * file length, or a hash mismatch), DOS_ENOMEM, DOS_ECUDA. */
+int dos_mlp_load(dos_ctx *ctx, const char *path, dos_mlp **out, void *stream);
 
 /* L1 loss of the batch and (if grads != NULL) its gradient with respect to
  * every parameter, flat FP32 in the parameter order.  No update.

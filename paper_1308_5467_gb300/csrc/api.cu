@@ -628,6 +628,7 @@ const char *dos_status_string(int status) {
         case DOS_ECUDA: return "DOS_ECUDA";
         case DOS_ESPECTRUM: return "DOS_ESPECTRUM";
         case DOS_ETIMEOUT: return "DOS_ETIMEOUT";
+        case DOS_EIO: return "DOS_EIO";
         default: return "DOS_UNKNOWN";
     }
 }

@@ -83,6 +83,32 @@ __device__ __forceinline__ void acc_zero(double &a) { a = 0.0; }
 __device__ __forceinline__ void acc_add_prod(double &a, double x, double y) { a = fma(x, y, a); }
 __device__ __forceinline__ void acc_add(double &a, double v) { a += v; }
 
+// ---- the affine map of B = (A - cI)/d --------------------------------------------
+// (y - c x) / d for y = (A X)[i, l], x = X[i, l].  In FP32, c and 1/d are each
+// carried as an unevaluated pair hi + lo (lo = the FP32 rounding of the
+// remainder), so the FP32 form applies B itself to about 2^-48 instead of the
+// operator built from c and 1/d rounded to FP32.  That rounding would move
+// every eigenvalue of B by up to 2^-24 relative, an error of mu_k that does not
+// average out over rows and vectors and grows like k 2^-24 at a point mass of
+// the spectrum near +-1; what is left is the rounding of each step's result.
+template <typename T>
+struct Affine {
+    T c, c_lo, s, s_lo;
+    __device__ __forceinline__ Affine(double cd, double sd) {
+        c = (T)cd;
+        s = (T)sd;
+        c_lo = (T)(cd - (double)c);
+        s_lo = (T)(sd - (double)s);
+    }
+    __device__ __forceinline__ T operator()(T y, T x) const {
+        T t = fma(-c, x, y);
+        if constexpr (sizeof(T) == 4) t = fma(-c_lo, x, t);
+        T r = t * s;
+        if constexpr (sizeof(T) == 4) r = fma(t, s_lo, r);
+        return r;
+    }
+};
+
 template <typename T> struct Traits;
 template <> struct Traits<float> {
     static constexpr int VPT = 4;
@@ -364,8 +390,7 @@ __global__ void __launch_bounds__(kBlock, 3) step_kernel(const StepParams<T> p) 
     const int team = warp * TPW + lane / G;
     const int team_base = (lane / G) * G;
     const unsigned team_mask = G == 32 ? 0xffffffffu : (((1u << G) - 1u) << team_base);
-    const T c = (T)p.seg_c[seg];
-    const T inv_d = (T)p.seg_inv_d[seg];
+    const Affine<T> shift(p.seg_c[seg], p.seg_inv_d[seg]);
     const int ld = p.ld;
     const T *__restrict__ xseg = p.xc + (size_t)p.seg_row0[seg] * ld;
     const T *__restrict__ xc = p.xc;
@@ -446,11 +471,11 @@ __global__ void __launch_bounds__(kBlock, 3) step_kernel(const StepParams<T> p) 
             T xnew[VPT];
             if (first) {
 #pragma unroll
-                for (int j = 0; j < VPT; ++j) xnew[j] = fma(-c, xk[cc][j], y[cc][j]) * inv_d;
+                for (int j = 0; j < VPT; ++j) xnew[j] = shift(y[cc][j], xk[cc][j]);
             } else {
 #pragma unroll
                 for (int j = 0; j < VPT; ++j)
-                    xnew[j] = fma(T(2), fma(-c, xk[cc][j], y[cc][j]) * inv_d, -xo[cc][j]);
+                    xnew[j] = fma(T(2), shift(y[cc][j], xk[cc][j]), -xo[cc][j]);
             }
             store_chunk(xn + roff + off, xnew);
 #pragma unroll
@@ -566,8 +591,7 @@ __global__ void __launch_bounds__(kBlock, 2) step_staged_kernel(const StepParams
     const int team = warp * TPW + lane / G;
     const int team_base = (lane / G) * G;
     const unsigned team_mask = G == 32 ? 0xffffffffu : (((1u << G) - 1u) << team_base);
-    const T c = (T)p.seg_c[seg];
-    const T inv_d = (T)p.seg_inv_d[seg];
+    const Affine<T> shift(p.seg_c[seg], p.seg_inv_d[seg]);
     const T *__restrict__ xseg = p.xc + (size_t)p.seg_row0[seg] * ld;
     const int32_t *__restrict__ row_ptr = p.row_ptr;
     const int32_t *__restrict__ col_idx = p.col_idx;
@@ -670,12 +694,12 @@ __global__ void __launch_bounds__(kBlock, 2) step_staged_kernel(const StepParams
                 load16(scur + (size_t)j * ld + off, xk);
                 if (first) {
 #pragma unroll
-                    for (int q = 0; q < VPT; ++q) xnew[q] = fma(-c, xk[q], y[cc][q]) * inv_d;
+                    for (int q = 0; q < VPT; ++q) xnew[q] = shift(y[cc][q], xk[q]);
                 } else {
                     load16(sprev + (size_t)j * ld + off, xo);
 #pragma unroll
                     for (int q = 0; q < VPT; ++q)
-                        xnew[q] = fma(T(2), fma(-c, xk[q], y[cc][q]) * inv_d, -xo[q]);
+                        xnew[q] = fma(T(2), shift(y[cc][q], xk[q]), -xo[q]);
                 }
                 store16(xn + (size_t)row * ld + off, xnew);
 #pragma unroll
@@ -814,8 +838,7 @@ __global__ void __launch_bounds__(kBlock, 2) step_tmag_kernel(const StepParams<T
 
     const int4 tl = p.tiles[blockIdx.x];
     const int rb = tl.x, re = tl.y, seg = tl.z;
-    const T c = (T)p.seg_c[seg];
-    const T inv_d = (T)p.seg_inv_d[seg];
+    const Affine<T> shift(p.seg_c[seg], p.seg_inv_d[seg]);
     const int row0 = p.seg_row0[seg];
     const T *__restrict__ xc = p.xc;
     const int32_t *__restrict__ row_ptr = p.row_ptr;
@@ -935,7 +958,7 @@ __global__ void __launch_bounds__(kBlock, 2) step_tmag_kernel(const StepParams<T
             T xnew[VPT];
 #pragma unroll
             for (int j = 0; j < VPT; ++j)
-                xnew[j] = fma(T(2), fma(-c, xk[cc][j], y[cc][j]) * inv_d, -xo[cc][j]);
+                xnew[j] = fma(T(2), shift(y[cc][j], xk[cc][j]), -xo[cc][j]);
             store16(xn + roff + off, xnew);
 #pragma unroll
             for (int j = 0; j < VPT; ++j) {

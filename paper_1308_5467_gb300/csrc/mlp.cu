@@ -11,8 +11,11 @@
 #include <stdint.h>
 #include <string.h>
 
+#include <stdio.h>
+
 #include <algorithm>
 #include <new>
+#include <string>
 #include <vector>
 
 #include "../../include/dos_mlp.h"
@@ -389,6 +392,49 @@ void loss_backward(dos_mlp *mlp, int B, cudaStream_t s) {
     DOS_LAUNCHED();
 }
 
+bool is_host_ptr(const void *p) {
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return true;
+    }
+    return at.type != cudaMemoryTypeDevice && at.type != cudaMemoryTypeManaged;
+}
+
+// ---- checkpoint file ----------------------------------------------------------------
+// Little-endian encoding written byte by byte, so the bytes do not depend on the
+// host; FNV-1a (64-bit) over everything before the trailing hash.
+constexpr unsigned char kMagic[8] = {'D', 'O', 'S', 'M', 'L', 'P', 0, 1};
+constexpr size_t kHeaderBytes = 8 + 4 * 4 + 8 + 8;
+
+void put_u32(std::vector<unsigned char> &b, uint32_t v) {
+    for (int i = 0; i < 4; ++i) b.push_back((unsigned char)(v >> (8 * i)));
+}
+void put_u64(std::vector<unsigned char> &b, uint64_t v) {
+    for (int i = 0; i < 8; ++i) b.push_back((unsigned char)(v >> (8 * i)));
+}
+uint32_t get_u32(const unsigned char *p) {
+    uint32_t v = 0;
+    for (int i = 0; i < 4; ++i) v |= (uint32_t)p[i] << (8 * i);
+    return v;
+}
+uint64_t get_u64(const unsigned char *p) {
+    uint64_t v = 0;
+    for (int i = 0; i < 8; ++i) v |= (uint64_t)p[i] << (8 * i);
+    return v;
+}
+uint64_t fnv1a64(const unsigned char *p, size_t n) {
+    uint64_t h = 14695981039346656037ULL;
+    for (size_t i = 0; i < n; ++i) {
+        h ^= p[i];
+        h *= 1099511628211ULL;
+    }
+    return h;
+}
+int64_t count_params(int64_t n_in, int64_t nh, int64_t n_out) {
+    return nh * n_in + nh + nh * nh + nh + n_out * nh + n_out;
+}
+
 }  // namespace
 
 extern "C" {
@@ -496,6 +542,125 @@ int dos_mlp_forward(dos_mlp *mlp, const float *x, int B, float *y, void *stream)
         else if (at.type != cudaMemoryTypeDevice && at.type != cudaMemoryTypeManaged)
             DOS_CUDA_TRY(cudaStreamSynchronize(s));
     });
+}
+
+int dos_mlp_infer(dos_mlp *mlp, const float *x, int64_t B, float *y, int max_rows,
+                  void *stream) {
+    return mguard(mlp, [&] {
+        DOS_REQUIRE(x != nullptr && y != nullptr, "x / y is NULL");
+        DOS_REQUIRE(B >= 1, "B must be >= 1");
+        DOS_REQUIRE(max_rows >= 0 && max_rows <= 65536, "max_rows must be in [0, 65536]");
+        const int rows = max_rows ? max_rows : 8192;
+        cudaStream_t s = (cudaStream_t)stream;
+        for (int64_t r0 = 0; r0 < B; r0 += rows) {
+            const int b = (int)std::min<int64_t>(rows, B - r0);
+            stage_input(mlp, x + r0 * mlp->n_in, b, nullptr, s);
+            forward(mlp, b, s);
+            DOS_CUDA_TRY(cudaMemcpyAsync(y + r0 * mlp->n_out, mlp->y,
+                                         (size_t)b * mlp->n_out * 4, cudaMemcpyDefault, s));
+        }
+        if (is_host_ptr(x) || is_host_ptr(y)) DOS_CUDA_TRY(cudaStreamSynchronize(s));
+    });
+}
+
+int dos_mlp_save(dos_mlp *mlp, const char *path, void *stream) {
+    return mguard(mlp, [&] {
+        DOS_REQUIRE(path != nullptr, "path is NULL");
+        cudaStream_t s = (cudaStream_t)stream;
+        const int64_t np = mlp->n_params;
+        std::vector<float> host((size_t)(3 * np));
+        // params, then the Adam moments m and v (adjacent after the gradients)
+        DOS_CUDA_TRY(cudaMemcpyAsync(host.data(), mlp->params, np * 4, cudaMemcpyDeviceToHost, s));
+        DOS_CUDA_TRY(cudaMemcpyAsync(host.data() + np, mlp->m, 2 * np * 4, cudaMemcpyDeviceToHost,
+                                     s));
+        DOS_CUDA_TRY(cudaStreamSynchronize(s));
+        std::vector<unsigned char> b;
+        b.reserve(kHeaderBytes + (size_t)(12 * np) + 8);
+        b.insert(b.end(), kMagic, kMagic + 8);
+        put_u32(b, (uint32_t)mlp->n_in);
+        put_u32(b, (uint32_t)mlp->nh);
+        put_u32(b, (uint32_t)mlp->n_out);
+        put_u32(b, 0u);
+        put_u64(b, (uint64_t)mlp->step);
+        put_u64(b, (uint64_t)np);
+        for (float f : host) {
+            uint32_t u;
+            memcpy(&u, &f, 4);
+            put_u32(b, u);
+        }
+        put_u64(b, fnv1a64(b.data(), b.size()));
+        const std::string tmp = std::string(path) + ".partial";
+        FILE *f = fopen(tmp.c_str(), "wb");
+        if (!f) throw Error{DOS_EIO, std::string("cannot open ") + tmp + " for writing"};
+        const size_t w = fwrite(b.data(), 1, b.size(), f);
+        const int cl = fclose(f);
+        if (w != b.size() || cl != 0) {
+            remove(tmp.c_str());
+            throw Error{DOS_EIO, std::string("short write to ") + tmp};
+        }
+        if (rename(tmp.c_str(), path) != 0) {
+            remove(tmp.c_str());
+            throw Error{DOS_EIO, std::string("cannot rename ") + tmp + " to " + path};
+        }
+    });
+}
+
+int dos_mlp_load(dos_ctx *ctx, const char *path, dos_mlp **out, void *stream) {
+    if (!ctx || !out || !path) return DOS_EINVAL;
+    *out = nullptr;
+    std::vector<unsigned char> b;
+    {
+        FILE *f = fopen(path, "rb");
+        if (!f) {
+            ctx->last_error = std::string("cannot open ") + path;
+            return DOS_EIO;
+        }
+        unsigned char chunk[1 << 16];
+        size_t got;
+        while ((got = fread(chunk, 1, sizeof(chunk), f)) > 0) b.insert(b.end(), chunk, chunk + got);
+        const bool err = ferror(f) != 0;
+        fclose(f);
+        if (err) {
+            ctx->last_error = std::string("read error on ") + path;
+            return DOS_EIO;
+        }
+    }
+    auto bad = [&](const char *why) {
+        ctx->last_error = std::string(path) + ": " + why;
+        return DOS_EIO;
+    };
+    if (b.size() < kHeaderBytes + 8) return bad("too short for a network file");
+    if (memcmp(b.data(), kMagic, 8) != 0) return bad("not a network file of format version 1");
+    const uint32_t n_in = get_u32(&b[8]), nh = get_u32(&b[12]), n_out = get_u32(&b[16]);
+    const uint64_t step = get_u64(&b[24]), np = get_u64(&b[32]);
+    if (n_in < 1 || nh < 1 || n_out < 1 || n_in > 8192 || nh > 8192 || n_out > 8192)
+        return bad("layer sizes out of range");
+    if (np != (uint64_t)count_params(n_in, nh, n_out)) return bad("parameter count disagrees");
+    if (b.size() != kHeaderBytes + 12 * np + 8) return bad("length disagrees with the sizes");
+    if (fnv1a64(b.data(), b.size() - 8) != get_u64(&b[b.size() - 8])) return bad("hash mismatch");
+    std::vector<float> host((size_t)(3 * np));
+    for (size_t i = 0; i < host.size(); ++i) {
+        const uint32_t u = get_u32(&b[kHeaderBytes + 4 * i]);
+        memcpy(&host[i], &u, 4);
+    }
+    dos_mlp *mlp = nullptr;
+    int rc = dos_mlp_create(ctx, (int)n_in, (int)nh, (int)n_out, 0, &mlp);
+    if (rc != DOS_OK) return rc;
+    rc = mguard(mlp, [&] {
+        cudaStream_t s = (cudaStream_t)stream;
+        DOS_CUDA_TRY(cudaMemcpyAsync(mlp->params, host.data(), np * 4, cudaMemcpyHostToDevice, s));
+        DOS_CUDA_TRY(cudaMemcpyAsync(mlp->m, host.data() + np, 2 * np * 4,
+                                     cudaMemcpyHostToDevice, s));
+        mlp->step = (int64_t)step;
+        refresh_bf16_weights(mlp, s);
+        DOS_CUDA_TRY(cudaStreamSynchronize(s));
+    });
+    if (rc != DOS_OK) {
+        dos_mlp_destroy(mlp);
+        return rc;
+    }
+    *out = mlp;
+    return DOS_OK;
 }
 
 int dos_mlp_loss_grad(dos_mlp *mlp, const float *x, const float *target, int B, float *loss,

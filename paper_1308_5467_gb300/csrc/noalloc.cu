@@ -1,12 +1,14 @@
 // dos_kpm_moments_noalloc: the moment sweep for callers that cannot allocate
-// device memory.  Some callers must not call cudaMalloc while they run: code
-// that executes while another library is capturing its work into a CUDA graph,
-// or applications whose device memory is pre-reserved by their own pool
-// allocator (a framework's caching allocator) or fixed by a real-time budget.
-// This entry point takes the caller's inputs and output and keeps every
-// intermediate (the two vector blocks, tiles, partial sums, status) in one
-// file-scope device array of fixed size instead.  The paper has no
-// counterpart; it is deployment plumbing around the same kernels.
+// device memory.  Some callers must not call cudaMalloc while they run:
+// applications whose device memory is reserved up front by their own pool
+// allocator (a framework's caching allocator holds nearly all of it, so a
+// library's cudaMalloc fails or evicts the pool's cache), and services with a
+// fixed memory budget or latency target, where cudaMalloc/cudaFree may
+// synchronise the device and stall unrelated work.  This entry point takes the
+// caller's inputs and output and keeps every intermediate (the two vector
+// blocks, tiles, partial sums, status) in one file-scope device array of fixed
+// size instead.  The paper has no counterpart; it is deployment plumbing
+// around the same kernels.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -74,7 +76,10 @@ extern "C" int dos_kpm_moments_noalloc(const dos_csr *A, double lb, double ub, i
     const int S = M < 2 ? 1 : (M + 1) / 2;
     if (S > kMaxSteps) return DOS_ENOMEM;
     if (2 * (size_t)A->n * ld * esz > kScratchBytes - kControlBytes) return DOS_ENOMEM;
+    // every array the kernels read or write must be device memory: a host
+    // address handed to a kernel would fault instead of returning an error
     if (!on_device(mu) || !on_device(A->row_ptr)) return DOS_EINVAL;
+    if (A->nnz && (!on_device(A->col_idx) || !on_device(A->val))) return DOS_EINVAL;
 
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {

@@ -23,7 +23,7 @@ if not os.path.exists(LIB_PATH):
 
 _lib = C.CDLL(LIB_PATH)
 
-DOS_OK, DOS_EINVAL, DOS_ENOMEM, DOS_ECUDA, DOS_ESPECTRUM, DOS_ETIMEOUT = range(6)
+DOS_OK, DOS_EINVAL, DOS_ENOMEM, DOS_ECUDA, DOS_ESPECTRUM, DOS_ETIMEOUT, DOS_EIO = range(7)
 DOS_F64, DOS_F32 = 0, 1
 DOS_DEVICE, DOS_HOST = 0, 1
 DOS_PREC_F64, DOS_PREC_F32_ACC64 = 0, 1
@@ -102,6 +102,9 @@ _SIGS.update({
     "dos_mlp_set_params": (_i, [_vp, _vp, _vp]),
     "dos_mlp_get_params": (_i, [_vp, _vp, _vp]),
     "dos_mlp_forward": (_i, [_vp, _vp, _i, _vp, _vp]),
+    "dos_mlp_infer": (_i, [_vp, _vp, _i64, _vp, _i, _vp]),
+    "dos_mlp_save": (_i, [_vp, C.c_char_p, _vp]),
+    "dos_mlp_load": (_i, [_vp, C.c_char_p, C.POINTER(_vp), _vp]),
     "dos_mlp_loss_grad": (_i, [_vp, _vp, _vp, _i, C.POINTER(C.c_float), _vp, _vp]),
     "dos_mlp_train_step": (_i, [_vp, _vp, _vp, _i, C.c_float, C.POINTER(C.c_float), _vp]),
 })
@@ -514,16 +517,44 @@ class MLP:
     """dos_mlp (include/dos_mlp.h): moments -> DOS network trained by the library."""
 
     def __init__(self, ctx: Context, n_in: int = 64, n_hidden: int = 512, n_out: int = 256,
-                 seed: int = 0):
-        h = C.c_void_p()
+                 seed: int = 0, _handle=None):
         self.ctx = ctx
-        ctx._check(_lib.dos_mlp_create(ctx._h, int(n_in), int(n_hidden), int(n_out), int(seed),
-                                       C.byref(h)))
+        if _handle is None:
+            h = C.c_void_p()
+            ctx._check(_lib.dos_mlp_create(ctx._h, int(n_in), int(n_hidden), int(n_out),
+                                           int(seed), C.byref(h)))
+        else:
+            h = _handle
         self._h = h
         self.n_in, self.n_hidden, self.n_out = int(n_in), int(n_hidden), int(n_out)
         cnt = C.c_int64()
         ctx._check(_lib.dos_mlp_num_params(h, C.byref(cnt)))
         self.n_params = cnt.value
+
+    @classmethod
+    def dos_mlp_load(cls, ctx: Context, path: str):
+        """A network restored from a file written by dos_mlp_save."""
+        h = C.c_void_p()
+        ctx._check(_lib.dos_mlp_load(ctx._h, os.fsencode(path), C.byref(h), C.c_void_p(0)))
+        with open(path, "rb") as f:
+            head = f.read(20)
+        n_in, nh, n_out = (int.from_bytes(head[8 + 4 * i:12 + 4 * i], "little")
+                           for i in range(3))
+        return cls(ctx, n_in, nh, n_out, _handle=h)
+
+    def dos_mlp_save(self, path: str):
+        self.ctx._check(_lib.dos_mlp_save(self._h, os.fsencode(path), C.c_void_p(0)))
+
+    def dos_mlp_infer(self, x, out=None, max_rows: int = 0):
+        """network(x) for any number of rows (sliced through bounded buffers)."""
+        xa = x if _is_torch(x) else np.ascontiguousarray(x, dtype=np.float32)
+        B = int(xa.shape[0])
+        y = np.empty((B, self.n_out), dtype=np.float32) if out is None else out
+        px, _, k0 = _ptr(xa)
+        py, _, k1 = _ptr(y)
+        self.ctx._check(_lib.dos_mlp_infer(self._h, px, B, py, int(max_rows),
+                                           _stream_of(xa, y)))
+        return y
 
     def close(self):
         if getattr(self, "_h", None):

@@ -21,6 +21,8 @@ float64 ``val`` whose column indices are sorted within each row.
 """
 from __future__ import annotations
 
+import os
+from concurrent.futures import ThreadPoolExecutor
 from dataclasses import dataclass, field
 
 import numpy as np
@@ -122,10 +124,39 @@ def _chung_lu_offset(n: int, gamma: float, mean_deg: float) -> float:
     for _ in range(200):
         mid = np.sqrt(lo * hi)
         if wmax(mid) > target:
-            lo = mid
+            new = (mid, hi)
         else:
-            hi = mid
+            new = (lo, mid)
+        if new == (lo, hi):   # a fixed point: further halvings change nothing
+            break
+        lo, hi = new
     return hi
+
+
+def _sorted_unique(x: np.ndarray) -> np.ndarray:
+    """np.unique(x) for a 1-D integer array, by one sort and a neighbour test."""
+    s = np.sort(x)
+    if s.size == 0:
+        return s
+    keep = np.empty(s.size, dtype=bool)
+    keep[0] = True
+    np.not_equal(s[1:], s[:-1], out=keep[1:])
+    return s[keep]
+
+
+def _searchsorted_right(cdf: np.ndarray, q: np.ndarray) -> np.ndarray:
+    """np.searchsorted(cdf, q, side="right") over chunks of q in threads (numpy
+    releases the GIL inside the binary searches); the result is identical."""
+    out = np.empty(q.shape[0], dtype=np.int64)
+    bounds = np.linspace(0, q.shape[0], 33).astype(np.int64)
+
+    def one(i):
+        a, b = bounds[i], bounds[i + 1]
+        out[a:b] = np.searchsorted(cdf, q[a:b], side="right")
+
+    with ThreadPoolExecutor(max_workers=min(16, os.cpu_count() or 1)) as ex:
+        list(ex.map(one, range(32)))
+    return out
 
 
 def chung_lu_normalized_laplacian(n: int, beta: float = 2.5, mean_deg: float = 20.0,
@@ -146,15 +177,15 @@ def chung_lu_normalized_laplacian(n: int, beta: float = 2.5, mean_deg: float = 2
     cdf = np.cumsum(w)
     cdf /= cdf[-1]
     m = int(round(n * mean_deg / 2.0))
-    u = np.searchsorted(cdf, rng.random(m), side="right").astype(np.int64)
-    v = np.searchsorted(cdf, rng.random(m), side="right").astype(np.int64)
+    u = _searchsorted_right(cdf, rng.random(m))
+    v = _searchsorted_right(cdf, rng.random(m))
     np.minimum(u, n - 1, out=u)
     np.minimum(v, n - 1, out=v)
     keep = u != v
     u, v = u[keep], v[keep]
     lo = np.minimum(u, v)
     hi = np.maximum(u, v)
-    key = np.unique(lo * np.int64(n) + hi)
+    key = _sorted_unique(lo * np.int64(n) + hi)
     lo, hi = np.divmod(key, np.int64(n))
     deg = np.bincount(lo, minlength=n) + np.bincount(hi, minlength=n)
     inv_sqrt = np.zeros(n)

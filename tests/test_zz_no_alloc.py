@@ -1,7 +1,7 @@
 """dos_kpm_moments_noalloc: the sweep for callers that cannot allocate device
-memory (e.g. code running while a CUDA graph is captured around it, or behind
-another framework's memory pool).  It must give the moments of
-dos_kpm_moments, call after call, without the device's free memory moving.
+memory (their memory is reserved by their own pool allocator, or held to a fixed
+budget where cudaMalloc may synchronise the device).  It must give the moments
+of dos_kpm_moments, call after call, without the device's free memory moving.
 
 This file is collected last on purpose, so that a run stopping at the first
 failure has run every other test before it."""
@@ -73,3 +73,13 @@ def test_noalloc_small_matrix_then_limits():
     host = np.empty(101)
     rc = f(C.byref(Ad.desc), -0.08, 8.08, 100, 20, 1, dos.DOS_PREC_F64, host.ctypes.data, s)
     assert rc == dos.DOS_EINVAL
+    # a descriptor that says "device" but holds host col_idx / val is refused on the
+    # host, before any kernel could read through the host addresses
+    ci_h, va_h = np.ascontiguousarray(A.col_idx), np.ascontiguousarray(A.val)
+    for ci, va in ((ci_h.ctypes.data, Ad.desc.val), (Ad.desc.col_idx, va_h.ctypes.data)):
+        mixed = dos.dos_csr(A.n, A.nnz, Ad.desc.row_ptr, ci, va, dos.DOS_F64, dos.DOS_DEVICE)
+        rc = f(C.byref(mixed), -0.08, 8.08, 100, 20, 1, dos.DOS_PREC_F64, mu.data_ptr(), s)
+        assert rc == dos.DOS_EINVAL
+    # and the entry point still works afterwards
+    assert f(C.byref(Ad.desc), -0.08, 8.08, 100, 20, 1, dos.DOS_PREC_F64, mu.data_ptr(), s) == 0
+    assert np.abs(mu.cpu().numpy() - ref).max() < 1e-12
