@@ -10,8 +10,10 @@ moments per second, nnz * n_v * M / t_step.
 Default workload: the normalized Laplacian of a seeded Chung-Lu graph (n =
 4,194,304, power-law expected degrees with exponent 2.5, mean degree 20, skewed
 rows up to ~10^4 nonzeros), FP32 values and int32 indices; M = 1000, n_v = 256;
-bounds from a 20-step Lanczos run (Gershgorin's discs are ~20x too wide for a
-normalized Laplacian).  FP32 vectors and SpMM with FP32 row sums accumulated as
+bounds [0, 2] padded by 1% per side, the interval that holds every normalized
+Laplacian's spectrum and that this graph reaches at both ends (isolated
+vertices and an isolated edge); Gershgorin's discs are ~20x wider and a
+Lanczos run cannot see the isolated edge's eigenvalue 2.  FP32 vectors and SpMM with FP32 row sums accumulated as
 float pairs and FP64; the FP64 form is measured too and reported under
 "forms".  Inputs are synthetic and seeded.
 
@@ -55,22 +57,30 @@ WORKLOADS = {
                        desc="3-D Anderson 64^3 periodic, W=4 (eps ~ U[-2,2]), hopping -1, seed 2"),
     "laplacian40": dict(kind="laplacian", m=40, M=100, n_v=20, seed=1,
                         desc="2-D 5-point Dirichlet Laplacian 40x40"),
-    # bounds: "lanczos" = 20 Lanczos steps + residual, padded 1% per side; the
+    # bounds: "normalized_laplacian" = [0, 2] padded 1% per side; the
     # reference DOS of the smoothed error: ref_nv independent vectors in ref_prec;
     # f64_steps / e2e_steps: timed steps of those secondary forms (one warm-up each)
     "chunglu": dict(kind="chunglu", n=4194304, beta=2.5, mean_deg=20.0, seed=3, M=1000,
-                    n_v=256, bounds="lanczos", ref_nv=1024, ref_prec="f32", f64_steps=1,
-                    e2e_steps=2,
+                    n_v=256, bounds="normalized_laplacian", ref_nv=1024, ref_prec="f32",
+                    f64_steps=1, e2e_steps=2,
                     desc="normalized Laplacian of a Chung-Lu graph, n=4194304, "
                          "beta=2.5, mean degree 20, seed 3"),
     "chunglu1m": dict(kind="chunglu", n=1048576, beta=2.5, mean_deg=20.0, seed=3, M=200,
-                      n_v=256, bounds="lanczos", ref_nv=1024, ref_prec="f32", f64_steps=2,
-                      e2e_steps=2,
+                      n_v=256, bounds="normalized_laplacian", ref_nv=1024, ref_prec="f32",
+                      f64_steps=2, e2e_steps=2,
                       desc="normalized Laplacian of a Chung-Lu graph, n=1048576, "
                            "beta=2.5, mean degree 20, seed 3 (a quarter of the 4M-row "
                            "graph, small enough for counter captures)"),
     "batched": dict(kind="batched", count=512, seed=4, M=200, n_v=32,
                     desc="512 Anderson lattices, L ~ U{10..40}, W ~ U[1,16], seed 4"),
+    # the learned moments-to-DOS network: instances (2/3 Anderson lattices, 1/3
+    # Chung-Lu normalized Laplacians, n in [n_lo, n_hi]); the first held_out are
+    # kept for scoring and for the timed serving step, the rest train the network
+    "learned": dict(kind="learned", instances=20000, held_out=2000, n_lo=4096, n_hi=64000,
+                    seed=5, n_v_in=4, M_in=64, n_v_ref=1024, M_ref=256, train_steps=20000,
+                    batch=512, lr=1e-3, kpm_nv=(4, 16, 64, 256),
+                    desc="learned moments-to-DOS network on generated Anderson lattices and "
+                         "Chung-Lu graphs"),
 }
 
 
@@ -117,6 +127,10 @@ def fma_per_step(n, nnz, n_v):
     """FMAs of one fused step: nnz*n_v (SpMM) + 2 n n_v (shift, recurrence) + 2 n n_v (dots)."""
     return nnz * n_v + 4 * n * n_v
 
+
+# The spectrum of a normalized Laplacian I - D^-1/2 A D^-1/2 lies in [0, 2];
+# padded by 1% of the width per side.
+NORMALIZED_LAPLACIAN_BOUNDS = (-0.02, 2.02)
 
 # GB300's FP64 rate is not measured here: NVIDIA's nominal figure, next to which
 # the FP64 fused step's ncu FP64-pipe utilisation is the evidence of the bound.
@@ -267,10 +281,7 @@ def run_reference(args):
     if w["kind"] == "batched":
         return run_reference_batched(args, w)
     if w["kind"] == "learned":
-        print(json.dumps({"impl": "reference", "unavailable":
-                          "the learned workload trains the library's network; its oracle is "
-                          "the CPU KPM of the kpm workloads"}))
-        return 0
+        return run_reference_learned(args, w)
     if args.method != "kpm":
         return run_reference_method(args, w)
     from oracle import bounds as obounds
@@ -278,8 +289,11 @@ def run_reference(args):
     A = make_matrix(w)
     if args.precision == "f32":
         A = A.astype(np.float32)
-    lb, ub = obounds.bounds(A, w.get("bounds", "gershgorin"), steps=20, seed=w["seed"],
-                            pad_frac=0.01)
+    if w.get("bounds") == "normalized_laplacian":
+        lb, ub = NORMALIZED_LAPLACIAN_BOUNDS
+    else:
+        lb, ub = obounds.bounds(A, w.get("bounds", "gershgorin"), steps=20, seed=w["seed"],
+                                pad_frac=0.01)
     M = w["M"]
     cores = os.cpu_count() or 1
     step_s = min(6.0, max(0.5, 90.0 / max(1, args.steps + args.warmup)))
@@ -308,6 +322,69 @@ def run_reference(args):
             "cpu_baseline": {"value": value, "unit": "moments/s", "cores": min(cores, nv),
                              "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": "moments/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+def run_reference_learned(args, w):
+    """Reference arm of the learned workload: its serving path on the host cores
+    with the oracle -- FP64 KPM oracle (n_v = 4, M = 64) and the FP64 network
+    reference with bfloat16 operands emulated -- over a bounded sample of the
+    held-out instances.  The cost does not depend on the weights, so the network
+    is the reference's own initialisation (no training on the host)."""
+    from oracle import bounds as obounds
+    from oracle import kpm as okpm
+    from oracle import mlp as omlp
+    from synthetic.instances import learned_instance_specs, make_instance
+    specs = learned_instance_specs(w["instances"], w["seed"], w["n_lo"], w["n_hi"])
+    cores = os.cpu_count() or 1
+    step_s = min(6.0, max(0.5, 90.0 / max(1, args.steps + args.warmup)))
+    p = omlp.init_params(w["M_in"], 512, 256, 3)
+    seed_in = w["seed"] * 1000 + 1
+    mats, t_est = [], 0.0
+    for b, sp in enumerate(specs[:w["held_out"]]):
+        A = make_instance(sp)
+        if "chung" in A.meta["family"]:
+            lb, ub = -0.02, 2.02
+        else:
+            lb, ub = obounds.bounds(A, "gershgorin", pad_frac=0.01)
+        t0 = time.perf_counter()
+        mu = okpm.kpm_moments(A, lb, ub, w["M_in"], w["n_v_in"], seed_in, batch_index=b,
+                              nthreads=cores)
+        omlp.forward(p, mu[1:][None, :].astype(np.float32).astype(np.float64), bf16=True)
+        t_est += time.perf_counter() - t0
+        mats.append((b, A, lb, ub))
+        if t_est >= step_s:
+            break
+
+    def one():
+        for b, A, lb, ub in mats:
+            mu = okpm.kpm_moments(A, lb, ub, w["M_in"], w["n_v_in"], seed_in, batch_index=b,
+                                  nthreads=cores)
+            omlp.forward(p, mu[1:][None, :].astype(np.float32).astype(np.float64), bf16=True)
+    for _ in range(min(args.warmup, 1)):
+        one()
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        one()
+        times.append(time.perf_counter() - t0)
+    t = sum(times) / len(times)
+    value = len(mats) / t
+    sample = (f"each step: {len(mats)} of the {w['held_out']} held-out instances, FP64 KPM "
+              f"oracle (n_v={w['n_v_in']}, M={w['M_in']}) + FP64 network reference, "
+              f"{cores} threads")
+    line = {"metric": "DOS/sec (learned: n_v=4, M=64 sweep + network, 256-point DOS)",
+            "value": value, "unit": "DOS/s", "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * t, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": args.workload, "instances": w["instances"],
+                       "held_out": w["held_out"], "sampled": len(mats)},
+            "impl": "reference",
+            "cpu_baseline": {"value": value, "unit": "DOS/s", "cores": cores, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": "DOS/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
     return 0
@@ -581,6 +658,173 @@ def run_batched(args, w, world, rank, local, device):
     return 0
 
 
+def run_learned(args, w, world, rank, local, device):
+    """The learned part at its configured scale.
+
+    Setup (reported, not timed as the step): generate the instances (host pool),
+    sweep them for the network's inputs (n_v = 4, M = 64) and targets (n_v = 1024,
+    M = 256 Jackson DOS on 256 nodes), train the network on all but the held-out
+    instances.  A step is the serving path over all held-out instances: bounds,
+    the batched n_v = 4, M = 64 sweep and the network reading the moments in
+    place -- one DOS per instance on the 256-point grid.  Metric: DOS per second,
+    next to the held-out smoothed L1 error of the network and of plain Jackson KPM
+    at n_v = 4, and the plain-KPM path at the vector count that matches the
+    network's error (DOS/s at equal error)."""
+    import torch
+
+    from paper_1308_5467_gb300 import dos, learned
+    from synthetic.instances import learned_instance_specs, stream_instances
+    count = w["instances"] if not args.instances else args.instances
+    held = max(1, min(w["held_out"], count // 10)) if args.instances else w["held_out"]
+    specs = learned_instance_specs(count, w["seed"], w["n_lo"], w["n_hi"])
+    seed_in = w["seed"] * 1000 + 1
+    ctx = dos.Context(local)
+    t0 = time.perf_counter()
+    stream = stream_instances(specs)
+    held_mats = (next(stream) for _ in range(held))
+    test = learned.make_dataset(ctx, held_mats, seed_in, w["n_v_in"], w["M_in"], w["n_v_ref"],
+                                w["M_ref"], b0=0, keep_groups=True)
+    train = learned.make_dataset(ctx, stream, seed_in, w["n_v_in"], w["M_in"], w["n_v_ref"],
+                                 w["M_ref"], b0=held)
+    gen_s = time.perf_counter() - t0
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    steps = args.train_steps or w["train_steps"]
+    net = learned.train(ctx, train["x"], train["y"], steps=steps, batch=w["batch"], lr=w["lr"],
+                        seed=3)
+    train_s = time.perf_counter() - t1
+    e_kpm4, e_net = learned.score(ctx, test, net)
+    curve = {}
+    for nv in w["kpm_nv"]:
+        curve[nv] = float(learned.kpm_errors(ctx, test, nv, w["M_ref"], seed_in).mean())
+    match = next((nv for nv in w["kpm_nv"] if curve[nv] <= e_net.mean()), None)
+
+    groups = test["groups"]
+    pipe = learned.LearnedPipeline(ctx, net, groups, seed_in, w["n_v_in"], w["M_in"])
+
+    def timed(fn, steps_, warmup, profile=False):
+        for _ in range(warmup):
+            fn()
+        torch.cuda.synchronize()
+        if profile:
+            ctx.dos_profile_enable(True)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(steps_):
+            fn()
+        e1.record()
+        torch.cuda.synchronize()
+        prof = ctx.dos_profile_read() if profile else None
+        if profile:
+            ctx.dos_profile_enable(False)
+        return e0.elapsed_time(e1) / steps_, prof
+
+    with ClockSampler(gpu_id_for(local)) as clk:
+        ms, prof = timed(pipe.run, args.steps, args.warmup, profile=True)
+    value = held / (ms * 1e-3)
+    # the plain-KPM path at the matching vector count (or the largest tried)
+    nv_eq = match or w["kpm_nv"][-1]
+    kpm = learned.KPMPipeline(ctx, groups, seed_in, nv_eq, w["M_ref"])
+    ms_kpm, _ = timed(kpm.run, max(2, args.steps // 4), 1)
+    kpm4 = learned.KPMPipeline(ctx, groups, seed_in, w["n_v_in"], w["M_in"])
+    ms_kpm4, _ = timed(kpm4.run, max(2, args.steps // 4), 1)
+    # end to end: host CSR and a host read of every DOS, through the same calls
+    e2e = None
+    if not args.no_e2e:
+        for g in groups:
+            g.host_A
+        ms_e2e, _ = timed(lambda: pipe.run(host=True).cpu(), max(2, args.steps // 2), 1)
+        h2d = 2 * sum(g.host_bytes for g in groups)
+        e2e = {"value": held / (ms_e2e * 1e-3), "unit": "DOS/s", "h2d_bytes_per_step": h2d,
+               "d2h_bytes_per_step": held * net.n_out * 4, "ms_per_step": ms_e2e}
+    # roofline of the fused step kernel of the sweep (the dominant kernel)
+    peaks, peak_kind = measured_peaks()
+    launch_ms = prof["step_ms"] / max(1, prof["step_launches"])
+    S = max(1, (w["M_in"] + 1) // 2)
+    alg = sum(algorithmic_bytes_per_step(g.n, g.nnz, w["n_v_in"], "f32") for g in groups) / \
+        len(groups)
+    achieved = alg / (launch_ms * 1e-3) / 1e9
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        cpu = learned_cpu_baseline(ctx, net, test, groups, w, seed_in)
+    hold_n = test["n"]
+    line = {
+        "metric": "DOS/sec (learned: n_v=4, M=64 sweep + network, 256-point DOS)",
+        "value": value, "unit": "DOS/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32 sweep, bf16 network (FP32 accumulation)",
+        "data": "synthetic",
+        "config": {"workload": "learned", "desc": w["desc"], "instances": count,
+                   "train_instances": count - held, "held_out": held,
+                   "n_range": [w["n_lo"], w["n_hi"]],
+                   "held_out_rows": int(hold_n.sum()), "held_out_laplacians":
+                       int(test["laplacian"].sum()),
+                   "inputs": f"mu_1..mu_{w['M_in']} from n_v={w['n_v_in']}",
+                   "targets": f"Jackson DOS at 256 Chebyshev nodes from n_v={w['n_v_ref']}, "
+                              f"M={w['M_ref']}",
+                   "network": "64-512-512-256 ReLU, BF16 operands, FP32 accumulation, Adam",
+                   "train_steps": steps, "batch": w["batch"],
+                   "l2": "inputs larger than L2: %.1f GB of CSR held out" %
+                         (sum(g.host_bytes for g in groups) / 1e9)},
+        "e1_network": float(e_net.mean()), "e1_jackson_nv4_M64": float(e_kpm4.mean()),
+        "e1_jackson_M256_by_nv": {str(k): v for k, v in curve.items()},
+        "equal_error": {"kpm_nv": nv_eq, "reached": match is not None,
+                        "kpm_M": w["M_ref"], "kpm_dos_per_s": held / (ms_kpm * 1e-3),
+                        "kpm_ms_per_step": ms_kpm},
+        "jackson_nv4_M64": {"dos_per_s": held / (ms_kpm4 * 1e-3), "ms_per_step": ms_kpm4},
+        "setup": {"generation_s": gen_s, "host_wait_s": test["timing"]["host_wait_s"] +
+                  train["timing"]["host_wait_s"],
+                  "gpu_sweep_s": test["timing"]["gpu_s"] + train["timing"]["gpu_s"],
+                  "gpu_moments_per_s": (test["timing"]["moments"] + train["timing"]["moments"])
+                  / max(1e-9, test["timing"]["gpu_s"] + train["timing"]["gpu_s"]),
+                  "train_s": train_s, "train_samples_per_s": steps * w["batch"] / train_s},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"],
+                     "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"], "traffic": None,
+                     "peak_source": peak_kind, "kernel": "fused sweep step (n_v = 4)",
+                     "algorithmic_bytes_per_launch": alg, "launch_ms": launch_ms,
+                     "steps_per_sweep": S},
+        "e2e": e2e, "cpu_baseline": cpu, "gpu_launches": prof["launches"],
+        "clocks": clk.summary(),
+    }
+    if rank == 0:
+        print(json.dumps(line))
+    ctx.close()
+    return 0
+
+
+def learned_cpu_baseline(ctx, net, test, groups, w, seed_in, target_s=12.0):
+    """The serving path on the host cores with the oracle: the FP64 KPM oracle
+    (n_v = 4, M = 64) and the FP64 network reference (bfloat16 operands emulated)
+    on a sample of held-out instances, DOS per second."""
+    from oracle import kpm as okpm
+    from oracle import mlp as omlp
+    from synthetic import CSR
+    cores = os.cpu_count() or 1
+    p = omlp.unflatten(net.dos_mlp_get_params().astype(np.float64), net.n_in, net.n_hidden,
+                       net.n_out)
+    done, t_used = 0, 0.0
+    for g in groups:
+        rp, ci, va = g.host
+        for b in range(g.B):
+            r0, r1 = int(g.seg[b]), int(g.seg[b + 1])
+            e0, e1 = int(rp[r0]), int(rp[r1])
+            A = CSR(r1 - r0, (rp[r0:r1 + 1] - e0).astype(np.int32), ci[e0:e1], va[e0:e1])
+            t0 = time.perf_counter()
+            mu = okpm.kpm_moments(A, float(g.lb[b]), float(g.ub[b]), w["M_in"], w["n_v_in"],
+                                  seed_in, batch_index=g.b0 + b, nthreads=cores)
+            omlp.forward(p, mu[1:][None, :].astype(np.float32).astype(np.float64), bf16=True)
+            t_used += time.perf_counter() - t0
+            done += 1
+            if t_used >= target_s:
+                break
+        if t_used >= target_s:
+            break
+    return {"value": done / t_used, "unit": "DOS/s", "cores": cores, "kind": "oracle",
+            "sample": f"{done} held-out instances: FP64 KPM oracle (n_v={w['n_v_in']}, "
+                      f"M={w['M_in']}, {cores} threads over the vectors) and the FP64 network "
+                      f"reference, {t_used:.1f} s"}
+
+
 def lanczos_spmm_bytes(n, nnz, ld):
     """Compulsory bytes of one Lanczos block-SpMM launch (FP64): CSR once, q_j read
     once, q_{j-1} read and w written."""
@@ -765,8 +1009,10 @@ def main():
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
-    ap.add_argument("--seconds", type=float, default=0.0,
-                    help="learned workload: training budget in seconds (0: its default)")
+    ap.add_argument("--instances", type=int, default=0,
+                    help="learned workload: number of generated instances (0: its default)")
+    ap.add_argument("--train-steps", type=int, default=0,
+                    help="learned workload: Adam steps (0: its default)")
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--workload", default="chunglu", choices=sorted(WORKLOADS))
     ap.add_argument("--method", default="kpm", choices=["kpm"] + sorted(METHODS),
@@ -819,6 +1065,8 @@ def main():
     bmethod = w.get("bounds", "gershgorin")
 
     def bounds_of(Acsr):
+        if bmethod == "normalized_laplacian":   # known analytically: no kernel to run
+            return NORMALIZED_LAPLACIAN_BOUNDS
         return ctx.dos_bounds(Acsr, bmethod, steps=20, seed=seed, pad_frac=0.01)
 
     lb, ub = bounds_of(Ad)
@@ -978,7 +1226,9 @@ def main():
                        "accumulation": ("FP32 products summed per row in FP32, rows "
                                         "accumulated as float pairs per thread, blocks and "
                                         "tiles in FP64") if prec == "f32" else "FP64",
-                       "bounds": f"{bmethod}, padded 1% per side",
+                       "bounds": ("[0, 2] (any normalized Laplacian)"
+                                  if bmethod == "normalized_laplacian" else bmethod)
+                                 + ", padded 1% per side",
                        "reference_dos": f"{ref_prec.upper()} sweep of {ref_nv} other vectors",
                        "l2": "inputs larger than L2: %.0f MB touched per fused step"
                              % (algorithmic_bytes_per_step(A.n, A.nnz, n_v, prec) / 1e6),

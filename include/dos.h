@@ -329,6 +329,19 @@ int dos_reconstruct(dos_ctx *ctx, const double *mu, int M, int damping, double l
                     const double *t, int N_t, double *phi_hat, double *phi_lambda, void *stream);
 
 /*
+ * dos_reconstruct for B moment rows at once (the output of
+ * dos_kpm_moments_batched): mu is B x (M+1) doubles, row-major; phi_hat is
+ * B x N_t doubles, row b the density in t of row b of mu (Eq. tdosFinal with
+ * the coefficients of Eq. expmu and, for DOS_DAMP_JACKSON, Appendix A's
+ * factors), on the points t (N_t, in (-1, 1)) or, when t is NULL, the Chebyshev
+ * nodes.  Each row equals dos_reconstruct's output for that row bit for bit.
+ * Host or device arrays; synchronises `stream` when phi_hat is host memory.
+ * 1 <= B <= 2^20, B N_t <= 2^31.  Errors: DOS_EINVAL, DOS_ENOMEM, DOS_ECUDA.
+ */
+int dos_reconstruct_batched(dos_ctx *ctx, const double *mu, int B, int M, int damping,
+                            const double *t, int N_t, double *phi_hat, void *stream);
+
+/*
  * Inverse of dos_reconstruct on the Chebyshev grid: given phi_hat at the N_t
  * nodes t_i = -cos(pi (i + 1/2) / N_t) (host or device), the moments
  *     mu_k = integral phi_hat(t) T_k(t) dt = (pi/N_t) sum_i sqrt(1 - t_i^2) phi_hat(t_i) T_k(t_i)

@@ -53,13 +53,17 @@ int dos_mlp_get_params(dos_mlp *mlp, float *params, void *stream);
  * memory. */
 int dos_mlp_forward(dos_mlp *mlp, const float *x, int B, float *y, void *stream);
 
-/* Inference: y = network(x) for any number of rows B >= 1 (x: B x n_in,
- * y: B x n_out, row-major FP32, host or device).  Runs the forward kernels over
- * consecutive slices of at most `max_rows` rows (0: 8192), so the activation
- * buffers stay bounded whatever B is; each row's output is bitwise the same as
- * from dos_mlp_forward.  Synchronises when x or y is host memory. */
-int dos_mlp_infer(dos_mlp *mlp, const float *x, int64_t B, float *y, int max_rows,
-                  void *stream);
+/* Inference: y = network(x) for any number of rows B >= 1.  Row r of x is the
+ * n_in elements at x + r * ldx (ldx >= n_in; 0 means n_in) of type x_dtype
+ * (DOS_F32, or DOS_F64 converted to FP32 on the device), so the network can
+ * read mu_1..mu_{n_in} straight out of dos_kpm_moments_batched's output
+ * (x = mu + 1, ldx = M + 1).  y: B x n_out row-major FP32.  Host or device
+ * arrays.  Runs the forward kernels over consecutive slices of at most
+ * `max_rows` rows (0: 8192), so the activation buffers stay bounded whatever B
+ * is; each row's output is bitwise the same as dos_mlp_forward's for the same
+ * FP32 input.  Synchronises when x or y is host memory. */
+int dos_mlp_infer(dos_mlp *mlp, const void *x, int x_dtype, int64_t ldx, int64_t B, float *y,
+                  int max_rows, void *stream);
 
 /* Checkpoint: write the network to `path` in a byte-stable little-endian file:
  *   bytes 0-7   magic "DOSMLP\0\1" (format version 1)

@@ -950,6 +950,45 @@ int dos_reconstruct(dos_ctx *ctx, const double *mu, int M, int damping, double l
     });
 }
 
+int dos_reconstruct_batched(dos_ctx *ctx, const double *mu, int B, int M, int damping,
+                            const double *t, int N_t, double *phi_hat, void *stream) {
+    return guarded(ctx, [&] {
+        DOS_REQUIRE(mu && phi_hat, "mu / phi_hat is NULL");
+        DOS_REQUIRE(B >= 1 && B <= (1 << 20), "B must be in [1, 2^20]");
+        DOS_REQUIRE(M >= 0 && M <= 100000, "M must be in [0, 100000]");
+        DOS_REQUIRE(N_t >= 1 && N_t <= (1 << 20), "N_t must be in [1, 2^20]");
+        DOS_REQUIRE((int64_t)B * N_t <= (int64_t(1) << 31), "B * N_t must be <= 2^31");
+        DOS_REQUIRE(damping == DOS_DAMP_NONE || damping == DOS_DAMP_JACKSON, "bad damping");
+        cudaStream_t s = (cudaStream_t)stream;
+        const size_t nmu = (size_t)B * (M + 1);
+        const bool mu_dev = is_device_ptr(mu), out_dev = is_device_ptr(phi_hat);
+        // device staging: coefficients | mu (if host) | t (if given) | phi_hat (if host)
+        const size_t nd = nmu + (mu_dev ? 0 : nmu) + (t ? N_t : 0) +
+                          (out_dev ? 0 : (size_t)B * N_t);
+        double *buf = (double *)ctx->rec_in.get(nd * sizeof(double));
+        double *coef = buf, *p = buf + nmu;
+        const double *dmu = mu;
+        if (!mu_dev) {
+            DOS_CUDA_TRY(cudaMemcpyAsync(p, mu, nmu * sizeof(double), cudaMemcpyHostToDevice, s));
+            dmu = p;
+            p += nmu;
+        }
+        const double *dt = nullptr;
+        if (t) {
+            DOS_CUDA_TRY(cudaMemcpyAsync(p, t, N_t * sizeof(double), cudaMemcpyDefault, s));
+            dt = p;
+            p += N_t;
+        }
+        double *dphi = out_dev ? phi_hat : p;
+        launch_reconstruct_rows(dmu, M + 1, B, M, damping, dt, N_t, coef, dphi, s);
+        if (!out_dev) {
+            DOS_CUDA_TRY(cudaMemcpyAsync(phi_hat, dphi, (size_t)B * N_t * sizeof(double),
+                                         cudaMemcpyDeviceToHost, s));
+            DOS_CUDA_TRY(cudaStreamSynchronize(s));
+        }
+    });
+}
+
 int dos_lanczos_ritz(dos_ctx *ctx, const dos_csr *Adesc, int M, int n_v, uint64_t seed,
                      double *theta, double *weight, int *m_used, void *stream) {
     return guarded(ctx, [&] {

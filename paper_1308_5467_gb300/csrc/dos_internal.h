@@ -239,6 +239,10 @@ int reduce_blocks(int num_sms, int64_t n);
 void launch_reconstruct(const double *mu, int M, int damping, double lb, double ub,
                         const double *t, int N_t, double *coef_scratch, double *phi_hat,
                         double *phi_lambda, cudaStream_t s);
+// B rows of moments (row stride ldm) -> B x N_t phi_hat; coef_scratch: B (M+1) doubles
+void launch_reconstruct_rows(const double *mu, int64_t ldm, int B, int M, int damping,
+                             const double *t, int N_t, double *coef_scratch, double *phi_hat,
+                             cudaStream_t s);
 void launch_blur_kpm(const double *mu, int M, int damping, double lb, double ub, double sigma,
                      int N_q, double x0, double h, int N_x, double *poly_scratch, double *out,
                      cudaStream_t s);

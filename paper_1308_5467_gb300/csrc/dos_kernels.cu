@@ -51,6 +51,39 @@ __global__ void reconstruct_kernel(const double *__restrict__ a, int M, double d
     }
 }
 
+// Many moment rows at once: row b of mu (stride ldm) -> coefficients (stride M+1)
+// -> phi_hat row b (stride N_t), the same arithmetic as the single-row kernels.
+__global__ void coef_rows_kernel(const double *__restrict__ mu, int64_t ldm, int B, int M,
+                                 int damping, double *__restrict__ a) {
+    const double alpha = M_PI / (double)(M + 2);
+    const double sa = sin(alpha), ca = cos(alpha);
+    const int64_t total = (int64_t)B * (M + 1);
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t b = e / (M + 1);
+        const int k = (int)(e - b * (M + 1));
+        double g = 1.0;
+        if (damping == DOS_DAMP_JACKSON) {
+            const double ka = k * alpha;
+            g = ((1.0 - (double)k / (M + 2)) * sa * cos(ka) + ca * sin(ka) / (M + 2)) / sa;
+        }
+        a[e] = (k == 0 ? 1.0 : 2.0) * g * mu[b * ldm + k];
+    }
+}
+
+__global__ void reconstruct_rows_kernel(const double *__restrict__ a, int B, int M,
+                                        const double *__restrict__ t, int N_t,
+                                        double *__restrict__ phi_hat) {
+    const int64_t total = (int64_t)B * N_t;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t b = e / N_t;
+        const int i = (int)(e - b * N_t);
+        const double ti = t ? t[i] : -cospi((i + 0.5) / (double)N_t);
+        phi_hat[e] = clenshaw(a + b * (M + 1), M, ti) / (M_PI * sqrt((1.0 - ti) * (1.0 + ti)));
+    }
+}
+
 // P(t_i) and the node's position c + d t_i in eigenvalue units.
 __global__ void nodes_kernel(const double *__restrict__ a, int M, int N_q, double c, double d,
                              double *__restrict__ P, double *__restrict__ Y) {
@@ -187,6 +220,17 @@ void launch_reconstruct(const double *mu, int M, int damping, double lb, double 
     DOS_LAUNCHED();
     reconstruct_kernel<<<grid_cap(N_t, 256, 4096), 256, 0, s>>>(
         coef_scratch, M, 0.5 * (ub - lb), t, N_t, phi_hat, phi_lambda);
+    DOS_LAUNCHED();
+}
+
+void launch_reconstruct_rows(const double *mu, int64_t ldm, int B, int M, int damping,
+                             const double *t, int N_t, double *coef_scratch, double *phi_hat,
+                             cudaStream_t s) {
+    coef_rows_kernel<<<grid_cap((int64_t)B * (M + 1), 256, 4096), 256, 0, s>>>(
+        mu, ldm, B, M, damping, coef_scratch);
+    DOS_LAUNCHED();
+    reconstruct_rows_kernel<<<grid_cap((int64_t)B * N_t, 256, 8192), 256, 0, s>>>(
+        coef_scratch, B, M, t, N_t, phi_hat);
     DOS_LAUNCHED();
 }
 

@@ -32,6 +32,7 @@ struct dos_mlp {
     int64_t wsz[3] = {0};  // element counts of W1, W2, W3
     Buffer state;          // params | grads | adam m | adam v (FP32), bf16 weight copies
     Buffer acts;           // per-batch activations
+    Buffer in_stage;       // dos_mlp_infer: a host input slice copied to the device
     int cap_B = 0;
     int64_t step = 0;
     float *params = nullptr, *grads = nullptr, *m = nullptr, *v = nullptr;
@@ -344,6 +345,20 @@ void stage_input(dos_mlp *mlp, const float *x, int B, const float *target, cudaS
     DOS_LAUNCHED();
 }
 
+// Input rows of any stride and element type to the bfloat16 operand, through
+// FP32 (the type of the network's input): xb[r, j] = bf16(float(x[r * ldx + j])).
+template <typename T>
+__global__ void stage_rows_kernel(const T *__restrict__ x, int64_t ldx, int n_in, int B,
+                                  bf16 *__restrict__ xb) {
+    const int64_t total = (int64_t)B * n_in;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t r = e / n_in;
+        const int j = (int)(e - r * n_in);
+        xb[e] = __float2bfloat16_rn((float)x[r * ldx + j]);
+    }
+}
+
 void forward(dos_mlp *mlp, int B, cudaStream_t s) {
     const bf16 *W1 = mlp->wb, *W2 = mlp->wb + mlp->wsz[0], *W3 = W2 + mlp->wsz[1];
     const float *p = mlp->params;
@@ -497,6 +512,7 @@ int dos_mlp_destroy(dos_mlp *mlp) {
     cudaDeviceSynchronize();
     mlp->state.release();
     mlp->acts.release();
+    mlp->in_stage.release();
     if (prev >= 0) cudaSetDevice(prev);
     cudaGetLastError();
     delete mlp;
@@ -544,22 +560,43 @@ int dos_mlp_forward(dos_mlp *mlp, const float *x, int B, float *y, void *stream)
     });
 }
 
-int dos_mlp_infer(dos_mlp *mlp, const float *x, int64_t B, float *y, int max_rows,
-                  void *stream) {
+int dos_mlp_infer(dos_mlp *mlp, const void *x, int x_dtype, int64_t ldx, int64_t B, float *y,
+                  int max_rows, void *stream) {
     return mguard(mlp, [&] {
         DOS_REQUIRE(x != nullptr && y != nullptr, "x / y is NULL");
+        DOS_REQUIRE(x_dtype == DOS_F32 || x_dtype == DOS_F64, "x_dtype must be DOS_F32 or DOS_F64");
         DOS_REQUIRE(B >= 1, "B must be >= 1");
         DOS_REQUIRE(max_rows >= 0 && max_rows <= 65536, "max_rows must be in [0, 65536]");
+        if (ldx == 0) ldx = mlp->n_in;
+        DOS_REQUIRE(ldx >= mlp->n_in, "ldx must be >= n_in");
         const int rows = max_rows ? max_rows : 8192;
+        const size_t esz = x_dtype == DOS_F64 ? 8 : 4;
+        const bool x_host = is_host_ptr(x);
         cudaStream_t s = (cudaStream_t)stream;
         for (int64_t r0 = 0; r0 < B; r0 += rows) {
             const int b = (int)std::min<int64_t>(rows, B - r0);
-            stage_input(mlp, x + r0 * mlp->n_in, b, nullptr, s);
+            ensure_batch(mlp, b);
+            const uint8_t *src = (const uint8_t *)x + (size_t)r0 * ldx * esz;
+            if (x_host) {  // the slice's rows, copied as one block
+                const size_t bytes = ((size_t)(b - 1) * ldx + mlp->n_in) * esz;
+                void *d = mlp->in_stage.get(bytes);
+                DOS_CUDA_TRY(cudaMemcpyAsync(d, src, bytes, cudaMemcpyHostToDevice, s));
+                src = (const uint8_t *)d;
+            }
+            if (x_dtype == DOS_F64)
+                stage_rows_kernel<double><<<grid1((int64_t)b * mlp->n_in), 256, 0, s>>>(
+                    (const double *)src, ldx, mlp->n_in, b, mlp->xb);
+            else
+                stage_rows_kernel<float><<<grid1((int64_t)b * mlp->n_in), 256, 0, s>>>(
+                    (const float *)src, ldx, mlp->n_in, b, mlp->xb);
+            DOS_LAUNCHED();
             forward(mlp, b, s);
             DOS_CUDA_TRY(cudaMemcpyAsync(y + r0 * mlp->n_out, mlp->y,
                                          (size_t)b * mlp->n_out * 4, cudaMemcpyDefault, s));
+            // the next slice overwrites the staging and activation buffers: with a host
+            // output the copy above must finish first (stream order covers device ones)
+            if (x_host || is_host_ptr(y)) DOS_CUDA_TRY(cudaStreamSynchronize(s));
         }
-        if (is_host_ptr(x) || is_host_ptr(y)) DOS_CUDA_TRY(cudaStreamSynchronize(s));
     });
 }
 

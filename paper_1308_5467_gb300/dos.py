@@ -78,6 +78,7 @@ _SIGS = {
                                      _i, _vp, _vp, C.POINTER(dos_kpm_opts), _vp]),
     "dos_tune": (_i, [_vp, C.POINTER(dos_csr), _i, _vp, _i, _i, C.POINTER(dos_launch), _dp, _vp]),
     "dos_reconstruct": (_i, [_vp, _vp, _i, _i, _d, _d, _vp, _i, _vp, _vp, _vp]),
+    "dos_reconstruct_batched": (_i, [_vp, _vp, _i, _i, _i, _vp, _i, _vp, _vp]),
     "dos_smoothed_error": (_i, [_vp, _vp, _i, _i, _d, _d, _vp, _i64, _vp, _i, _i, _d, _i, _dp,
                                 _dp, _vp]),
     "dos_moments_from_grid": (_i, [_vp, _vp, _i, _i, _vp, _vp]),
@@ -102,7 +103,7 @@ _SIGS.update({
     "dos_mlp_set_params": (_i, [_vp, _vp, _vp]),
     "dos_mlp_get_params": (_i, [_vp, _vp, _vp]),
     "dos_mlp_forward": (_i, [_vp, _vp, _i, _vp, _vp]),
-    "dos_mlp_infer": (_i, [_vp, _vp, _i64, _vp, _i, _vp]),
+    "dos_mlp_infer": (_i, [_vp, _vp, _i, _i64, _i64, _vp, _i, _vp]),
     "dos_mlp_save": (_i, [_vp, C.c_char_p, _vp]),
     "dos_mlp_load": (_i, [_vp, C.c_char_p, C.POINTER(_vp), _vp]),
     "dos_mlp_loss_grad": (_i, [_vp, _vp, _vp, _i, C.POINTER(C.c_float), _vp, _vp]),
@@ -336,6 +337,22 @@ class Context:
                                          int(N_t), po, pl, _stream_of(mu, out)))
         return (out, outl) if want_lambda or phi_lambda is not None else out
 
+    def dos_reconstruct_batched(self, mu, damping="jackson", t=None, N_t: int = 1000,
+                                phi_hat=None):
+        """Rows of moments (B, M+1) -> rows of phi_hat (B, N_t)."""
+        damp = DAMPINGS[damping] if isinstance(damping, str) else int(damping)
+        B, M = int(mu.shape[0]), int(mu.shape[1]) - 1
+        if t is not None:
+            N_t = int(t.shape[0])
+        out = np.empty((B, N_t), dtype=np.float64) if phi_hat is None else phi_hat
+        m = mu if _is_torch(mu) else np.ascontiguousarray(mu, dtype=np.float64)
+        pm, _, k0 = _ptr(m)
+        pt, _, k1 = _ptr(t)
+        po, _, k2 = _ptr(out)
+        self._check(_lib.dos_reconstruct_batched(self._h, pm, B, M, damp, pt, int(N_t), po,
+                                                 _stream_of(m, out)))
+        return out
+
     def dos_lanczos_ritz(self, A: CSRArrays, M: int, n_v: int, seed: int):
         """(theta, weight, m_used): Ritz values / weights per run, shape (n_v, M)."""
         theta = np.empty((n_v, M))
@@ -545,15 +562,30 @@ class MLP:
     def dos_mlp_save(self, path: str):
         self.ctx._check(_lib.dos_mlp_save(self._h, os.fsencode(path), C.c_void_p(0)))
 
-    def dos_mlp_infer(self, x, out=None, max_rows: int = 0):
-        """network(x) for any number of rows (sliced through bounded buffers)."""
-        xa = x if _is_torch(x) else np.ascontiguousarray(x, dtype=np.float32)
-        B = int(xa.shape[0])
+    def dos_mlp_infer(self, x, out=None, max_rows: int = 0, col0: int = 0):
+        """network(x[:, col0:col0 + n_in]) for any number of rows (sliced through
+        bounded buffers); x float32 or float64 (e.g. the moments of a batched sweep
+        with col0 = 1), host or device, rows contiguous."""
+        if _is_torch(x):
+            xa = x
+            dt = str(x.dtype).replace("torch.", "")
+        else:
+            xa = np.ascontiguousarray(x)
+            if xa.dtype not in (np.float32, np.float64):
+                xa = xa.astype(np.float32)
+            dt = str(xa.dtype)
+        if _is_torch(xa) and not xa.is_contiguous():
+            raise ValueError("x must be contiguous")
+        B, ldx = int(xa.shape[0]), int(xa.shape[1])
+        if col0 < 0 or col0 + self.n_in > ldx:
+            raise ValueError("x has too few columns for n_in at col0")
+        esz = 8 if dt == "float64" else 4
         y = np.empty((B, self.n_out), dtype=np.float32) if out is None else out
         px, _, k0 = _ptr(xa)
         py, _, k1 = _ptr(y)
-        self.ctx._check(_lib.dos_mlp_infer(self._h, px, B, py, int(max_rows),
-                                           _stream_of(xa, y)))
+        self.ctx._check(_lib.dos_mlp_infer(self._h, px + col0 * esz,
+                                           DOS_F64 if dt == "float64" else DOS_F32, ldx, B, py,
+                                           int(max_rows), _stream_of(xa, y)))
         return y
 
     def close(self):

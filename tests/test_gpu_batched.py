@@ -61,12 +61,13 @@ def test_small_batch_parity(ctx, precision, M, n_v):
     pv = np.empty((B, n_v, M + 1))
     mu = ctx.dos_kpm_moments_batched(A, seg, lb, ub, M, n_v, seed=11, precision=precision,
                                      mu_per_vec=pv)
-    tol = 1e-12 if precision == "f64" else tol32(M)
     for b, Ab in enumerate(mats):
         ref = okpm.kpm_moments_per_vector(Ab.astype(dtype), lb[b], ub[b], M, n_v, seed=11,
                                           batch_index=b)
+        tol, tolt = (1e-12, 1e-12) if precision == "f64" else (tol32(M, Ab.n),
+                                                               tol32(M, Ab.n * n_v))
         assert np.all(np.abs(pv[b] - ref) <= tol), (b, fp32_ratio(pv[b], ref))
-        assert np.all(np.abs(mu[b] - ref.mean(axis=0)) <= tol), (b, fp32_ratio(mu[b], ref.mean(0)))
+        assert np.all(np.abs(mu[b] - ref.mean(axis=0)) <= tolt), (b, fp32_ratio(mu[b], ref.mean(0)))
 
 
 def test_batch_of_one_equals_single_call(ctx):
@@ -96,11 +97,11 @@ def test_full_batch_512_f32_sampled(ctx, batch512):
     assert np.all(np.abs(mu) <= 1.0 + 1e-5)
     sizes = np.array([m.n for m in mats])
     picks = sorted({int(np.argmin(sizes)), int(np.argmax(sizes)), 0, 255, 511, 100})
-    tol = tol32(200)
     for b in picks:
         ref = okpm.kpm_moments(mats[b].astype(np.float32), lb[b], ub[b], 200, 32, seed=4,
                                batch_index=b, nthreads=8)
-        assert np.all(np.abs(mu[b] - ref) <= tol), (b, fp32_ratio(mu[b], ref))
+        assert np.all(np.abs(mu[b] - ref) <= tol32(200, mats[b].n * 32)), (b, fp32_ratio(mu[b],
+                                                                                       ref))
 
 
 def test_autotuned_shape_gives_same_moments(ctx, batch512):
@@ -113,4 +114,5 @@ def test_autotuned_shape_gives_same_moments(ctx, batch512):
     tuned = ctx.dos_kpm_moments_batched(A, seg, lb, ub, 40, 32, seed=4, precision="f32")
     # another launch shape groups the FP32 row sums differently: both within the FP32
     # bound of the oracle, so within twice that bound of each other
-    assert np.all(np.abs(tuned - default) <= 2 * tol32(40)), fp32_ratio(tuned, default)
+    n_min = int(np.diff(seg).min())
+    assert np.all(np.abs(tuned - default) <= 2 * tol32(40, n_min * 32)), fp32_ratio(tuned, default)

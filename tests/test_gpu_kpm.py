@@ -96,9 +96,9 @@ def test_random_ragged_parity(ctx, precision, n, M, n_v):
     pv = np.empty((n_v, M + 1))
     mu = ctx.dos_kpm_moments(dev(Aw), lb, ub, M, n_v, seed=7, precision=precision, mu_per_vec=pv)
     ref = okpm.kpm_moments_per_vector(Aw, lb, ub, M, n_v, seed=7)
-    tol = TOL64 if precision == "f64" else tol32(M)
+    tol, tolt = (TOL64, TOL64) if precision == "f64" else (tol32(M, n), tol32(M, n * n_v))
     assert np.all(np.abs(pv - ref) <= tol), fp32_ratio(pv, ref)
-    assert np.all(np.abs(mu - ref.mean(axis=0)) <= tol), fp32_ratio(mu, ref.mean(axis=0))
+    assert np.all(np.abs(mu - ref.mean(axis=0)) <= tolt), fp32_ratio(mu, ref.mean(axis=0))
 
 
 @pytest.mark.parametrize("precision", ["f64", "f32"])
@@ -133,9 +133,9 @@ def test_vector_panels_large_n_v(ctx, precision):
     mu = ctx.dos_kpm_moments(dev(A), lb, ub, M, n_v, seed=4, precision=precision, mu_per_vec=pv)
     ref = okpm.kpm_moments_per_vector(A.astype(np.float32) if precision == "f32" else A,
                                       lb, ub, M, n_v, seed=4)
-    tol = TOL64 if precision == "f64" else tol32(M)
-    assert np.all(np.abs(pv - ref) <= tol)
-    assert np.all(np.abs(mu - ref.mean(axis=0)) <= tol)
+    tol, tolt = (TOL64, TOL64) if precision == "f64" else (tol32(M, A.n), tol32(M, A.n * n_v))
+    assert np.all(np.abs(pv - ref) <= tol), fp32_ratio(pv, ref)
+    assert np.all(np.abs(mu - ref.mean(axis=0)) <= tolt), fp32_ratio(mu, ref.mean(axis=0))
 
 
 def test_vec_offset_shards_union(ctx):
@@ -180,10 +180,11 @@ def test_staged_panels_parity(ctx, precision, launch):
         mu_tot = ctx.dos_kpm_moments(dev(Aw), lb, ub, 70, n_v, seed=5, precision=precision,
                                      launch=launch)
         ref = okpm.kpm_moments_per_vector(Aw, lb, ub, 70, n_v, seed=5)
-        tol = TOL64 if precision == "f64" else tol32(70)
-        assert np.all(np.abs(pv - ref) <= tol)
-        assert np.all(np.abs(mu - ref.mean(axis=0)) <= tol)
-        assert np.all(np.abs(mu_tot - ref.mean(axis=0)) <= tol)
+        tol, tolt = (TOL64, TOL64) if precision == "f64" else (tol32(70, A.n),
+                                                               tol32(70, A.n * n_v))
+        assert np.all(np.abs(pv - ref) <= tol), fp32_ratio(pv, ref)
+        assert np.all(np.abs(mu - ref.mean(axis=0)) <= tolt)
+        assert np.all(np.abs(mu_tot - ref.mean(axis=0)) <= tolt), fp32_ratio(mu_tot, ref.mean(0))
 
 
 @pytest.mark.parametrize("precision", ["f64", "f32"])
@@ -214,10 +215,11 @@ def test_wide_chunk_parity(ctx, precision, launch):
         mu_tot = ctx.dos_kpm_moments(dev(Aw), lb, ub, 70, n_v, seed=5, precision=precision,
                                      launch=launch)
         ref = okpm.kpm_moments_per_vector(Aw, lb, ub, 70, n_v, seed=5)
-        tol = TOL64 if precision == "f64" else tol32(70)
-        assert np.all(np.abs(pv - ref) <= tol)
-        assert np.all(np.abs(mu - ref.mean(axis=0)) <= tol)
-        assert np.all(np.abs(mu_tot - ref.mean(axis=0)) <= tol)
+        tol, tolt = (TOL64, TOL64) if precision == "f64" else (tol32(70, A.n),
+                                                               tol32(70, A.n * n_v))
+        assert np.all(np.abs(pv - ref) <= tol), fp32_ratio(pv, ref)
+        assert np.all(np.abs(mu - ref.mean(axis=0)) <= tolt)
+        assert np.all(np.abs(mu_tot - ref.mean(axis=0)) <= tolt), fp32_ratio(mu_tot, ref.mean(0))
 
 
 @pytest.mark.parametrize("precision", ["f64", "f32"])
@@ -253,10 +255,12 @@ def test_tma_gather_parity(ctx, precision, launch):
             mu_tot = ctx.dos_kpm_moments(dev(Aw), lb, ub, 70, n_v, seed=5, precision=precision,
                                          launch=launch)
             ref = okpm.kpm_moments_per_vector(Aw, lb, ub, 70, n_v, seed=5)
-            tol = TOL64 if precision == "f64" else tol32(70)
-            assert np.all(np.abs(pv - ref) <= tol)
-            assert np.all(np.abs(mu - ref.mean(axis=0)) <= tol)
-            assert np.all(np.abs(mu_tot - ref.mean(axis=0)) <= tol)
+            tol, tolt = (TOL64, TOL64) if precision == "f64" else (tol32(70, A.n),
+                                                                   tol32(70, A.n * n_v))
+            assert np.all(np.abs(pv - ref) <= tol), fp32_ratio(pv, ref)
+            assert np.all(np.abs(mu - ref.mean(axis=0)) <= tolt)
+            assert np.all(np.abs(mu_tot - ref.mean(axis=0)) <= tolt), fp32_ratio(mu_tot,
+                                                                                 ref.mean(0))
 
 
 def test_tma_gather_wait_timeout_is_reported(ctx):
@@ -310,7 +314,7 @@ def test_bounded_wait_timeout_is_reported_and_context_survives(ctx):
                              launch={"staged": 2})
     ref = okpm.kpm_moments(anderson_3d(10, 3.0, seed=2).astype(np.float32), -8.0, 8.0, 10, 16,
                            seed=1)
-    assert np.all(np.abs(ok - ref) <= tol32(10))
+    assert np.all(np.abs(ok - ref) <= tol32(10, 1000 * 16))
 
 
 def test_launch_shape_that_misses_columns_is_rejected(ctx):

@@ -206,6 +206,11 @@ def test_infer_any_batch_equals_forward(ctx):
     net.dos_mlp_infer(xd, out=yd)
     torch.cuda.synchronize()
     assert np.array_equal(yd.cpu().numpy(), y[:5000])
+    # FP64 rows of moments read in place (mu_1..mu_64 of rows of 65), host and device
+    mu = np.concatenate([np.ones((3000, 1)), rng.uniform(-1, 1, (3000, 64))], axis=1)
+    want = net.dos_mlp_forward(mu[:, 1:].astype(np.float32))
+    assert np.array_equal(net.dos_mlp_infer(mu, col0=1, max_rows=1000), want)
+    assert np.array_equal(net.dos_mlp_infer(torch.from_numpy(mu).cuda(), col0=1), want)
 
 
 def test_save_load_round_trip_is_bitwise(ctx, tmp_path):
