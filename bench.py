@@ -76,6 +76,10 @@ WORKLOADS = {
     # the learned moments-to-DOS network: instances (2/3 Anderson lattices, 1/3
     # Chung-Lu normalized Laplacians, n in [n_lo, n_hi]); the first held_out are
     # kept for scoring and for the timed serving step, the rest train the network
+    # the network alone: Adam training steps at the learned workload's batch and
+    # inference over a large batch, on random inputs (the tensor-core products)
+    "mlp": dict(kind="mlp", n_in=64, n_hidden=512, n_out=256, batch=512, infer_rows=65536,
+                desc="moments-to-DOS network 64-512-512-256, BF16 operands, FP32 accumulation"),
     "learned": dict(kind="learned", instances=20000, held_out=2000, n_lo=4096, n_hi=64000,
                     seed=5, n_v_in=4, M_in=64, n_v_ref=1024, M_ref=256, train_steps=20000,
                     batch=512, lr=1e-3, kpm_nv=(4, 16, 64, 256),
@@ -282,6 +286,8 @@ def run_reference(args):
         return run_reference_batched(args, w)
     if w["kind"] == "learned":
         return run_reference_learned(args, w)
+    if w["kind"] == "mlp":
+        return run_reference_mlp(args, w)
     if args.method != "kpm":
         return run_reference_method(args, w)
     from oracle import bounds as obounds
@@ -390,13 +396,51 @@ def run_reference_learned(args, w):
     return 0
 
 
+def run_reference_mlp(args, w):
+    """Reference arm of the network workload: the FP64 network reference (bfloat16
+    operands emulated) as it stands, one Adam step per step on the same batch size."""
+    from oracle import mlp as omlp
+    B = w["batch"]
+    rng = np.random.default_rng(5)
+    x = rng.uniform(-1, 1, (B, w["n_in"]))
+    t = rng.uniform(0, 1, (B, w["n_out"]))
+    p = omlp.init_params(w["n_in"], w["n_hidden"], w["n_out"], 3)
+    m = {k: np.zeros_like(a) for k, a in p.items()}
+    v = {k: np.zeros_like(a) for k, a in p.items()}
+    times = []
+    for i in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        _, g = omlp.loss_and_grads(p, x, t, bf16=True)
+        p, m, v = omlp.adam_step(p, g, m, v, i + 1, 1e-4)
+        if i >= args.warmup:
+            times.append(time.perf_counter() - t0)
+    dt = sum(times) / len(times)
+    value = B / dt
+    cores = os.cpu_count() or 1
+    line = {"metric": "training samples/sec (Adam steps of the moments-to-DOS network)",
+            "value": value, "unit": "samples/s", "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * dt, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": args.workload, "batch": B}, "impl": "reference",
+            "cpu_baseline": {"value": value, "unit": "samples/s", "cores": cores,
+                             "kind": "oracle",
+                             "sample": f"each step: one Adam step of batch {B}, FP64 network "
+                                       f"reference (NumPy)"},
+            "e2e": {"value": value, "unit": "samples/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
 def batched_sample(mats, M, n_v, step_s, cores):
     """Matrices of the 512-lattice batch for a bounded oracle sample: a spread of
     sizes (the smallest, the largest and evenly spaced indices), as many as fit
     in about step_s seconds at the full M and n_v."""
     from oracle import kpm as okpm
     sizes = np.array([m.n for m in mats])
-    order = [int(np.argmin(sizes)), int(np.argmax(sizes))] + list(range(0, len(mats), 37))
+    # the smallest, the largest, then every matrix in a fixed stride-37 order
+    order = [int(np.argmin(sizes)), int(np.argmax(sizes))] + \
+        [(37 * i) % len(mats) for i in range(len(mats))]
     picks, t_used = [], 0.0
     for b in order:
         if b in picks:
@@ -685,7 +729,7 @@ def run_learned(args, w, world, rank, local, device):
     test = learned.make_dataset(ctx, held_mats, seed_in, w["n_v_in"], w["M_in"], w["n_v_ref"],
                                 w["M_ref"], b0=0, keep_groups=True)
     train = learned.make_dataset(ctx, stream, seed_in, w["n_v_in"], w["M_in"], w["n_v_ref"],
-                                 w["M_ref"], b0=held)
+                                 w["M_ref"], b0=held, tune=True)
     gen_s = time.perf_counter() - t0
     torch.cuda.synchronize()
     t1 = time.perf_counter()
@@ -790,6 +834,99 @@ def run_learned(args, w, world, rank, local, device):
         print(json.dumps(line))
     ctx.close()
     return 0
+
+
+def run_mlp(args, w, world, rank, local, device):
+    """The network's tensor-core path on its own: a step is one Adam training step
+    on a batch (forward, L1 loss, backward, update: nine products), and inference
+    over infer_rows rows is timed alongside (three products per 8192-row slice),
+    which gives the products' throughput against the tensor-core peak."""
+    import torch
+
+    from paper_1308_5467_gb300 import dos
+    ctx = dos.Context(local)
+    n_in, nh, n_out, B = w["n_in"], w["n_hidden"], w["n_out"], w["batch"]
+    net = dos.MLP(ctx, n_in, nh, n_out, seed=3)
+    g = torch.Generator(device="cpu").manual_seed(5)
+    x = torch.rand((B, n_in), generator=g).to(device) * 2 - 1
+    t = torch.rand((B, n_out), generator=g).to(device)
+    R = w["infer_rows"]
+    xi = (torch.rand((R, n_in), generator=g) * 2 - 1).to(device)
+    yi = torch.empty((R, n_out), dtype=torch.float32, device=device)
+    flops_row = 2 * (n_in * nh + nh * nh + nh * n_out)     # forward products per row
+
+    def timed(fn, steps, warmup):
+        for _ in range(warmup):
+            fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(steps):
+            fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / steps
+
+    with ClockSampler(gpu_id_for(local)) as clk:
+        ms = timed(lambda: net.dos_mlp_train_step(x, t, 1e-4, want_loss=False), args.steps,
+                   args.warmup)
+        # one slice of R rows: the input staging kernel, the three products and the
+        # copy of the output into yi -- the products' rate is understated by the rest
+        ms_inf = timed(lambda: net.dos_mlp_infer(xi, out=yi, max_rows=R), max(3, args.steps // 2),
+                       1)
+    peaks, peak_kind = measured_peaks()
+    tflops = R * flops_row / (ms_inf * 1e-3) / 1e12
+    train_flops = 3 * B * flops_row       # forward + the two backward products per layer
+    # end to end: host inputs and targets copied in and the loss read back every step
+    xh, th = x.cpu().pin_memory(), t.cpu().pin_memory()
+    ms_e2e = timed(lambda: net.dos_mlp_train_step(xh.numpy(), th.numpy(), 1e-4), max(3, args.steps // 2), 1)
+    line = {
+        "metric": "training samples/sec (Adam steps of the moments-to-DOS network)",
+        "value": B / (ms * 1e-3), "unit": "samples/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "bf16 (FP32 accumulation)", "data": "synthetic",
+        "config": {"workload": "mlp", "desc": w["desc"], "batch": B, "infer_rows": R,
+                   "l2": "weights 0.9 MB stay in L2; inference inputs/outputs %d MB"
+                         % ((R * (n_in + n_out) * 4) >> 20)},
+        "train_tflops": train_flops / (ms * 1e-3) / 1e12,
+        "inference": {"rows": R, "ms": ms_inf, "rows_per_s": R / (ms_inf * 1e-3),
+                      "tflops": tflops},
+        "roofline": {"bound": "tensor", "achieved": tflops, "peak": peaks["bf16_tflops"],
+                     "unit": "TFLOP/s", "frac": tflops / peaks["bf16_tflops"], "traffic": None,
+                     "peak_source": f"{peak_kind} bf16 (cuBLAS burst)",
+                     "kernel": "gemm_tc_kernel (tcgen05.mma, inference products)",
+                     "flops_per_launch": R * flops_row / 3, "launch_ms": ms_inf / 3},
+        "e2e": {"value": B / (ms_e2e * 1e-3), "unit": "samples/s",
+                "h2d_bytes_per_step": B * (n_in + n_out) * 4, "d2h_bytes_per_step": 4,
+                "ms_per_step": ms_e2e},
+        "cpu_baseline": mlp_cpu_baseline(net, x.cpu().numpy(), t.cpu().numpy()),
+        "clocks": clk.summary(),
+    }
+    if rank == 0:
+        print(json.dumps(line))
+    net.close()
+    ctx.close()
+    return 0
+
+
+def mlp_cpu_baseline(net, x, t, target_s=8.0):
+    """The FP64 network reference (bfloat16 operands emulated) as it stands: loss,
+    gradients and an Adam update per step on the same batch, on the host."""
+    from oracle import mlp as omlp
+    p = omlp.unflatten(net.dos_mlp_get_params().astype(np.float64), net.n_in, net.n_hidden,
+                       net.n_out)
+    m = {k: np.zeros_like(v) for k, v in p.items()}
+    v = {k: np.zeros_like(a) for k, a in p.items()}
+    steps, t0 = 0, time.perf_counter()
+    while time.perf_counter() - t0 < target_s or steps < 1:
+        _, g = omlp.loss_and_grads(p, x.astype(np.float64), t.astype(np.float64), bf16=True)
+        p, m, v = omlp.adam_step(p, g, m, v, steps + 1, 1e-4)
+        steps += 1
+    dt = time.perf_counter() - t0
+    return {"value": steps * x.shape[0] / dt, "unit": "samples/s",
+            "cores": os.cpu_count() or 1, "kind": "oracle",
+            "sample": f"{steps} Adam steps of batch {x.shape[0]} with the FP64 network "
+                      f"reference (NumPy, bfloat16 operands emulated), {dt:.1f} s"}
 
 
 def learned_cpu_baseline(ctx, net, test, groups, w, seed_in, target_s=12.0):
@@ -1021,6 +1158,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-f64-form", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-reference-dos", action="store_true",
+                    help="skip the reference sweep of the smoothed error (profiling runs; e1 null)")
     ap.add_argument("--no-pdl", action="store_true",
                     help="plain stream order between sweep steps (no programmatic dependent launch)")
     ap.add_argument("--launch", default=None,
@@ -1052,6 +1191,8 @@ def main():
         return run_batched(args, w, world, rank, local, device)
     if w["kind"] == "learned":
         return run_learned(args, w, world, rank, local, device)
+    if w["kind"] == "mlp":
+        return run_mlp(args, w, world, rank, local, device)
     A = make_matrix(w)
     if w["kind"] == "chunglu":
         A = A.astype(np.float32)      # the graph's values are FP32 (both forms read them)
@@ -1085,8 +1226,8 @@ def main():
     # (another seed); FP32 on the graph, whose FP32 error (~1e-6 per moment) is far
     # below the stochastic error of 1024 vectors (~2e-5)
     ref_nv, ref_prec = w.get("ref_nv", 1024), w.get("ref_prec", "f64")
-    ref_mu = ctx.dos_kpm_moments(Ad if ref_prec == prec else Ad64, lb, ub, M, ref_nv,
-                                 seed=seed + 1000, precision=ref_prec)
+    ref_mu = None if args.no_reference_dos else ctx.dos_kpm_moments(
+        Ad if ref_prec == prec else Ad64, lb, ub, M, ref_nv, seed=seed + 1000, precision=ref_prec)
 
     sweep_flags = dos.DOS_OPT_NO_PDL if args.no_pdl else 0
 
@@ -1096,6 +1237,8 @@ def main():
                                  vec_offset=vec_offset, flags=sweep_flags,
                                  launch=fixed if precision == prec else None)
         phi = ctx.dos_reconstruct(mu, M, "jackson", lo, hi, N_t=1000)
+        if ref_mu is None:
+            return mu, phi, None, None
         e1, einf = ctx.dos_smoothed_error(mu, M, "jackson", lo, hi, sigma, ref_mu=ref_mu)
         return mu, phi, e1, einf
 

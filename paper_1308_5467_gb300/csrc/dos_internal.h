@@ -239,6 +239,25 @@ int reduce_blocks(int num_sms, int64_t n);
 void launch_reconstruct(const double *mu, int M, int damping, double lb, double ub,
                         const double *t, int N_t, double *coef_scratch, double *phi_hat,
                         double *phi_lambda, cudaStream_t s);
+// The learned network's tensor-core product (mlp_tc.cu): C = epilogue(A B^T) with
+// A (M x K) and B (N x K) bfloat16, K contiguous, leading dimensions multiples of 8.
+enum TcEpi { TC_EPI_BIAS_RELU_BF16 = 0, TC_EPI_BIAS_F32 = 1, TC_EPI_MASK = 2, TC_EPI_F32 = 3 };
+struct TcGemm {
+    int M, N, K, epi;
+    const float *bias;   // N: TC_EPI_BIAS_RELU_BF16 (relu(acc + b) in bf16), TC_EPI_BIAS_F32
+    const void *mask;    // bf16 M x N (ld ldm): TC_EPI_MASK keeps acc where mask > 0
+    int ldm;
+    float *Cf;           // FP32 output (ld ldc): TC_EPI_BIAS_F32, TC_EPI_MASK, TC_EPI_F32
+    void *Cb;            // bf16 output (ld ldc) or null
+    int ldc;
+    void *Ct;            // bf16 transposed output, N x M (ld ldt), or null
+    int ldt;
+    int *status;         // bit 8: a bounded wait ran out
+    long long spin;      // wait limit in SM clock cycles
+};
+void launch_gemm_tc(const TcGemm &g, const void *A, int lda, const void *B, int ldb,
+                    cudaStream_t s);
+
 // B rows of moments (row stride ldm) -> B x N_t phi_hat; coef_scratch: B (M+1) doubles
 void launch_reconstruct_rows(const double *mu, int64_t ldm, int B, int M, int damping,
                              const double *t, int N_t, double *coef_scratch, double *phi_hat,

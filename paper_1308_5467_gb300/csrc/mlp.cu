@@ -1,10 +1,13 @@
 // The learned part (not in the paper): a 3-layer perceptron from low-order
 // Chebyshev moments to a DOS on a grid, trained and run entirely by these
-// kernels.  Matrix products use the tensor cores through warp-level
-// mma.sync m16n8k16 (bfloat16 operands, FP32 accumulation) with fused
-// epilogues (bias + ReLU, ReLU-mask back-propagation); the loss, bias
-// gradients and Adam run in FP32.  All reductions have a fixed order, so a
-// training run is bitwise reproducible.
+// kernels.  The nine matrix products of a training step (three forward, six
+// backward) run on the fifth-generation tensor cores (mlp_tc.cu: TMA-fed
+// tcgen05.mma with the FP32 accumulator in tensor memory, bfloat16 operands)
+// with fused epilogues (bias + ReLU, ReLU-mask back-propagation).  Every product
+// is C = A B^T with both operands K-contiguous, so the kernels that produce an
+// operand also write the transposed copy the backward pass needs (activations,
+// output gradient, weights).  The loss, bias gradients and Adam run in FP32.
+// All reductions have a fixed order, so a training run is bitwise reproducible.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <math.h>
@@ -33,15 +36,20 @@ struct dos_mlp {
     Buffer state;          // params | grads | adam m | adam v (FP32), bf16 weight copies
     Buffer acts;           // per-batch activations
     Buffer in_stage;       // dos_mlp_infer: a host input slice copied to the device
+    Buffer flags;          // status word of the bounded waits of the tensor-core kernels
     int cap_B = 0;
     int64_t step = 0;
     float *params = nullptr, *grads = nullptr, *m = nullptr, *v = nullptr;
-    bf16 *wb = nullptr;    // W1 | W2 | W3 in bfloat16
-    // batch buffers (cap_B rows)
+    // bfloat16 weights with leading dimensions padded to 8 (tensor-map rows), and
+    // the transposes of W2 and W3 for the backward products
+    bf16 *W1b = nullptr, *W2b = nullptr, *W2t = nullptr, *W3b = nullptr, *W3t = nullptr;
+    int *status = nullptr;
+    // batch buffers (cap_B rows; bf16 operands with padded leading dimensions)
     float *xf = nullptr, *tf = nullptr, *y = nullptr, *dyf = nullptr, *dh2f = nullptr,
           *dh1f = nullptr, *loss_part = nullptr;
-    bf16 *xb = nullptr, *h1 = nullptr, *h2 = nullptr, *dyb = nullptr, *dh2b = nullptr,
-         *dh1b = nullptr;
+    bf16 *xb = nullptr, *xbt = nullptr, *h1 = nullptr, *h1t = nullptr, *h2 = nullptr,
+         *h2t = nullptr, *dyb = nullptr, *dybt = nullptr, *dh2b = nullptr, *dh2t = nullptr,
+         *dh1t = nullptr;
 };
 
 namespace {
@@ -75,146 +83,45 @@ __global__ void init_params_kernel(float *p, int64_t n, int64_t o0, int64_t s0, 
     }
 }
 
-__global__ void to_bf16_kernel(const float *__restrict__ in, bf16 *__restrict__ out, int64_t n) {
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
-         i += (int64_t)gridDim.x * blockDim.x)
-        out[i] = __float2bfloat16_rn(in[i]);
-}
+// Leading dimension of a bfloat16 operand with k contiguous elements per row:
+// rows of a tensor map must be multiples of 16 bytes.
+inline int pad8(int k) { return (k + 7) / 8 * 8; }
 
-// ---- tensor-core GEMM -------------------------------------------------------------
-// C(m, n) = sum_k A(m, k) * B(n, k), with A(m, k) = TA ? A[k*lda + m] : A[m*lda + k] and
-// B(n, k) = TB ? B[k*ldb + n] : B[n*ldb + k].  64x64 block tile, 32-deep k
-// slices staged in shared memory, 4 warps of 32x32, each as 2x4 m16n8k16 MMAs.
-enum Epi { EPI_BIAS_RELU_BF16 = 0, EPI_BIAS_F32 = 1, EPI_MASK = 2, EPI_F32 = 3 };
-
-__device__ __forceinline__ uint32_t ld_pair(const bf16 *p) {
-    return *reinterpret_cast<const uint32_t *>(p);
-}
-
-__device__ __forceinline__ void mma_bf16(float (&c)[4], const uint32_t (&a)[4],
-                                         const uint32_t (&b)[2]) {
-    asm volatile(
-        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 "
-        "{%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, {%0,%1,%2,%3};\n"
-        : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
-        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
-}
-
-template <bool TA, bool TB, int EPI>
-__global__ void __launch_bounds__(128) gemm_kernel(int M, int N, int K, const bf16 *__restrict__ A,
-                                                   int lda, const bf16 *__restrict__ B, int ldb,
-                                                   const float *__restrict__ bias,
-                                                   const bf16 *__restrict__ mask, int ldm,
-                                                   float *__restrict__ Cf, bf16 *__restrict__ Cb,
-                                                   int ldc) {
-    __shared__ __align__(16) bf16 As[64][40];
-    __shared__ __align__(16) bf16 Bs[64][40];
-    const int bm = blockIdx.y * 64, bn = blockIdx.x * 64;
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int wm = (warp >> 1) * 32, wn = (warp & 1) * 32;
-    const int g = lane >> 2, t = lane & 3;
-    const bf16 zero = __float2bfloat16_rn(0.f);
-    float acc[2][4][4];
-#pragma unroll
-    for (int i = 0; i < 2; ++i)
-#pragma unroll
-        for (int j = 0; j < 4; ++j)
-#pragma unroll
-            for (int e = 0; e < 4; ++e) acc[i][j][e] = 0.f;
-
-    for (int k0 = 0; k0 < K; k0 += 32) {
-        for (int idx = tid; idx < 64 * 32; idx += 128) {
-            int r, k;
-            if (TA) { r = idx & 63; k = idx >> 6; } else { k = idx & 31; r = idx >> 5; }
-            const int gm = bm + r, gk = k0 + k;
-            bf16 val = zero;
-            if (gm < M && gk < K) val = TA ? A[(size_t)gk * lda + gm] : A[(size_t)gm * lda + gk];
-            As[r][k] = val;
-        }
-        for (int idx = tid; idx < 64 * 32; idx += 128) {
-            int r, k;
-            if (TB) { r = idx & 63; k = idx >> 6; } else { k = idx & 31; r = idx >> 5; }
-            const int gn = bn + r, gk = k0 + k;
-            bf16 val = zero;
-            if (gn < N && gk < K) val = TB ? B[(size_t)gk * ldb + gn] : B[(size_t)gn * ldb + gk];
-            Bs[r][k] = val;
-        }
-        __syncthreads();
-#pragma unroll
-        for (int kk = 0; kk < 32; kk += 16) {
-            uint32_t a[2][4], b[4][2];
-#pragma unroll
-            for (int i = 0; i < 2; ++i) {
-                const int r = wm + i * 16;
-                a[i][0] = ld_pair(&As[r + g][kk + 2 * t]);
-                a[i][1] = ld_pair(&As[r + g + 8][kk + 2 * t]);
-                a[i][2] = ld_pair(&As[r + g][kk + 2 * t + 8]);
-                a[i][3] = ld_pair(&As[r + g + 8][kk + 2 * t + 8]);
-            }
-#pragma unroll
-            for (int j = 0; j < 4; ++j) {
-                const int c = wn + j * 8;
-                b[j][0] = ld_pair(&Bs[c + g][kk + 2 * t]);
-                b[j][1] = ld_pair(&Bs[c + g][kk + 2 * t + 8]);
-            }
-#pragma unroll
-            for (int i = 0; i < 2; ++i)
-#pragma unroll
-                for (int j = 0; j < 4; ++j) mma_bf16(acc[i][j], a[i], b[j]);
-        }
-        __syncthreads();
+// FP32 rows x cols matrix (contiguous) -> bf16 with leading dimension ld and,
+// when out_t is given, the transpose (cols x rows, leading dimension ld_t).
+__global__ void to_bf16_pad_kernel(const float *__restrict__ in, int rows, int cols,
+                                   bf16 *__restrict__ out, int ld, bf16 *__restrict__ out_t,
+                                   int ld_t) {
+    const int64_t total = (int64_t)rows * cols;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int r = (int)(e / cols), c = (int)(e - (int64_t)r * cols);
+        const bf16 h = __float2bfloat16_rn(in[e]);
+        out[(size_t)r * ld + c] = h;
+        if (out_t) out_t[(size_t)c * ld_t + r] = h;
     }
-#pragma unroll
-    for (int i = 0; i < 2; ++i)
-#pragma unroll
-        for (int j = 0; j < 4; ++j)
-#pragma unroll
-            for (int h = 0; h < 2; ++h)
-#pragma unroll
-                for (int e = 0; e < 2; ++e) {
-                    const int row = bm + wm + i * 16 + g + h * 8;
-                    const int col = bn + wn + j * 8 + 2 * t + e;
-                    if (row >= M || col >= N) continue;
-                    float v = acc[i][j][h * 2 + e];
-                    const size_t o = (size_t)row * ldc + col;
-                    if (EPI == EPI_BIAS_RELU_BF16) {
-                        v = fmaxf(v + bias[col], 0.f);
-                        Cb[o] = __float2bfloat16_rn(v);
-                    } else if (EPI == EPI_BIAS_F32) {
-                        Cf[o] = v + bias[col];
-                    } else if (EPI == EPI_MASK) {
-                        v = __bfloat162float(mask[(size_t)row * ldm + col]) > 0.f ? v : 0.f;
-                        Cf[o] = v;
-                        Cb[o] = __float2bfloat16_rn(v);
-                    } else {
-                        Cf[o] = v;
-                    }
-                }
-}
-
-template <bool TA, bool TB, int EPI>
-void gemm(int M, int N, int K, const bf16 *A, int lda, const bf16 *B, int ldb, const float *bias,
-          const bf16 *mask, int ldm, float *Cf, bf16 *Cb, int ldc, cudaStream_t s) {
-    dim3 grid((N + 63) / 64, (M + 63) / 64);
-    gemm_kernel<TA, TB, EPI><<<grid, 128, 0, s>>>(M, N, K, A, lda, B, ldb, bias, mask, ldm, Cf,
-                                                   Cb, ldc);
-    DOS_LAUNCHED();
 }
 
 // ---- loss, gradients, optimiser -----------------------------------------------------
-// dy = sign(y - target) / (B n_out) (FP32 and bfloat16); per-block sums of |y - target|.
+// dy = sign(y - target) / (B n_out): FP32 (for the bias gradient) and bfloat16, row-major
+// and transposed (operands of the two layer-3 products); per-block sums of |y - target|.
 __global__ void l1_loss_kernel(const float *__restrict__ y, const float *__restrict__ target,
-                               int64_t count, float scale, float *__restrict__ dyf,
-                               bf16 *__restrict__ dyb, float *__restrict__ part) {
+                               int B, int n_out, float scale, float *__restrict__ dyf,
+                               bf16 *__restrict__ dyb, int ldb, bf16 *__restrict__ dybt,
+                               int ldt, float *__restrict__ part) {
     __shared__ float sh[32];
     float s = 0.f;
+    const int64_t count = (int64_t)B * n_out;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < count;
          i += (int64_t)gridDim.x * blockDim.x) {
+        const int b = (int)(i / n_out), o = (int)(i - (int64_t)b * n_out);
         const float d = y[i] - target[i];
         s += fabsf(d);
         const float gsgn = d > 0.f ? scale : (d < 0.f ? -scale : 0.f);
         dyf[i] = gsgn;
-        dyb[i] = __float2bfloat16_rn(gsgn);
+        const bf16 h = __float2bfloat16_rn(gsgn);
+        dyb[(size_t)b * ldb + o] = h;
+        dybt[(size_t)o * ldt + b] = h;
     }
     for (int off = 16; off > 0; off >>= 1) s += __shfl_down_sync(0xffffffffu, s, off);
     if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = s;
@@ -246,9 +153,7 @@ __global__ void colsum_kernel(const float *__restrict__ D, int B, int N, int ld,
 
 __global__ void adam_kernel(float *__restrict__ p, const float *__restrict__ g,
                             float *__restrict__ m, float *__restrict__ v, int64_t n, float lr,
-                            float b1, float b2, float eps, float c1, float c2,
-                            bf16 *__restrict__ wb, int64_t o0, int64_t s0, int64_t o1,
-                            int64_t s1, int64_t o2, int64_t s2) {
+                            float b1, float b2, float eps, float c1, float c2) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x) {
         const float gi = g[i];
@@ -256,13 +161,7 @@ __global__ void adam_kernel(float *__restrict__ p, const float *__restrict__ g,
         const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
         m[i] = mi;
         v[i] = vi;
-        const float pi = p[i] - lr * (mi / c1) / (sqrtf(vi / c2) + eps);
-        p[i] = pi;
-        int64_t w = -1;
-        if (i >= o0 && i < o0 + s0) w = i - o0;
-        else if (i >= o1 && i < o1 + s1) w = s0 + (i - o1);
-        else if (i >= o2 && i < o2 + s2) w = s0 + s1 + (i - o2);
-        if (w >= 0) wb[w] = __float2bfloat16_rn(pi);
+        p[i] = p[i] - lr * (mi / c1) / (sqrtf(vi / c2) + eps);
     }
 }
 
@@ -295,44 +194,80 @@ int mguard(dos_mlp *mlp, F &&f) {
 }
 
 void refresh_bf16_weights(dos_mlp *mlp, cudaStream_t s) {
-    to_bf16_kernel<<<grid1(mlp->wsz[0]), 256, 0, s>>>(mlp->params + mlp->off[0], mlp->wb,
-                                                      mlp->wsz[0]);
+    const int nh = mlp->nh, n_in = mlp->n_in, n_out = mlp->n_out;
+    to_bf16_pad_kernel<<<grid1(mlp->wsz[0]), 256, 0, s>>>(mlp->params + mlp->off[0], nh, n_in,
+                                                          mlp->W1b, pad8(n_in), nullptr, 0);
     DOS_LAUNCHED();
-    to_bf16_kernel<<<grid1(mlp->wsz[1]), 256, 0, s>>>(mlp->params + mlp->off[2],
-                                                      mlp->wb + mlp->wsz[0], mlp->wsz[1]);
+    to_bf16_pad_kernel<<<grid1(mlp->wsz[1]), 256, 0, s>>>(mlp->params + mlp->off[2], nh, nh,
+                                                          mlp->W2b, pad8(nh), mlp->W2t, pad8(nh));
     DOS_LAUNCHED();
-    to_bf16_kernel<<<grid1(mlp->wsz[2]), 256, 0, s>>>(mlp->params + mlp->off[4],
-                                                      mlp->wb + mlp->wsz[0] + mlp->wsz[1],
-                                                      mlp->wsz[2]);
+    to_bf16_pad_kernel<<<grid1(mlp->wsz[2]), 256, 0, s>>>(mlp->params + mlp->off[4], n_out, nh,
+                                                          mlp->W3b, pad8(nh), mlp->W3t,
+                                                          pad8(n_out));
     DOS_LAUNCHED();
 }
+
+// Bump allocator over one device buffer; every piece 256-byte aligned (TMA needs 16).
+struct Carve {
+    uint8_t *p;
+    template <typename T>
+    T *take(size_t count) {
+        T *r = (T *)p;
+        p += (count * sizeof(T) + 255) / 256 * 256;
+        return r;
+    }
+};
 
 void ensure_batch(dos_mlp *mlp, int B) {
     if (B <= mlp->cap_B) return;
-    const size_t nb = (size_t)B;
-    const size_t f32 = nb * (mlp->n_in + 3 * (size_t)mlp->n_out + 2 * (size_t)mlp->nh) +
-                       kLossBlocks + 1;
-    const size_t b16 = nb * ((size_t)mlp->n_in + 4 * (size_t)mlp->nh + mlp->n_out);
-    uint8_t *base = (uint8_t *)mlp->acts.get(f32 * 4 + b16 * 2 + 64);
-    float *f = (float *)base;
-    mlp->xf = f; f += nb * mlp->n_in;
-    mlp->tf = f; f += nb * mlp->n_out;
-    mlp->y = f; f += nb * mlp->n_out;
-    mlp->dyf = f; f += nb * mlp->n_out;
-    mlp->dh2f = f; f += nb * mlp->nh;
-    mlp->dh1f = f; f += nb * mlp->nh;
-    mlp->loss_part = f; f += kLossBlocks + 1;
-    bf16 *h = (bf16 *)(((uintptr_t)f + 15) & ~uintptr_t(15));
-    mlp->xb = h; h += nb * mlp->n_in;
-    mlp->h1 = h; h += nb * mlp->nh;
-    mlp->h2 = h; h += nb * mlp->nh;
-    mlp->dyb = h; h += nb * mlp->n_out;
-    mlp->dh2b = h; h += nb * mlp->nh;
-    mlp->dh1b = h;
+    const size_t nb = (size_t)B, pb = (size_t)pad8(B);
+    const size_t ni = mlp->n_in, nh = mlp->nh, no = mlp->n_out;
+    const size_t pi = pad8(mlp->n_in), ph = pad8(mlp->nh), po = pad8(mlp->n_out);
+    const size_t f32 = nb * (ni + 3 * no + 2 * ph) + kLossBlocks + 1;
+    const size_t b16 = nb * (pi + 2 * ph + po + ph) + pb * (ni + 2 * nh + no + 2 * nh);
+    Carve c{(uint8_t *)mlp->acts.get(f32 * 4 + b16 * 2 + 20 * 256)};
+    mlp->xf = c.take<float>(nb * ni);
+    mlp->tf = c.take<float>(nb * no);
+    mlp->y = c.take<float>(nb * no);
+    mlp->dyf = c.take<float>(nb * no);
+    mlp->dh2f = c.take<float>(nb * ph);
+    mlp->dh1f = c.take<float>(nb * ph);
+    mlp->loss_part = c.take<float>(kLossBlocks + 1);
+    mlp->xb = c.take<bf16>(nb * pi);
+    mlp->h1 = c.take<bf16>(nb * ph);
+    mlp->h2 = c.take<bf16>(nb * ph);
+    mlp->dyb = c.take<bf16>(nb * po);
+    mlp->dh2b = c.take<bf16>(nb * ph);
+    mlp->xbt = c.take<bf16>(ni * pb);
+    mlp->h1t = c.take<bf16>(nh * pb);
+    mlp->h2t = c.take<bf16>(nh * pb);
+    mlp->dybt = c.take<bf16>(no * pb);
+    mlp->dh2t = c.take<bf16>(nh * pb);
+    mlp->dh1t = c.take<bf16>(nh * pb);
     mlp->cap_B = B;
 }
 
-void stage_input(dos_mlp *mlp, const float *x, int B, const float *target, cudaStream_t s) {
+// Input rows of any stride and element type to the bfloat16 operand (leading
+// dimension ld), through FP32 (the type of the network's input):
+// xb[r, j] = bf16(float(x[r * ldx + j])); with xbt, also the transpose.
+template <typename T>
+__global__ void stage_rows_kernel(const T *__restrict__ x, int64_t ldx, int n_in, int B,
+                                  bf16 *__restrict__ xb, int ld, bf16 *__restrict__ xbt,
+                                  int ldt) {
+    const int64_t total = (int64_t)B * n_in;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t r = e / n_in;
+        const int j = (int)(e - r * n_in);
+        const bf16 h = __float2bfloat16_rn((float)x[r * ldx + j]);
+        xb[r * ld + j] = h;
+        if (xbt) xbt[(size_t)j * ldt + r] = h;
+    }
+}
+
+// Training-batch input: x (B x n_in FP32, host or device) and optional target.
+void stage_input(dos_mlp *mlp, const float *x, int B, const float *target, bool train,
+                 cudaStream_t s) {
     DOS_REQUIRE(x != nullptr, "x is NULL");
     DOS_REQUIRE(B >= 1 && B <= 65536, "B must be in [1, 65536]");
     ensure_batch(mlp, B);
@@ -340,71 +275,113 @@ void stage_input(dos_mlp *mlp, const float *x, int B, const float *target, cudaS
     if (target)
         DOS_CUDA_TRY(cudaMemcpyAsync(mlp->tf, target, (size_t)B * mlp->n_out * 4,
                                      cudaMemcpyDefault, s));
-    to_bf16_kernel<<<grid1((int64_t)B * mlp->n_in), 256, 0, s>>>(mlp->xf, mlp->xb,
-                                                                 (int64_t)B * mlp->n_in);
+    stage_rows_kernel<float><<<grid1((int64_t)B * mlp->n_in), 256, 0, s>>>(
+        mlp->xf, mlp->n_in, mlp->n_in, B, mlp->xb, pad8(mlp->n_in), train ? mlp->xbt : nullptr,
+        pad8(B));
     DOS_LAUNCHED();
 }
 
-// Input rows of any stride and element type to the bfloat16 operand, through
-// FP32 (the type of the network's input): xb[r, j] = bf16(float(x[r * ldx + j])).
-template <typename T>
-__global__ void stage_rows_kernel(const T *__restrict__ x, int64_t ldx, int n_in, int B,
-                                  bf16 *__restrict__ xb) {
-    const int64_t total = (int64_t)B * n_in;
-    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
-         e += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t r = e / n_in;
-        const int j = (int)(e - r * n_in);
-        xb[e] = __float2bfloat16_rn((float)x[r * ldx + j]);
-    }
+constexpr long long kSpinCycles = 4000000000LL;  // about two seconds at 2 GHz
+
+TcGemm tc(dos_mlp *mlp, int M, int N, int K, int epi) {
+    TcGemm g{};
+    g.M = M;
+    g.N = N;
+    g.K = K;
+    g.epi = epi;
+    g.status = mlp->status;
+    g.spin = kSpinCycles;
+    return g;
 }
 
-void forward(dos_mlp *mlp, int B, cudaStream_t s) {
-    const bf16 *W1 = mlp->wb, *W2 = mlp->wb + mlp->wsz[0], *W3 = W2 + mlp->wsz[1];
+// With train, the products also write the transposed activations the backward
+// products read.
+void forward(dos_mlp *mlp, int B, bool train, cudaStream_t s) {
     const float *p = mlp->params;
-    gemm<false, false, EPI_BIAS_RELU_BF16>(B, mlp->nh, mlp->n_in, mlp->xb, mlp->n_in, W1,
-                                           mlp->n_in, p + mlp->off[1], nullptr, 0, nullptr,
-                                           mlp->h1, mlp->nh, s);
-    gemm<false, false, EPI_BIAS_RELU_BF16>(B, mlp->nh, mlp->nh, mlp->h1, mlp->nh, W2, mlp->nh,
-                                           p + mlp->off[3], nullptr, 0, nullptr, mlp->h2,
-                                           mlp->nh, s);
-    gemm<false, false, EPI_BIAS_F32>(B, mlp->n_out, mlp->nh, mlp->h2, mlp->nh, W3, mlp->nh,
-                                     p + mlp->off[5], nullptr, 0, mlp->y, nullptr, mlp->n_out, s);
+    const int pi = pad8(mlp->n_in), ph = pad8(mlp->nh), pb = pad8(B);
+    TcGemm g = tc(mlp, B, mlp->nh, mlp->n_in, TC_EPI_BIAS_RELU_BF16);
+    g.bias = p + mlp->off[1];
+    g.Cb = mlp->h1;
+    g.ldc = ph;
+    g.Ct = train ? mlp->h1t : nullptr;
+    g.ldt = pb;
+    launch_gemm_tc(g, mlp->xb, pi, mlp->W1b, pi, s);
+    g = tc(mlp, B, mlp->nh, mlp->nh, TC_EPI_BIAS_RELU_BF16);
+    g.bias = p + mlp->off[3];
+    g.Cb = mlp->h2;
+    g.ldc = ph;
+    g.Ct = train ? mlp->h2t : nullptr;
+    g.ldt = pb;
+    launch_gemm_tc(g, mlp->h1, ph, mlp->W2b, ph, s);
+    g = tc(mlp, B, mlp->n_out, mlp->nh, TC_EPI_BIAS_F32);
+    g.bias = p + mlp->off[5];
+    g.Cf = mlp->y;
+    g.ldc = mlp->n_out;
+    launch_gemm_tc(g, mlp->h2, ph, mlp->W3b, ph, s);
 }
 
 // loss into loss_part[kLossBlocks], gradients into mlp->grads
 void loss_backward(dos_mlp *mlp, int B, cudaStream_t s) {
     const int64_t cnt = (int64_t)B * mlp->n_out;
     const float scale = (float)(1.0 / (double)cnt);
-    l1_loss_kernel<<<kLossBlocks, 256, 0, s>>>(mlp->y, mlp->tf, cnt, scale, mlp->dyf, mlp->dyb,
-                                               mlp->loss_part);
+    const int H = mlp->nh, pb = pad8(B), ph = pad8(H), po = pad8(mlp->n_out);
+    l1_loss_kernel<<<kLossBlocks, 256, 0, s>>>(mlp->y, mlp->tf, B, mlp->n_out, scale, mlp->dyf,
+                                               mlp->dyb, po, mlp->dybt, pb, mlp->loss_part);
     DOS_LAUNCHED();
     loss_final_kernel<<<1, 32, 0, s>>>(mlp->loss_part, kLossBlocks, scale,
                                        mlp->loss_part + kLossBlocks);
     DOS_LAUNCHED();
-    const bf16 *W2 = mlp->wb + mlp->wsz[0], *W3 = W2 + mlp->wsz[1];
-    float *g = mlp->grads;
-    const int H = mlp->nh;
+    float *gr = mlp->grads;
     // layer 3: dW3 = dy^T h2, db3 = sum dy, dh2 = (dy W3) * [h2 > 0]
-    gemm<true, true, EPI_F32>(mlp->n_out, H, B, mlp->dyb, mlp->n_out, mlp->h2, H, nullptr,
-                              nullptr, 0, g + mlp->off[4], nullptr, H, s);
+    TcGemm g = tc(mlp, mlp->n_out, H, B, TC_EPI_F32);
+    g.Cf = gr + mlp->off[4];
+    g.ldc = H;
+    launch_gemm_tc(g, mlp->dybt, pb, mlp->h2t, pb, s);
     colsum_kernel<<<(mlp->n_out + 255) / 256, 256, 0, s>>>(mlp->dyf, B, mlp->n_out, mlp->n_out,
-                                                            g + mlp->off[5]);
+                                                            gr + mlp->off[5]);
     DOS_LAUNCHED();
-    gemm<false, true, EPI_MASK>(B, H, mlp->n_out, mlp->dyb, mlp->n_out, W3, H, nullptr, mlp->h2,
-                                H, mlp->dh2f, mlp->dh2b, H, s);
-    // layer 2
-    gemm<true, true, EPI_F32>(H, H, B, mlp->dh2b, H, mlp->h1, H, nullptr, nullptr, 0,
-                              g + mlp->off[2], nullptr, H, s);
-    colsum_kernel<<<(H + 255) / 256, 256, 0, s>>>(mlp->dh2f, B, H, H, g + mlp->off[3]);
+    g = tc(mlp, B, H, mlp->n_out, TC_EPI_MASK);
+    g.mask = mlp->h2;
+    g.ldm = ph;
+    g.Cf = mlp->dh2f;
+    g.Cb = mlp->dh2b;
+    g.ldc = ph;
+    g.Ct = mlp->dh2t;
+    g.ldt = pb;
+    launch_gemm_tc(g, mlp->dyb, po, mlp->W3t, po, s);
+    // layer 2: dW2 = dh2^T h1, db2 = sum dh2, dh1 = (dh2 W2) * [h1 > 0]
+    g = tc(mlp, H, H, B, TC_EPI_F32);
+    g.Cf = gr + mlp->off[2];
+    g.ldc = H;
+    launch_gemm_tc(g, mlp->dh2t, pb, mlp->h1t, pb, s);
+    colsum_kernel<<<(H + 255) / 256, 256, 0, s>>>(mlp->dh2f, B, H, ph, gr + mlp->off[3]);
     DOS_LAUNCHED();
-    gemm<false, true, EPI_MASK>(B, H, H, mlp->dh2b, H, W2, H, nullptr, mlp->h1, H, mlp->dh1f,
-                                mlp->dh1b, H, s);
-    // layer 1
-    gemm<true, true, EPI_F32>(H, mlp->n_in, B, mlp->dh1b, H, mlp->xb, mlp->n_in, nullptr,
-                              nullptr, 0, g + mlp->off[0], nullptr, mlp->n_in, s);
-    colsum_kernel<<<(H + 255) / 256, 256, 0, s>>>(mlp->dh1f, B, H, H, g + mlp->off[1]);
+    g = tc(mlp, B, H, H, TC_EPI_MASK);
+    g.mask = mlp->h1;
+    g.ldm = ph;
+    g.Cf = mlp->dh1f;
+    g.ldc = ph;
+    g.Ct = mlp->dh1t;
+    g.ldt = pb;
+    launch_gemm_tc(g, mlp->dh2b, ph, mlp->W2t, ph, s);
+    // layer 1: dW1 = dh1^T x, db1 = sum dh1
+    g = tc(mlp, H, mlp->n_in, B, TC_EPI_F32);
+    g.Cf = gr + mlp->off[0];
+    g.ldc = mlp->n_in;
+    launch_gemm_tc(g, mlp->dh1t, pb, mlp->xbt, pb, s);
+    colsum_kernel<<<(H + 255) / 256, 256, 0, s>>>(mlp->dh1f, B, H, ph, gr + mlp->off[1]);
     DOS_LAUNCHED();
+}
+
+// The tensor-core products' bounded waits (status bit 8): read after a sync.
+void check_status(dos_mlp *mlp, cudaStream_t s) {
+    int h = 0;
+    DOS_CUDA_TRY(cudaMemcpyAsync(&h, mlp->status, sizeof(int), cudaMemcpyDeviceToHost, s));
+    DOS_CUDA_TRY(cudaStreamSynchronize(s));
+    if (h & 8) {
+        DOS_CUDA_TRY(cudaMemsetAsync(mlp->status, 0, sizeof(int), s));
+        throw Error{DOS_ETIMEOUT, "a bounded wait of the tensor-core product ran out"};
+    }
 }
 
 bool is_host_ptr(const void *p) {
@@ -480,13 +457,21 @@ int dos_mlp_create(dos_ctx *ctx, int n_in, int n_hidden, int n_out, uint64_t see
     mlp->n_params = o;
     int rc = mguard(mlp, [&] {
         const int64_t np = mlp->n_params;
-        const int64_t nw = mlp->wsz[0] + mlp->wsz[1] + mlp->wsz[2];
-        uint8_t *base = (uint8_t *)mlp->state.get(np * 16 + nw * 2 + 64);
-        mlp->params = (float *)base;
+        const size_t pi = pad8(n_in), ph = pad8(n_hidden), po = pad8(n_out);
+        const size_t nwb = (size_t)n_hidden * pi + 2 * (size_t)n_hidden * ph +
+                           (size_t)n_out * ph + (size_t)n_hidden * po;
+        Carve c{(uint8_t *)mlp->state.get(np * 16 + nwb * 2 + 8 * 256)};
+        mlp->params = c.take<float>(4 * np);  // params | grads | m | v, adjacent
         mlp->grads = mlp->params + np;
         mlp->m = mlp->grads + np;
         mlp->v = mlp->m + np;
-        mlp->wb = (bf16 *)(((uintptr_t)(mlp->v + np) + 15) & ~uintptr_t(15));
+        mlp->W1b = c.take<bf16>((size_t)n_hidden * pi);
+        mlp->W2b = c.take<bf16>((size_t)n_hidden * ph);
+        mlp->W2t = c.take<bf16>((size_t)n_hidden * ph);
+        mlp->W3b = c.take<bf16>((size_t)n_out * ph);
+        mlp->W3t = c.take<bf16>((size_t)n_hidden * po);
+        mlp->status = (int *)mlp->flags.get(sizeof(int));
+        DOS_CUDA_TRY(cudaMemset(mlp->status, 0, sizeof(int)));
         DOS_CUDA_TRY(cudaMemset(mlp->grads, 0, 3 * np * sizeof(float)));
         init_params_kernel<<<grid1(np), 256>>>(mlp->params, np, mlp->off[0], mlp->wsz[0], n_in,
                                                mlp->off[2], mlp->wsz[1], n_hidden, mlp->off[4],
@@ -497,6 +482,7 @@ int dos_mlp_create(dos_ctx *ctx, int n_in, int n_hidden, int n_out, uint64_t see
     });
     if (rc != DOS_OK) {
         mlp->state.release();
+        mlp->flags.release();
         delete mlp;
         return rc;
     }
@@ -513,6 +499,7 @@ int dos_mlp_destroy(dos_mlp *mlp) {
     mlp->state.release();
     mlp->acts.release();
     mlp->in_stage.release();
+    mlp->flags.release();
     if (prev >= 0) cudaSetDevice(prev);
     cudaGetLastError();
     delete mlp;
@@ -542,7 +529,7 @@ int dos_mlp_get_params(dos_mlp *mlp, float *params, void *stream) {
         DOS_REQUIRE(params != nullptr, "params is NULL");
         cudaStream_t s = (cudaStream_t)stream;
         DOS_CUDA_TRY(cudaMemcpyAsync(params, mlp->params, mlp->n_params * 4, cudaMemcpyDefault, s));
-        DOS_CUDA_TRY(cudaStreamSynchronize(s));
+        check_status(mlp, s);
     });
 }
 
@@ -550,13 +537,10 @@ int dos_mlp_forward(dos_mlp *mlp, const float *x, int B, float *y, void *stream)
     return mguard(mlp, [&] {
         DOS_REQUIRE(y != nullptr, "y is NULL");
         cudaStream_t s = (cudaStream_t)stream;
-        stage_input(mlp, x, B, nullptr, s);
-        forward(mlp, B, s);
+        stage_input(mlp, x, B, nullptr, false, s);
+        forward(mlp, B, false, s);
         DOS_CUDA_TRY(cudaMemcpyAsync(y, mlp->y, (size_t)B * mlp->n_out * 4, cudaMemcpyDefault, s));
-        cudaPointerAttributes at;
-        if (cudaPointerGetAttributes(&at, y) != cudaSuccess) cudaGetLastError();
-        else if (at.type != cudaMemoryTypeDevice && at.type != cudaMemoryTypeManaged)
-            DOS_CUDA_TRY(cudaStreamSynchronize(s));
+        if (is_host_ptr(y)) check_status(mlp, s);
     });
 }
 
@@ -583,20 +567,22 @@ int dos_mlp_infer(dos_mlp *mlp, const void *x, int x_dtype, int64_t ldx, int64_t
                 DOS_CUDA_TRY(cudaMemcpyAsync(d, src, bytes, cudaMemcpyHostToDevice, s));
                 src = (const uint8_t *)d;
             }
+            const int pi = pad8(mlp->n_in);
             if (x_dtype == DOS_F64)
                 stage_rows_kernel<double><<<grid1((int64_t)b * mlp->n_in), 256, 0, s>>>(
-                    (const double *)src, ldx, mlp->n_in, b, mlp->xb);
+                    (const double *)src, ldx, mlp->n_in, b, mlp->xb, pi, nullptr, 0);
             else
                 stage_rows_kernel<float><<<grid1((int64_t)b * mlp->n_in), 256, 0, s>>>(
-                    (const float *)src, ldx, mlp->n_in, b, mlp->xb);
+                    (const float *)src, ldx, mlp->n_in, b, mlp->xb, pi, nullptr, 0);
             DOS_LAUNCHED();
-            forward(mlp, b, s);
+            forward(mlp, b, false, s);
             DOS_CUDA_TRY(cudaMemcpyAsync(y + r0 * mlp->n_out, mlp->y,
                                          (size_t)b * mlp->n_out * 4, cudaMemcpyDefault, s));
             // the next slice overwrites the staging and activation buffers: with a host
             // output the copy above must finish first (stream order covers device ones)
             if (x_host || is_host_ptr(y)) DOS_CUDA_TRY(cudaStreamSynchronize(s));
         }
+        if (x_host || is_host_ptr(y)) check_status(mlp, s);
     });
 }
 
@@ -705,14 +691,14 @@ int dos_mlp_loss_grad(dos_mlp *mlp, const float *x, const float *target, int B, 
     return mguard(mlp, [&] {
         DOS_REQUIRE(target != nullptr, "target is NULL");
         cudaStream_t s = (cudaStream_t)stream;
-        stage_input(mlp, x, B, target, s);
-        forward(mlp, B, s);
+        stage_input(mlp, x, B, target, true, s);
+        forward(mlp, B, true, s);
         loss_backward(mlp, B, s);
         if (grads)
             DOS_CUDA_TRY(cudaMemcpyAsync(grads, mlp->grads, mlp->n_params * 4, cudaMemcpyDefault, s));
         float h = 0.f;
         DOS_CUDA_TRY(cudaMemcpyAsync(&h, mlp->loss_part + kLossBlocks, 4, cudaMemcpyDeviceToHost, s));
-        DOS_CUDA_TRY(cudaStreamSynchronize(s));
+        check_status(mlp, s);
         if (loss) *loss = h;
     });
 }
@@ -723,8 +709,8 @@ int dos_mlp_train_step(dos_mlp *mlp, const float *x, const float *target, int B,
         DOS_REQUIRE(target != nullptr, "target is NULL");
         DOS_REQUIRE(isfinite(lr) && lr > 0.f, "lr must be > 0");
         cudaStream_t s = (cudaStream_t)stream;
-        stage_input(mlp, x, B, target, s);
-        forward(mlp, B, s);
+        stage_input(mlp, x, B, target, true, s);
+        forward(mlp, B, true, s);
         loss_backward(mlp, B, s);
         mlp->step += 1;
         const double b1 = 0.9, b2 = 0.999;
@@ -732,14 +718,14 @@ int dos_mlp_train_step(dos_mlp *mlp, const float *x, const float *target, int B,
         const float c2 = (float)(1.0 - pow(b2, (double)mlp->step));
         adam_kernel<<<grid1(mlp->n_params), 256, 0, s>>>(
             mlp->params, mlp->grads, mlp->m, mlp->v, mlp->n_params, lr, (float)b1, (float)b2,
-            1e-8f, c1, c2, mlp->wb, mlp->off[0], mlp->wsz[0], mlp->off[2], mlp->wsz[1],
-            mlp->off[4], mlp->wsz[2]);
+            1e-8f, c1, c2);
         DOS_LAUNCHED();
+        refresh_bf16_weights(mlp, s);
         if (loss) {
             float h = 0.f;
             DOS_CUDA_TRY(cudaMemcpyAsync(&h, mlp->loss_part + kLossBlocks, 4,
                                          cudaMemcpyDeviceToHost, s));
-            DOS_CUDA_TRY(cudaStreamSynchronize(s));
+            check_status(mlp, s);
             *loss = h;
         }
     });

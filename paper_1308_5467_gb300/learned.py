@@ -104,16 +104,19 @@ def make_groups(ctx, mats, b0: int = 0, group_rows: int = 4_000_000, group_max: 
 
 def make_dataset(ctx: dos.Context, mats, seed: int, n_v_in: int = 4, M_in: int = N_IN,
                  n_v_ref: int = 1024, M_ref: int = 256, n_out: int = N_OUT, b0: int = 0,
-                 group_rows: int = 4_000_000, keep_groups: bool = False):
+                 group_rows: int = 4_000_000, keep_groups: bool = False, tune: bool = False):
     """Features, targets and the data needed to score them, for each matrix of the
     iterable `mats` (built lazily, e.g. by synthetic.instances.stream_instances).
 
     Returns dict with x (count, M_in) float32, y (count, n_out) float32, mu_in
     (count, M_in+1), mu_ref (count, M_ref+1), lb, ub (count,), laplacian (count,),
     n (count,), timing {"host_wait_s", "gpu_s", "moments"} and, with keep_groups,
-    the device Groups (for timing and further sweeps)."""
+    the device Groups (for timing and further sweeps).  With tune, the launch
+    shapes of both sweeps are autotuned on the first group and kept for the rest
+    (groups differ only in the instances they hold)."""
     import torch
     xs, ys, mus, refs, lbs, ubs, laps, ns, groups = [], [], [], [], [], [], [], [], []
+    shapes = None
     gpu_s, host_s, units = 0.0, 0.0, 0.0
     it = iter(make_groups(ctx, mats, b0, group_rows))
     while True:
@@ -122,12 +125,19 @@ def make_dataset(ctx: dos.Context, mats, seed: int, n_v_in: int = 4, M_in: int =
         host_s += time.perf_counter() - t0
         if g is None:
             break
+        if tune and shapes is None:
+            shapes = (ctx.dos_tune(g.A, n_v_in, "f32", seg_rows=g.seg)[0],
+                      ctx.dos_tune(g.A, n_v_ref, "f32", seg_rows=g.seg)[0])
+            for sh in shapes:
+                sh.pop("tiles")          # sized per group from its occupancy
         torch.cuda.synchronize()
         t1 = time.perf_counter()
         mu = ctx.dos_kpm_moments_batched(g.A, g.seg, g.lb, g.ub, M_in, n_v_in, seed=seed,
-                                         precision="f32", batch_index=g.b0)
+                                         precision="f32", batch_index=g.b0,
+                                         launch=shapes[0] if shapes else None)
         ref = ctx.dos_kpm_moments_batched(g.A, g.seg, g.lb, g.ub, M_ref, n_v_ref,
-                                          seed=seed + 7919, precision="f32", batch_index=g.b0)
+                                          seed=seed + 7919, precision="f32", batch_index=g.b0,
+                                          launch=shapes[1] if shapes else None)
         y = ctx.dos_reconstruct_batched(ref, "jackson", N_t=n_out)
         torch.cuda.synchronize()
         gpu_s += time.perf_counter() - t1
@@ -145,7 +155,8 @@ def make_dataset(ctx: dos.Context, mats, seed: int, n_v_in: int = 4, M_in: int =
     out = {"x": np.concatenate(xs), "y": np.concatenate(ys), "mu_in": np.concatenate(mus),
            "mu_ref": np.concatenate(refs), "lb": np.concatenate(lbs), "ub": np.concatenate(ubs),
            "laplacian": np.concatenate(laps), "n": np.concatenate(ns),
-           "timing": {"host_wait_s": host_s, "gpu_s": gpu_s, "moments": units}}
+           "timing": {"host_wait_s": host_s, "gpu_s": gpu_s, "moments": units},
+           "shapes": shapes}
     if keep_groups:
         out["groups"] = groups
     return out

@@ -83,6 +83,7 @@ def test_long_runs_with_ghost_copies(ctx):
                  merged=int(np.sum(weight == 0.0)),
                  theta_desc=float(min(np.diff(theta[l]).min() for l in range(n_v))),
                  dos_rel=float(np.abs(phi - ref).max() / np.abs(ref).max()))
+    print("ghost-run figures:", stats)
     # nodes whose true weight is ~0 come out within ~1e-11 of it (either sign)
     ok = (np.all(m_used == M) and stats["w_min"] > -1e-10 and stats["sum_err"] < 1e-10
           and stats["merged"] > 0 and stats["theta_desc"] >= -1e-12 and stats["dos_rel"] < 1e-9)
