@@ -84,8 +84,14 @@ def test_long_runs_with_ghost_copies(ctx):
                  theta_desc=float(min(np.diff(theta[l]).min() for l in range(n_v))),
                  dos_rel=float(np.abs(phi - ref).max() / np.abs(ref).max()))
     print("ghost-run figures:", stats)
-    # nodes whose true weight is ~0 come out within ~1e-11 of it (either sign)
-    ok = (np.all(m_used == M) and stats["w_min"] > -1e-10 and stats["sum_err"] < 1e-10
+    # Each weight is the residue of e_1^T (zI - T)^-1 e_1 by a contour integral of the
+    # M-step continued fraction, whose FP64 evaluation carries a relative error of
+    # about M u (u = 2^-53); so a weight is off by at most ~M u in absolute terms
+    # (weights are <= 1) -- nodes whose true weight is ~0 can come out slightly
+    # negative -- and the M weights of a run sum to one within ~M^2 u = 1e-11 at
+    # M = 300.  Bounds: w >= -M^2 u (-1e-11) and |sum - 1| <= 3 M^2 u (3e-11);
+    # measured -2.6e-12 and 8.2e-12.
+    ok = (np.all(m_used == M) and stats["w_min"] > -1e-11 and stats["sum_err"] < 3e-11
           and stats["merged"] > 0 and stats["theta_desc"] >= -1e-12 and stats["dos_rel"] < 1e-9)
     assert ok, stats
 
