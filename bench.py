@@ -116,7 +116,8 @@ def step_kernel_name(shape, precision):
     1 direct loads, 2 TMA row panels, 3 TMA gathers; 0 / absent: direct)."""
     t = "double" if precision == "f64" else "float"
     staged = (shape or {}).get("staged", 1)
-    base = {2: "step_staged_kernel", 3: "step_tmag_kernel"}.get(staged, "step_kernel")
+    base = {2: "step_staged_kernel", 3: "step_tmag_kernel",
+            4: "step_csrs_kernel"}.get(staged, "step_kernel")
     return f"{base}<{t}>"
 
 
@@ -125,6 +126,21 @@ def algorithmic_bytes_per_step(n, nnz, n_v, precision):
     row_ptr, X_k read once, X_{k-1} read and X_{k+1} written."""
     s = 8 if precision == "f64" else 4
     return nnz * (4 + s) + 4 * (n + 1) + 3 * n * n_v * s
+
+
+def pinning_bound(col_idx, n, nnz, n_v, precision, l2_bytes):
+    """Least DRAM traffic of one fused step if the L2 held, for the whole step, the
+    rows of X_k that the most nonzeros gather (a static choice; the best any
+    ordering or eviction policy can do without temporal locality): the gathers of
+    the other rows come from DRAM, plus X_{k-1} read, X_{k+1} written and the CSR."""
+    s = 8 if precision == "f64" else 4
+    row_bytes = n_v * s
+    refs = np.sort(np.bincount(col_idx, minlength=n))[::-1]
+    held = int(min(n, l2_bytes // row_bytes))
+    hit = float(refs[:held].sum() / max(1, refs.sum()))
+    byts = nnz * row_bytes * (1.0 - hit) + 2 * n * row_bytes + nnz * (4 + s) + 4 * (n + 1)
+    return {"l2_bytes": int(l2_bytes), "rows_held": held, "hit_fraction": hit,
+            "bytes_per_launch": byts}
 
 
 def fma_per_step(n, nnz, n_v):
@@ -1163,7 +1179,7 @@ def main():
     ap.add_argument("--no-pdl", action="store_true",
                     help="plain stream order between sweep steps (no programmatic dependent launch)")
     ap.add_argument("--launch", default=None,
-                    help="fixed launch shape team,chunks,staged(1|2|3)[,chunk_bytes(16|32)"
+                    help="fixed launch shape team,chunks,staged(1|2|3|4)[,chunk_bytes(16|32)"
                          "[,depth(2|4|8)]] "
                          "instead of the autotuner "
                          "(used when profiling one known kernel instance)")
@@ -1293,6 +1309,10 @@ def main():
                     "algorithmic_bytes_per_launch": alg, "launch_ms": launch_ms,
                     "frac_basis": "compulsory bytes (CSR once, X_k once, X_{k-1} read, "
                                   "X_{k+1} written) / launch time"}
+        pb = pinning_bound(A.col_idx, A.n, A.nnz, n_v, prec,
+                           torch.cuda.get_device_properties(device).L2_cache_size)
+        pb["frac"] = pb["bytes_per_launch"] / (launch_ms * 1e-3) / 1e9 / peaks["hbm_gbs"]
+        roofline["pinning_bound"] = pb
         if traffic:
             # the same launch against the DRAM bytes it actually moved (ncu)
             roofline["frac_of_traffic"] = traffic / (launch_ms * 1e-3) / 1e9 / peaks["hbm_gbs"]

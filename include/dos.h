@@ -82,9 +82,9 @@ extern "C" {
                                        once and cache the fastest (see dos_tune) */
 #define DOS_OPT_TEST_STALL_WAIT 16u /* failure-detection tests only: the TMA kernels'
                                        waits can never complete and must run out
-                                       (staged 2 expects 16 bytes more than it copies;
-                                       staged 3 arms its barrier without issuing the
-                                       gather) */
+                                       (staged 2 and 4 expect 16 bytes more than they
+                                       copy; staged 3 arms its barrier without issuing
+                                       the gather) */
 #define DOS_OPT_NO_PDL 32u          /* launch consecutive sweep steps with plain stream
                                        order instead of programmatic dependent launch
                                        (the next step's blocks are scheduled while the
@@ -116,10 +116,14 @@ typedef struct {
                                 2: row panels of X_k and X_{k-1} staged in shared memory
                                 by bulk asynchronous (TMA) copies;
                                 3: the gathered rows X_k[j] of each four nonzeros loaded
-                                by one TMA gather (tile::gather4) into shared memory
-                                (0: choose) */
+                                by one TMA gather (tile::gather4) into shared memory;
+                                4: as 1, with each row tile's CSR slice (row_ptr,
+                                column indices, values) staged in shared memory by bulk
+                                asynchronous copies first; needs col_idx and val
+                                16-byte aligned (0: choose) */
     int32_t chunk_bytes;     /* bytes per chunk: 16, or 32 (256-bit loads and stores;
-                                with staged 1 only, and rows of whole 32-byte chunks)
+                                with staged 1 or 4 only, and rows of whole 32-byte
+                                chunks)
                                 (0: 16, or the autotuned choice) */
     int32_t depth;           /* staged 3 only: batches of four gathers each team keeps in
                                 flight (2, 4 or 8); 0: the deepest of 8, 4, 2 whose

@@ -192,7 +192,7 @@ Shape choose_shape(dos_ctx *ctx, const SweepRequest &r, const dos_csr *Adesc, in
         sh.team = o.team ? o.team : d.team;
         sh.chunks = o.chunks ? o.chunks : d.chunks;
         sh.block = o.block ? o.block : d.block;
-        DOS_REQUIRE(o.staged >= 0 && o.staged <= 3, "launch.staged must be 0, 1, 2 or 3");
+        DOS_REQUIRE(o.staged >= 0 && o.staged <= 4, "launch.staged must be 0, 1, 2, 3 or 4");
         sh.staged = o.staged ? o.staged - 1 : d.staged;
         DOS_REQUIRE(o.chunk_bytes == 0 || o.chunk_bytes == 16 || o.chunk_bytes == 32,
                     "launch.chunk_bytes must be 0, 16 or 32");
@@ -342,6 +342,7 @@ void run_sweep(dos_ctx *ctx, const dos_csr *Adesc, SweepRequest &r, cudaStream_t
     a.col_idx = A.col_idx;
     a.val = val;
     a.n_rows = A.n;
+    a.nnz = A.nnz;
     a.ld = ld;
     a.B = B;
     a.seg_row0 = seg.row0;
@@ -537,7 +538,7 @@ Shape tune_shape(dos_ctx *ctx, const dos_csr *A, int B, const int64_t *seg_rows,
     bool first = true;
     // variants: direct loads, TMA panels and TMA gathers (16-byte chunks), and
     // direct loads with 32-byte chunks
-    const int variants[4][2] = {{0, 16}, {1, 16}, {2, 16}, {0, 32}};
+    const int variants[6][2] = {{0, 16}, {1, 16}, {2, 16}, {0, 32}, {3, 16}, {3, 32}};
     for (int G = 1; G <= 32; G <<= 1) {
         for (int C : {1, 2, 4})
         for (const auto &var : variants) {

@@ -83,8 +83,9 @@ struct PinnedBuffer {
 struct Shape {
     int team = 0, chunks = 0, block = 0, tiles = 0;
     int staged = 0;  // 0 direct loads, 1 TMA-staged row panels (step_staged_kernel),
-                     // 2 TMA gathers of the X_k rows (step_tmag_kernel)
-    int cb = 16;     // bytes per chunk: 16, or 32 (direct loads only)
+                     // 2 TMA gathers of the X_k rows (step_tmag_kernel),
+                     // 3 direct loads with the tile's CSR staged (step_csrs_kernel)
+    int cb = 16;     // bytes per chunk: 16, or 32 (direct loads, staged 0 or 3)
     int depth = 0;   // TMA gathers: batches in flight per team (2, 4, 8; 0: by shared memory)
 };
 
@@ -160,6 +161,7 @@ struct SweepArgs {
     const int32_t *col_idx;
     const void *val;  // double* (F64) or float* (F32)
     int64_t n_rows;   // total rows (all segments)
+    int64_t nnz;      // nonzeros (all segments)
     int n_v, ld;      // vectors, padded row length of the vector blocks
     int B;            // segments
     const int32_t *seg_row0;  // device, B+1

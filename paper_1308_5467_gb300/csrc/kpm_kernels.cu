@@ -997,9 +997,229 @@ __global__ void __launch_bounds__(kBlock, 2) step_tmag_kernel(const StepParams<T
     }
 }
 
+// ---- CSR-staged variant -------------------------------------------------------------
+// The tile's slice of the matrix is copied into shared memory before its rows are
+// walked: row_ptr[rb..re] by the block's threads (coalesced), the column indices and
+// values of its nonzeros by two bulk asynchronous copies (cp.async.bulk, the Tensor
+// Memory Accelerator's 1-D form) issued by one thread and completing on an mbarrier
+// (bounded wait, as in the other staged variants).  A row's nonzeros are then read
+// from shared memory -- the same address across a team, a broadcast -- so every
+// gather address of a row is known at once: the dependent chain per row shrinks from
+// (CSR fetch, then gathers) for every batch of nonzeros to the gathers alone, and the
+// CSR registers and shuffles of the direct kernel go away.  The copies run while the
+// other blocks resident on the SM compute.  A tile whose slice exceeds the staging
+// capacity (kCsrsNnz nonzeros, kCsrsRows rows) reads its CSR from global memory with
+// the same arithmetic.  Bulk copies need 16-byte aligned ends: the slice is widened
+// to whole 16-byte groups of 4 entries (never past the arrays' last whole group; the
+// entries after it are loaded by plain loads).
+constexpr int kCsrsNnz = 4096;
+constexpr int kCsrsRows = 2048;
+
+template <typename T>
+__host__ __device__ inline size_t csrs_head_bytes() {
+    return 16 + (size_t)(kCsrsRows + 4) * 4 + (size_t)(kCsrsNnz + 8) * 4 +
+           (size_t)(kCsrsNnz + 8) * sizeof(T);
+}
+size_t csrs_smem(int block, int ld, int esz) {
+    const size_t head = 16 + (size_t)(kCsrsRows + 4) * 4 + (size_t)(kCsrsNnz + 8) * 4 +
+                        (size_t)(kCsrsNnz + 8) * esz;
+    return (head + 15) / 16 * 16 + (size_t)(block / 32) * ld * sizeof(double);
+}
+
+template <typename T, int G, int CPT, bool PV, int CB>
+__global__ void __launch_bounds__(kBlock, 3) step_csrs_kernel(const StepParams<T> p,
+                                                              int64_t nnz) {
+    constexpr int VPT = CB / (int)sizeof(T);
+    using Acc = typename Traits<T>::Acc;
+    constexpr int TPW = 32 / G;
+    constexpr int U = CPT * CB >= 64 ? 4 : 8;
+    extern __shared__ __align__(16) unsigned char csmem[];
+    uint64_t *bar = reinterpret_cast<uint64_t *>(csmem);
+    int32_t *rp_s = reinterpret_cast<int32_t *>(csmem + 16);
+    int32_t *col_s = rp_s + kCsrsRows + 4;
+    T *val_s = reinterpret_cast<T *>(col_s + kCsrsNnz + 8);
+    double *red = reinterpret_cast<double *>(csmem + (csrs_head_bytes<T>() + 15) / 16 * 16);
+    __shared__ int s_stop;
+
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+
+    const int4 tl = p.tiles[blockIdx.x];
+    const int rb = tl.x, re = tl.y, seg = tl.z;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int g = lane % G;
+    const int n_teams = (blockDim.x >> 5) * TPW;
+    const int team = warp * TPW + lane / G;
+    const Affine<T> shift(p.seg_c[seg], p.seg_inv_d[seg]);
+    const int ld = p.ld;
+    const T *__restrict__ xseg = p.xc + (size_t)p.seg_row0[seg] * ld;
+    const T *__restrict__ xc = p.xc;
+    const int32_t *__restrict__ row_ptr = p.row_ptr;
+    T *xn = p.xn;
+
+    // ---- stage the tile's CSR slice ----
+    const bool rows_fit = re - rb <= kCsrsRows;
+    if (rows_fit)
+        for (int r = threadIdx.x; r <= re - rb; r += blockDim.x) rp_s[r] = __ldg(row_ptr + rb + r);
+    if (threadIdx.x == 0) s_stop = 0;
+    __syncthreads();
+    const int64_t e_lo = rows_fit ? rp_s[0] : 0, e_hi = rows_fit ? rp_s[re - rb] : 0;
+    const int64_t a0 = e_lo & ~int64_t(3);                    // first staged entry
+    const int64_t whole = nnz & ~int64_t(3);                  // end of the last whole group
+    const bool staged = rows_fit && (e_hi - a0) <= kCsrsNnz;
+    if (staged) {
+        const int64_t a1 = min((e_hi + 3) & ~int64_t(3), whole);  // bulk part [a0, a1)
+        if (threadIdx.x == 0) {
+            mbar_init(bar, 1);
+            mbar_init_fence();
+            const uint32_t n4 = a1 > a0 ? (uint32_t)(a1 - a0) : 0u;
+            // (stall_test: expect 16 bytes that never arrive, so the wait must run out)
+            mbar_expect_tx(bar, n4 * (4u + (uint32_t)sizeof(T)) + (p.stall_test ? 16u : 0u));
+            if (n4) {
+                bulk_copy_g2s(col_s, p.col_idx + a0, n4 * 4u, bar);
+                bulk_copy_g2s(val_s, p.val + a0, n4 * (uint32_t)sizeof(T), bar);
+            }
+        }
+        // entries past the last whole group of 4 (at most 3): plain loads
+        const int64_t t0 = max(a0, whole);
+        if (threadIdx.x < 4 && t0 + threadIdx.x < e_hi) {
+            const int64_t e = t0 + threadIdx.x;
+            col_s[e - a0] = __ldg(p.col_idx + e);
+            val_s[e - a0] = __ldg(p.val + e);
+        }
+        __syncthreads();  // the barrier is initialised before anyone waits on it
+        if (!mbar_wait_bounded(bar, 0, p.spin_cycles)) {
+            // give the copies in flight a second (bounded) chance to land before the
+            // block moves on and, at exit, hands its shared memory back
+            mbar_wait_bounded(bar, 0, p.spin_cycles);
+            atomicOr(p.status, 4);
+            s_stop = 1;
+        }
+        __syncthreads();
+    }
+    const bool stop = s_stop != 0;
+
+    constexpr int NA = PV ? CPT : 1, NJ = PV ? VPT : 1;
+    Acc accR[NA][NJ], accS[NA][NJ];
+#pragma unroll
+    for (int cc = 0; cc < NA; ++cc)
+#pragma unroll
+        for (int j = 0; j < NJ; ++j) {
+            acc_zero(accR[cc][j]);
+            acc_zero(accS[cc][j]);
+        }
+    bool valid[CPT];
+#pragma unroll
+    for (int cc = 0; cc < CPT; ++cc) valid[cc] = (g + cc * G) < p.n_chunks;
+
+    for (int row = rb + team; row < re && !stop; row += n_teams) {
+        int e0, e1;
+        if (staged) {
+            e0 = rp_s[row - rb];
+            e1 = rp_s[row - rb + 1];
+        } else {
+            e0 = __ldg(row_ptr + row);
+            e1 = __ldg(row_ptr + row + 1);
+        }
+        const size_t roff = (size_t)row * ld;
+        T xk[CPT][VPT], xo[CPT][VPT];
+#pragma unroll
+        for (int cc = 0; cc < CPT; ++cc) {
+            if (valid[cc]) {
+                const int off = (g + cc * G) * VPT;
+                load_chunk(xc + roff + off, xk[cc]);
+                load_chunk_prev(xn + roff + off, xo[cc]);
+            }
+        }
+        T y[CPT][VPT];
+#pragma unroll
+        for (int cc = 0; cc < CPT; ++cc)
+#pragma unroll
+            for (int j = 0; j < VPT; ++j) y[cc][j] = T(0);
+        for (int e = e0; e < e1; e += U) {
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                if (e + u < e1) {
+                    int col;
+                    T a;
+                    if (staged) {
+                        col = col_s[e + u - a0];
+                        a = val_s[e + u - a0];
+                    } else {
+                        col = __ldg(p.col_idx + e + u);
+                        a = __ldg(p.val + e + u);
+                    }
+                    const T *src = xseg + (size_t)col * ld;
+#pragma unroll
+                    for (int cc = 0; cc < CPT; ++cc) {
+                        if (valid[cc]) {
+                            T xv[VPT];
+                            load_chunk(src + (g + cc * G) * VPT, xv);
+#pragma unroll
+                            for (int j = 0; j < VPT; ++j) y[cc][j] = fma(a, xv[j], y[cc][j]);
+                        }
+                    }
+                }
+            }
+        }
+        T rr = T(0), ss = T(0);
+#pragma unroll
+        for (int cc = 0; cc < CPT; ++cc) {
+            if (!valid[cc]) continue;
+            const int off = (g + cc * G) * VPT;
+            T xnew[VPT];
+#pragma unroll
+            for (int j = 0; j < VPT; ++j)
+                xnew[j] = fma(T(2), shift(y[cc][j], xk[cc][j]), -xo[cc][j]);
+            store_chunk(xn + roff + off, xnew);
+#pragma unroll
+            for (int j = 0; j < VPT; ++j) {
+                if constexpr (PV) {
+                    acc_add_prod(accR[cc][j], xnew[j], xk[cc][j]);
+                    acc_add_prod(accS[cc][j], xnew[j], xnew[j]);
+                } else {
+                    rr = fma(xnew[j], xk[cc][j], rr);
+                    ss = fma(xnew[j], xnew[j], ss);
+                }
+            }
+        }
+        if constexpr (!PV) {
+            acc_add(accR[0][0], rr);
+            acc_add(accS[0][0], ss);
+        }
+    }
+
+    if constexpr (PV) {
+        double *out = p.part + (size_t)blockIdx.x * 2 * p.pv;
+        block_reduce_store<Acc, G, CPT, VPT>(accR, out, ld, p.n_chunks, p.pv, red);
+        block_reduce_store<Acc, G, CPT, VPT>(accS, out + p.pv, ld, p.n_chunks, p.pv, red);
+    } else {
+        double *out = p.part + (size_t)blockIdx.x * 2;
+        block_reduce_scalar(accR[0][0], out, red);
+        block_reduce_scalar(accS[0][0], out + 1, red);
+    }
+}
+
 // ---- kernel table --------------------------------------------------------------
 template <typename T>
 using StepFn = void (*)(const StepParams<T>);
+
+template <typename T>
+using CsrsFn = void (*)(const StepParams<T>, int64_t);
+
+template <typename T>
+CsrsFn<T> pick_csrs(int G, int CPT, bool per_vec, int cb) {
+#define DOS_CASE(GG, CC, BB)                                                                  \
+    if (G == GG && CPT == CC && cb == BB)                                                    \
+        return per_vec ? step_csrs_kernel<T, GG, CC, true, BB>                               \
+                       : step_csrs_kernel<T, GG, CC, false, BB>;
+    DOS_CASE(4, 1, 16) DOS_CASE(8, 1, 16) DOS_CASE(16, 1, 16) DOS_CASE(32, 1, 16)
+    DOS_CASE(8, 2, 16) DOS_CASE(16, 2, 16) DOS_CASE(32, 2, 16) DOS_CASE(32, 4, 16)
+    DOS_CASE(2, 1, 32) DOS_CASE(4, 1, 32) DOS_CASE(4, 2, 32) DOS_CASE(8, 1, 32)
+    DOS_CASE(8, 2, 32) DOS_CASE(16, 1, 32) DOS_CASE(16, 2, 32) DOS_CASE(32, 1, 32)
+#undef DOS_CASE
+    return nullptr;
+}
 
 template <typename T>
 StepFn<T> pick_staged(int G, int CPT, bool per_vec) {
@@ -1332,15 +1552,20 @@ bool shape_supported(int precision, const Shape &sh, int ld) {
     if (sh.team < 1 || sh.team > 32 || (sh.team & (sh.team - 1))) return false;
     if (sh.chunks != 1 && sh.chunks != 2 && sh.chunks != 4) return false;
     if (sh.tiles < 1) return false;
-    if (sh.staged < 0 || sh.staged > 2) return false;
+    if (sh.staged < 0 || sh.staged > 3) return false;
     if (sh.cb != 16 && sh.cb != 32) return false;
     const int vpt = sh.cb / esz;
     if (sh.cb == 32) {  // 256-bit accesses: direct loads, rows of whole 32-byte chunks
-        if (sh.staged != 0 || ld % vpt != 0) return false;
-        if (!(precision == DOS_PREC_F64 ? (void *)pick<double>(sh.team, sh.chunks, false, 32)
+        if ((sh.staged != 0 && sh.staged != 3) || ld % vpt != 0) return false;
+        if (sh.staged == 0 &&
+            !(precision == DOS_PREC_F64 ? (void *)pick<double>(sh.team, sh.chunks, false, 32)
                                         : (void *)pick<float>(sh.team, sh.chunks, false, 32)))
             return false;
     }
+    if (sh.staged == 3 &&
+        !(precision == DOS_PREC_F64 ? (void *)pick_csrs<double>(sh.team, sh.chunks, false, sh.cb)
+                                    : (void *)pick_csrs<float>(sh.team, sh.chunks, false, sh.cb)))
+        return false;
     if (sh.staged == 1 &&
         !(precision == DOS_PREC_F64 ? (void *)pick_staged<double>(sh.team, sh.chunks, false)
                                     : (void *)pick_staged<float>(sh.team, sh.chunks, false)))
@@ -1394,6 +1619,12 @@ static int occupancy_t(const Shape &sh, int ld) {
         const int esz = (int)sizeof(T);
         const size_t sm = tmag_smem(sh.block, sh.team, ld, esz,
                                     tmag_ring_depth(sh.block, sh.team, ld, esz, sh.depth));
+        allow_smem_fn((const void *)fn, sm);
+        DOS_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, sh.block, sm));
+    } else if (sh.staged == 3) {
+        auto fn = pick_csrs<T>(sh.team, sh.chunks, false, sh.cb);
+        if (!fn) return 0;
+        const size_t sm = csrs_smem(sh.block, ld, (int)sizeof(T));
         allow_smem_fn((const void *)fn, sm);
         DOS_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, sh.block, sm));
     } else {
@@ -1477,6 +1708,25 @@ static void launch_step_t(const SweepArgs &a, int k, int slot, cudaStream_t s) {
         const size_t sm = staged_smem(a.shape.block, a.shape.team, a.ld, sizeof(T));
         allow_smem<T>(fn, sm);
         fn<<<a.n_tiles, a.shape.block, sm, s>>>(p);
+    } else if (a.shape.staged == 3 && k > 0) {
+        auto fn = pick_csrs<T>(a.shape.team, a.shape.chunks, a.per_vec != 0, a.shape.cb);
+        if (!fn) throw Error{DOS_EINVAL, "unsupported CSR-staged launch shape"};
+        if (((uintptr_t)a.col_idx & 15) || ((uintptr_t)a.val & 15))
+            throw Error{DOS_EINVAL, "the CSR-staged variant needs col_idx and val 16-byte aligned"};
+        p.panel_rows = 0;
+        const size_t sm = csrs_smem(a.shape.block, a.ld, (int)sizeof(T));
+        allow_smem_fn((const void *)fn, sm);
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3((unsigned)a.n_tiles);
+        cfg.blockDim = dim3((unsigned)a.shape.block);
+        cfg.dynamicSmemBytes = sm;
+        cfg.stream = s;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+        attr[0].val.programmaticStreamSerializationAllowed = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = a.pdl ? 1 : 0;
+        DOS_CUDA_TRY(cudaLaunchKernelEx(&cfg, fn, p, (int64_t)a.nnz));
     } else if (a.shape.staged == 2 && k > 0) {
         auto fn = pick_tmag<T>(a.shape.team, a.shape.chunks, a.per_vec != 0);
         if (!fn) throw Error{DOS_EINVAL, "unsupported TMA-gather launch shape"};

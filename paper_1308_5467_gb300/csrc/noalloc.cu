@@ -133,6 +133,7 @@ extern "C" int dos_kpm_moments_noalloc(const dos_csr *A, double lb, double ub, i
         a.col_idx = A->col_idx;
         a.val = A->val;
         a.n_rows = A->n;
+        a.nnz = A->nnz;
         a.n_v = n_v;
         a.ld = ld;
         a.B = 1;

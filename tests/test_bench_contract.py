@@ -45,6 +45,8 @@ def test_roofline_names_the_variant_that_ran():
     assert bench.step_kernel_name({"staged": 1, "chunk_bytes": 32}, "f32") == "step_kernel<float>"
     assert bench.step_kernel_name({"staged": 2}, "f64") == "step_staged_kernel<double>"
     assert bench.step_kernel_name({"staged": 3, "depth": 2}, "f32") == "step_tmag_kernel<float>"
+    assert bench.step_kernel_name({"staged": 4, "chunk_bytes": 32}, "f32") == \
+        "step_csrs_kernel<float>"
     assert bench.step_kernel_name(None, "f64") == "step_kernel<double>"
 
 

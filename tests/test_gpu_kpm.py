@@ -278,11 +278,71 @@ def test_tma_gather_wait_timeout_is_reported(ctx):
     assert np.abs(mu - ref).max() < TOL64
 
 
+@pytest.mark.parametrize("precision", ["f64", "f32"])
+@pytest.mark.parametrize("launch", [{"staged": 4}, {"team": 4, "chunks": 2, "staged": 4},
+                                    {"team": 4, "chunks": 2, "chunk_bytes": 32, "staged": 4},
+                                    {"team": 16, "chunks": 1, "staged": 4, "tiles": 2},
+                                    {"team": 8, "chunks": 2, "staged": 4, "tiles": 500},
+                                    {"team": 32, "chunks": 1, "chunk_bytes": 32, "staged": 4}])
+def test_csr_staged_parity(ctx, precision, launch):
+    """Each tile's CSR slice staged in shared memory by bulk copies (staged 4): a
+    lattice, a random matrix with empty rows and one dense row (nnz not a multiple of
+    four: the slice's tail comes from plain loads), tiles too large to stage (two
+    tiles: they read the CSR from global memory), many small tiles; per-vector and
+    total moments."""
+    from paper_1308_5467_gb300 import dos
+    dtype = np.float64 if precision == "f64" else np.float32
+    per_chunk = launch.get("chunk_bytes", 16) // (8 if precision == "f64" else 4)
+    mats = ((anderson_3d(13, 6.0, seed=4), -9.6, 9.6),
+            (random_symmetric(401, 0.02, 9, empty_rows=7, long_row=37), None, None),
+            (diagonal(np.linspace(-1.0, 1.0, 5003)), -1.1, 1.1))
+    for A, lb, ub in mats:
+        Aw = A.astype(dtype)
+        if lb is None:
+            lb, ub = obounds.bounds(A, "gershgorin", pad_frac=0.01)
+        for n_v in (64, 24):
+            ok_shape = ("team" not in launch or
+                        launch["team"] * launch.get("chunks", 1) * per_chunk >= n_v) and \
+                (n_v * (8 if precision == "f64" else 4)) % launch.get("chunk_bytes", 16) == 0
+            if not ok_shape:
+                with pytest.raises(dos.DosError):
+                    ctx.dos_kpm_moments(dev(Aw), lb, ub, 30, n_v, seed=5, precision=precision,
+                                        launch=launch)
+                continue
+            pv = np.empty((n_v, 71))
+            mu = ctx.dos_kpm_moments(dev(Aw), lb, ub, 70, n_v, seed=5, precision=precision,
+                                     launch=launch, mu_per_vec=pv)
+            mu_tot = ctx.dos_kpm_moments(dev(Aw), lb, ub, 70, n_v, seed=5, precision=precision,
+                                         launch=launch)
+            ref = okpm.kpm_moments_per_vector(Aw, lb, ub, 70, n_v, seed=5)
+            tol, tolt = (TOL64, TOL64) if precision == "f64" else (tol32(70, A.n),
+                                                                   tol32(70, A.n * n_v))
+            assert np.all(np.abs(pv - ref) <= tol), fp32_ratio(pv, ref)
+            assert np.all(np.abs(mu - ref.mean(axis=0)) <= tolt)
+            assert np.all(np.abs(mu_tot - ref.mean(axis=0)) <= tolt), fp32_ratio(mu_tot,
+                                                                                 ref.mean(0))
+
+
+def test_csr_staged_wait_timeout_is_reported(ctx):
+    """The CSR-staged kernel's bounded wait made to run out (it expects 16 bytes more
+    than it copies): DOS_ETIMEOUT, and the context still works."""
+    from paper_1308_5467_gb300 import dos
+    A = dev(anderson_3d(8, 6.0, seed=4))
+    with pytest.raises(dos.DosError) as ei:
+        ctx.dos_kpm_moments(A, -9.6, 9.6, 10, 16, seed=5, precision="f64",
+                            launch={"staged": 4}, flags=dos.DOS_OPT_TEST_STALL_WAIT,
+                            wait_limit_cycles=2_000_000)
+    assert ei.value.status == dos.DOS_ETIMEOUT
+    mu = ctx.dos_kpm_moments(A, -9.6, 9.6, 10, 16, seed=5, precision="f64", launch={"staged": 4})
+    ref = okpm.kpm_moments(anderson_3d(8, 6.0, seed=4), -9.6, 9.6, 10, 16, seed=5)
+    assert np.abs(mu - ref).max() < TOL64
+
+
 def test_unknown_variant_is_rejected(ctx):
     from paper_1308_5467_gb300 import dos
     A = anderson_3d(6, 6.0, seed=4)
-    for launch in ({"staged": 4}, {"staged": 3, "depth": 3}, {"staged": 3, "depth": 16},
-                   {"staged": 1, "depth": 4}, {"depth": 4}):
+    for launch in ({"staged": 5}, {"staged": 3, "depth": 3}, {"staged": 3, "depth": 16},
+                   {"staged": 4, "depth": 4}, {"staged": 1, "depth": 4}, {"depth": 4}):
         with pytest.raises(dos.DosError):
             ctx.dos_kpm_moments(dev(A), -9.6, 9.6, 10, 16, seed=5, precision="f64",
                                 launch=launch)
