@@ -34,7 +34,9 @@ namespace {
 
 typedef __nv_bfloat16 bf16;
 
-constexpr int kBM = 128, kBN = 128, kBK = 64, kStages = 4, kThreads = 128;
+// Three stages (99 KB of shared memory) leave room for two CTAs per SM, so one
+// tile's epilogue overlaps another's loads and products.
+constexpr int kBM = 128, kBN = 128, kBK = 64, kStages = 3, kThreads = 128;
 constexpr uint32_t kTileBytes = kBM * kBK * 2;     // one operand slice: 128 rows x 128 B
 constexpr uint32_t kStageBytes = 2 * kTileBytes;   // A and B (kBN == kBM)
 constexpr uint32_t kTmemCols = kBN;                // FP32 accumulator: one column per n
@@ -145,7 +147,7 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
 }
 
 template <int EPI>
-__global__ void __launch_bounds__(kThreads, 1)
+__global__ void __launch_bounds__(kThreads, 2)
     gemm_tc_kernel(const __grid_constant__ CUtensorMap map_a,
                    const __grid_constant__ CUtensorMap map_b, const TcGemm g) {
     extern __shared__ uint8_t smem_raw[];

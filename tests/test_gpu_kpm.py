@@ -279,7 +279,7 @@ def test_tma_gather_wait_timeout_is_reported(ctx):
 
 
 @pytest.mark.parametrize("precision", ["f64", "f32"])
-@pytest.mark.parametrize("launch", [{"staged": 4}, {"team": 4, "chunks": 2, "staged": 4},
+@pytest.mark.parametrize("launch", [{"staged": 4}, {"team": 8, "chunks": 2, "staged": 4},
                                     {"team": 4, "chunks": 2, "chunk_bytes": 32, "staged": 4},
                                     {"team": 16, "chunks": 1, "staged": 4, "tiles": 2},
                                     {"team": 8, "chunks": 2, "staged": 4, "tiles": 500},
