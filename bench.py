@@ -234,14 +234,12 @@ def gpu_id_for(device):
 
 
 def kernel_source_hash():
-    """SHA-256 of the fused step kernel's source: kpm_kernels.cu up to the staged
-    variant (the load/store and accumulation helpers, the team fetch, the block
-    reductions and step_kernel itself), so a stored ncu figure is dropped as soon
-    as any of them changes."""
+    """SHA-256 of the sweep kernels' source (kpm_kernels.cu: every variant of the
+    fused step and its helpers), so a stored ncu figure is dropped as soon as any
+    of them changes."""
     with open(os.path.join(ROOT, "paper_1308_5467_gb300", "csrc", "kpm_kernels.cu")) as f:
         src = f.read()
-    region = src[:src.index("// ---- TMA-staged variant")]
-    return hashlib.sha256(region.encode()).hexdigest()[:16]
+    return hashlib.sha256(src.encode()).hexdigest()[:16]
 
 
 def oracle_sample(A, lb, ub, M, n_v_full, seed, target_s, cores):
@@ -915,7 +913,8 @@ def run_mlp(args, w, world, rank, local, device):
         "e2e": {"value": B / (ms_e2e * 1e-3), "unit": "samples/s",
                 "h2d_bytes_per_step": B * (n_in + n_out) * 4, "d2h_bytes_per_step": 4,
                 "ms_per_step": ms_e2e},
-        "cpu_baseline": mlp_cpu_baseline(net, x.cpu().numpy(), t.cpu().numpy()),
+        "cpu_baseline": (None if args.no_cpu_baseline else
+                         mlp_cpu_baseline(net, x.cpu().numpy(), t.cpu().numpy())),
         "clocks": clk.summary(),
     }
     if rank == 0:
@@ -1180,7 +1179,7 @@ def main():
                     help="plain stream order between sweep steps (no programmatic dependent launch)")
     ap.add_argument("--launch", default=None,
                     help="fixed launch shape team,chunks,staged(1|2|3|4)[,chunk_bytes(16|32)"
-                         "[,depth(2|4|8)]] "
+                         "[,depth(2|4|8)[,tiles]]] "
                          "instead of the autotuner "
                          "(used when profiling one known kernel instance)")
     args = ap.parse_args()
@@ -1231,7 +1230,7 @@ def main():
     # launch shape of the fused step chosen by the library's autotuner (cached in ctx)
     fixed = None
     if args.launch:
-        fixed = dict(zip(("team", "chunks", "staged", "chunk_bytes", "depth"),
+        fixed = dict(zip(("team", "chunks", "staged", "chunk_bytes", "depth", "tiles"),
                          (int(v) for v in args.launch.split(","))))
         tuned_shape, tuned64 = fixed, None
     else:

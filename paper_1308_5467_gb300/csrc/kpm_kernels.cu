@@ -1011,9 +1011,12 @@ __global__ void __launch_bounds__(kBlock, 2) step_tmag_kernel(const StepParams<T
 // capacity (kCsrsNnz nonzeros, kCsrsRows rows) reads its CSR from global memory with
 // the same arithmetic.  Bulk copies need 16-byte aligned ends: the slice is widened
 // to whole 16-byte groups of 4 entries (never past the arrays' last whole group; the
-// entries after it are loaded by plain loads).
-constexpr int kCsrsNnz = 4096;
-constexpr int kCsrsRows = 2048;
+// entries after it are loaded by plain loads).  The capacity is kept small: shared
+// memory taken from the L1 costs the gathers their L1 hits (a 4096-entry slice, 45 KB
+// per block, dropped the 64^3 lattice's L1 hit rate from 38% to 21%), and the tuner
+// picks tile counts whose slices fit.
+constexpr int kCsrsNnz = 1024;
+constexpr int kCsrsRows = 512;
 
 template <typename T>
 __host__ __device__ inline size_t csrs_head_bytes() {
