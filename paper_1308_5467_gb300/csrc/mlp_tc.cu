@@ -15,7 +15,11 @@
 //     refilled while the current slice's MMAs run;
 //   * a last commit to "done" releases the four warps, which read the
 //     accumulator with tcgen05.ld (warp w owns tensor-memory lanes 32w..32w+31,
-//     the tile's rows) and apply the epilogue.
+//     the tile's rows) into an FP32 tile in the (now idle) stage memory, padded to
+//     129 columns so that neither a thread writing its row nor a warp reading a
+//     row or a column conflicts on banks; the epilogue then leaves the tile in two
+//     coalesced passes, row by row for the row-major outputs (bias and mask read
+//     along the row) and column by column for the transposed bf16 copy.
 // Every mbarrier wait is bounded (spin cycles): a wait that runs out sets status
 // bit 8, the CTA waits (bounded again) for what it issued, frees its tensor
 // memory and skips the stores.
@@ -225,37 +229,52 @@ __global__ void __launch_bounds__(kThreads, 2)
     const int bad = __syncthreads_or(!waited || s_fail);
     tc_fence_after();
 
+    constexpr int kLd = kBN + 1;  // staged tile row stride (floats)
+    float *tile = reinterpret_cast<float *>(smem);
     if (!bad) {
-        const int row = m0 + warp * 32 + lane;
+        const int r = warp * 32 + lane;  // tile row of this thread's TMEM lane
 #pragma unroll 1
         for (int c = 0; c < kBN / 32; ++c) {
             if (n0 + c * 32 >= g.N) break;  // warp-uniform
             float v[32];
             tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(c * 32), v);
-            if (row >= g.M) continue;
 #pragma unroll
-            for (int j = 0; j < 32; ++j) {
-                const int col = n0 + c * 32 + j;
-                if (col >= g.N) break;
-                float x = v[j];
-                const size_t o = (size_t)row * g.ldc + col;
-                if (EPI == TC_EPI_BIAS_RELU_BF16) {
-                    x = fmaxf(x + g.bias[col], 0.f);
-                    const bf16 h = __float2bfloat16_rn(x);
-                    ((bf16 *)g.Cb)[o] = h;
-                    if (g.Ct) ((bf16 *)g.Ct)[(size_t)col * g.ldt + row] = h;
-                } else if (EPI == TC_EPI_BIAS_F32) {
-                    g.Cf[o] = x + g.bias[col];
-                } else if (EPI == TC_EPI_MASK) {
-                    x = __bfloat162float(((const bf16 *)g.mask)[(size_t)row * g.ldm + col]) > 0.f
-                            ? x : 0.f;
-                    g.Cf[o] = x;
-                    const bf16 h = __float2bfloat16_rn(x);
-                    if (g.Cb) ((bf16 *)g.Cb)[o] = h;
-                    if (g.Ct) ((bf16 *)g.Ct)[(size_t)col * g.ldt + row] = h;
-                } else {
-                    g.Cf[o] = x;
-                }
+            for (int j = 0; j < 32; ++j) tile[r * kLd + c * 32 + j] = v[j];
+        }
+    }
+    __syncthreads();
+    if (!bad) {
+        const int rows = min(kBM, g.M - m0), cols = min(kBN, g.N - n0);
+        // row-major outputs: a warp walks one row, lanes over consecutive columns
+        for (int idx = threadIdx.x; idx < rows * kBN; idx += kThreads) {
+            const int rr = idx / kBN, cc = idx - rr * kBN;
+            if (cc >= cols) continue;
+            const int row = m0 + rr, col = n0 + cc;
+            float x = tile[rr * kLd + cc];
+            const size_t o = (size_t)row * g.ldc + col;
+            if (EPI == TC_EPI_BIAS_RELU_BF16) {
+                x = fmaxf(x + g.bias[col], 0.f);
+                ((bf16 *)g.Cb)[o] = __float2bfloat16_rn(x);
+            } else if (EPI == TC_EPI_BIAS_F32) {
+                g.Cf[o] = x + g.bias[col];
+            } else if (EPI == TC_EPI_MASK) {
+                x = __bfloat162float(((const bf16 *)g.mask)[(size_t)row * g.ldm + col]) > 0.f
+                        ? x : 0.f;
+                g.Cf[o] = x;
+                if (g.Cb) ((bf16 *)g.Cb)[o] = __float2bfloat16_rn(x);
+            } else {
+                g.Cf[o] = x;
+            }
+            tile[rr * kLd + cc] = x;  // the epilogue's value, for the transposed pass
+        }
+        if (g.Ct) {
+            __syncthreads();
+            // transposed bf16 copy: a warp walks one column, lanes over consecutive rows
+            for (int idx = threadIdx.x; idx < cols * kBM; idx += kThreads) {
+                const int cc = idx / kBM, rr = idx - cc * kBM;
+                if (rr >= rows) continue;
+                ((bf16 *)g.Ct)[(size_t)(n0 + cc) * g.ldt + m0 + rr] =
+                    __float2bfloat16_rn(tile[rr * kLd + cc]);
             }
         }
     }
