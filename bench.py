@@ -51,11 +51,11 @@ NCU_TRAFFIC = {
     # count included), mean read + write per launch
     ("anderson64", "f32"): {"bytes": 203795541, "src": "09f9ac7bac0d0e3d",
                             "launch": {"team": 4, "chunks": 2, "staged": 1, "chunk_bytes": 32,
-                                       "tiles": 456},
+                                       "tiles": 456, "panel": 0},
                             "note": "ncu, step_kernel<float,4,2,0,32,0>, 3 launches"},
     ("chunglu", "f32"): {"bytes": 89473731840, "src": "09f9ac7bac0d0e3d",
                          "launch": {"team": 32, "chunks": 2, "staged": 3, "chunk_bytes": 16,
-                                    "depth": 2, "tiles": 4864},
+                                    "depth": 2, "tiles": 4864, "panel": 0},
                          "note": "ncu on the full-size graph, step_tmag_kernel<float,32,2,0>, "
                                  "3 launches (1 pass)"},
 }
@@ -149,6 +149,17 @@ def pinning_bound(col_idx, n, nnz, n_v, precision, l2_bytes):
     byts = nnz * row_bytes * (1.0 - hit) + 2 * n * row_bytes + nnz * (4 + s) + 4 * (n + 1)
     return {"l2_bytes": int(l2_bytes), "rows_held": held, "hit_fraction": hit,
             "bytes_per_launch": byts}
+
+
+def panel_geometry(n_v, panel, precision):
+    """Vector panels of a sweep as the library forms them (launch.panel): n_panels
+    passes over A of panel_nv vectors (the last possibly narrower), rows of ld
+    elements (whole 16-byte chunks)."""
+    vpt = 2 if precision == "f64" else 4
+    w = min(panel or 256, 256)
+    n_panels = -(-n_v // w)
+    panel_nv = -(-n_v // n_panels)
+    return n_panels, panel_nv, -(-panel_nv // vpt) * vpt
 
 
 def fma_per_step(n, nnz, n_v):
@@ -798,7 +809,7 @@ def run_learned(args, w, world, rank, local, device):
     e2e = None
     if not args.no_e2e:
         for g in groups:
-            g.host_A
+            assert g.host_A is not None      # pin the host copies before the timed region
         ms_e2e, _ = timed(lambda: pipe.run(host=True).cpu(), max(2, args.steps // 2), 1)
         h2d = 2 * sum(g.host_bytes for g in groups)
         e2e = {"value": held / (ms_e2e * 1e-3), "unit": "DOS/s", "h2d_bytes_per_step": h2d,
@@ -1151,7 +1162,7 @@ def run_method(args, w, world, rank, local, device):
             "metric": metric, "value": value, "unit": unit, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f64" if prec == "f64" else "f32+f64acc", "data": "synthetic",
+            "dtype": "f64" if prec == "f64" else "f32", "data": "synthetic",
             "config": {"workload": args.workload, "method": method, "desc": w["desc"],
                        "n": A.n, "nnz": A.nnz, "M": M, "n_v": n_v, "precision": prec,
                        "sigma": sigma, "lb": lb, "ub": ub, "launch": tuned_shape,
@@ -1187,7 +1198,7 @@ def main():
                     help="plain stream order between sweep steps (no programmatic dependent launch)")
     ap.add_argument("--launch", default=None,
                     help="fixed launch shape team,chunks,staged(1|2|3|4)[,chunk_bytes(16|32)"
-                         "[,depth(2|4|8)[,tiles]]] "
+                         "[,depth(0|2|4|8)[,tiles[,panel]]]] "
                          "instead of the autotuner "
                          "(used when profiling one known kernel instance)")
     args = ap.parse_args()
@@ -1238,7 +1249,7 @@ def main():
     # launch shape of the fused step chosen by the library's autotuner (cached in ctx)
     fixed = None
     if args.launch:
-        fixed = dict(zip(("team", "chunks", "staged", "chunk_bytes", "depth", "tiles"),
+        fixed = dict(zip(("team", "chunks", "staged", "chunk_bytes", "depth", "tiles", "panel"),
                          (int(v) for v in args.launch.split(","))))
         tuned_shape, tuned64 = fixed, None
     else:
@@ -1304,19 +1315,30 @@ def main():
     launch_ms = prof["step_ms"] / max(1, prof["step_launches"])
     kname = step_kernel_name(tuned_shape, prec)
     if prec == "f32":
-        alg = algorithmic_bytes_per_step(A.n, A.nnz, n_v, prec)
+        # one launch advances one vector panel by one step: its compulsory bytes are
+        # the CSR once and the panel's three vector blocks
+        n_panels, panel_nv, _ = panel_geometry(n_v, tuned_shape.get("panel", 0), prec)
+        alg = algorithmic_bytes_per_step(A.n, A.nnz, panel_nv, prec)
         achieved = alg / (launch_ms * 1e-3) / 1e9
         tr = NCU_TRAFFIC.get((args.workload, prec))
-        same_launch = tr is not None and all(tuned_shape.get(k) == v
+        same_launch = tr is not None and all(tuned_shape.get(k, 0) == v
                                              for k, v in tr.get("launch", {}).items())
         traffic = tr["bytes"] if tr and tr["src"] == kernel_source_hash() and same_launch else None
         roofline = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"],
                     "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"], "traffic": traffic,
                     "peak_source": peak_kind, "kernel": kname,
                     "algorithmic_bytes_per_launch": alg, "launch_ms": launch_ms,
-                    "frac_basis": "compulsory bytes (CSR once, X_k once, X_{k-1} read, "
-                                  "X_{k+1} written) / launch time"}
-        pb = pinning_bound(A.col_idx, A.n, A.nnz, n_v, prec,
+                    "frac_basis": "compulsory bytes of the launch's vector panel (CSR "
+                                  "once, X_k once, X_{k-1} read, X_{k+1} written) / launch "
+                                  "time",
+                    "panels": {"count": n_panels, "vectors": panel_nv}}
+        # the whole step (all n_v vectors, every panel) against the compulsory bytes
+        # of one pass over A for all of them
+        step_alg = algorithmic_bytes_per_step(A.n, A.nnz, n_v, prec)
+        roofline["step"] = {"compulsory_bytes": step_alg, "ms": launch_ms * n_panels,
+                            "frac": step_alg / (launch_ms * n_panels * 1e-3) / 1e9
+                            / peaks["hbm_gbs"]}
+        pb = pinning_bound(A.col_idx, A.n, A.nnz, panel_nv, prec,
                            torch.cuda.get_device_properties(device).L2_cache_size)
         pb["frac"] = pb["bytes_per_launch"] / (launch_ms * 1e-3) / 1e9 / peaks["hbm_gbs"]
         roofline["pinning_bound"] = pb
@@ -1353,7 +1375,9 @@ def main():
                         # FP32 form against the FP64 form on the same values and vectors:
                         # the arithmetic error, next to the stochastic error of the estimate
                         "max_abs_diff_vs_f32": float(diff.max()),
-                        "fp32_bound_2u_sqrt_k": float(2 * 2.0 ** -24 * np.sqrt(M + 1)),
+                        # u sqrt(k+1) (1/2 + 40/sqrt(N)) at k = M, N = n n_v
+                        "fp32_bound_at_M": float(2.0 ** -24 * np.sqrt(M + 1.0)
+                                                 * (0.5 + 40.0 / np.sqrt(A.n * n_v))),
                         "max_diff_over_u_sqrt_k": float((diff / (2.0 ** -24
                                                                  * np.sqrt(k + 1))).max()),
                         "stochastic_std_sqrt_2_over_n_nv": float(np.sqrt(2.0 / (A.n * n_v)))}

@@ -128,6 +128,16 @@ typedef struct {
     int32_t depth;           /* staged 3 only: batches of four gathers each team keeps in
                                 flight (2, 4 or 8); 0: the deepest of 8, 4, 2 whose
                                 stages leave room for two blocks per SM */
+    int32_t panel;           /* vectors per pass over A, 0..4096: the n_v vectors are
+                                swept in ceil(n_v / w) consecutive passes of at most
+                                w = min(panel, 256) vectors (equal widths, the last
+                                possibly narrower), each pass reading A once; the two
+                                vector blocks take 2 n w' s bytes of device memory
+                                (w' = the pass width rounded up to 16 bytes of the
+                                element size s), so narrower passes fit larger n.
+                                The moments do not depend on it beyond the rounding
+                                of their FP64 sums.  0: w = 256 (the autotuner keeps
+                                0: narrower passes measured slower) */
 } dos_launch;
 
 /* Optional arguments of the _ex / _batched entry points (NULL = defaults). */

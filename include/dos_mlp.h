@@ -17,8 +17,13 @@
  * Parameters are exchanged as one flat FP32 array in the order
  * W1 (row-major), b1, W2, b2, W3, b3.  Arrays may be host or device memory.
  * All functions return DOS_* status codes (include/dos.h); messages go to the
- * owning context's dos_last_error().  A dos_mlp is bound to the context it
- * was created from and must be destroyed before it.
+ * owning context's dos_last_error().  Every wait inside the tensor-core
+ * products is bounded: a wait that runs out skips that tile's stores and sets
+ * a status flag of the network, which every call that synchronises (a host
+ * output or loss, dos_mlp_get_params, dos_mlp_save) reads and clears,
+ * returning DOS_ETIMEOUT; a call that stays asynchronous on a device stream
+ * leaves the report to the next one that synchronises.  A dos_mlp is bound to
+ * the context it was created from and must be destroyed before it.
  */
 #ifndef DOS_MLP_H
 #define DOS_MLP_H

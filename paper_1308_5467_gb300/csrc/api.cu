@@ -183,12 +183,32 @@ struct SweepRequest {
 Shape tune_shape(dos_ctx *ctx, const dos_csr *A, int B, const int64_t *seg_rows, int n_v,
                  int precision, double *best_ms, cudaStream_t s);
 
-Shape choose_shape(dos_ctx *ctx, const SweepRequest &r, const dos_csr *Adesc, int ld,
-                   int64_t n_rows, int64_t nnz, cudaStream_t s) {
+// Vector panels: the n_v vectors are swept in n_panels consecutive passes over
+// A of panel_nv vectors each (the last may be narrower); ld is a panel's row
+// length in elements, rounded up to whole 16-byte chunks of the sweep precision.
+struct Panels {
+    int n_panels, panel_nv, ld;
+};
+Panels panels_of(int n_v, int width, int precision) {
+    const int vpt = precision == DOS_PREC_F64 ? 2 : 4;
+    const int w = std::min(width > 0 ? width : kPanelMax, kPanelMax);
+    Panels p;
+    p.n_panels = (n_v + w - 1) / w;
+    p.panel_nv = (n_v + p.n_panels - 1) / p.n_panels;
+    p.ld = (p.panel_nv + vpt - 1) / vpt * vpt;
+    return p;
+}
+
+Shape choose_shape(dos_ctx *ctx, const SweepRequest &r, const dos_csr *Adesc, int64_t n_rows,
+                   int64_t nnz, cudaStream_t s) {
     const dos_launch &o = r.opts.launch;
-    if (o.team || o.chunks || o.block || o.tiles || o.staged || o.chunk_bytes || o.depth) {
+    if (o.team || o.chunks || o.block || o.tiles || o.staged || o.chunk_bytes || o.depth ||
+        o.panel) {
+        DOS_REQUIRE(o.panel >= 0 && o.panel <= 4096, "launch.panel must be in [0, 4096]");
+        const int ld = panels_of(r.n_v, o.panel, r.precision).ld;
         Shape d = default_shape(r.precision, ld, ctx->num_sms, n_rows);
         Shape sh;
+        sh.panel = o.panel;
         sh.team = o.team ? o.team : d.team;
         sh.chunks = o.chunks ? o.chunks : d.chunks;
         sh.block = o.block ? o.block : d.block;
@@ -214,6 +234,7 @@ Shape choose_shape(dos_ctx *ctx, const SweepRequest &r, const dos_csr *Adesc, in
         }
         return sh;
     }
+    const int ld = panels_of(r.n_v, 0, r.precision).ld;
     auto it = ctx->tuned.find(std::make_tuple(n_rows, nnz, r.B, std::min(r.n_v, kPanelMax),
                                               r.precision));
     if (it != ctx->tuned.end() && shape_supported(r.precision, it->second, ld)) return it->second;
@@ -295,14 +316,11 @@ void run_sweep(dos_ctx *ctx, const dos_csr *Adesc, SweepRequest &r, cudaStream_t
         val = v32;
     }
 
-    // vector panels
-    const int vpt = r.precision == DOS_PREC_F64 ? 2 : 4;
     const int esz = r.precision == DOS_PREC_F64 ? 8 : 4;
-    const int n_panels = (r.n_v + kPanelMax - 1) / kPanelMax;
-    const int panel_nv = (r.n_v + n_panels - 1) / n_panels;
-    const int ld = (panel_nv + vpt - 1) / vpt * vpt;
-
-    const Shape sh = choose_shape(ctx, r, Adesc, ld, A.n, A.nnz, s);
+    const Shape sh = choose_shape(ctx, r, Adesc, A.n, A.nnz, s);
+    // vector panels of the chosen width
+    const Panels pan = panels_of(r.n_v, sh.panel, r.precision);
+    const int n_panels = pan.n_panels, panel_nv = pan.panel_nv, ld = pan.ld;
     Plan plan = make_plan(r, A, sh, s);
 
     std::vector<double> c(B), inv_d(B);
@@ -407,7 +425,7 @@ void run_sweep(dos_ctx *ctx, const dos_csr *Adesc, SweepRequest &r, cudaStream_t
         (uint64_t)(uintptr_t)val, (uint64_t)A.n, (uint64_t)A.nnz, (uint64_t)B, (uint64_t)ld,
         (uint64_t)r.n_v, (uint64_t)r.M, r.seed, (uint64_t)r.opts.vec_offset, r.opts.batch_index,
         (uint64_t)sh.team, (uint64_t)sh.chunks, (uint64_t)sh.block, (uint64_t)plan.n_tiles,
-        (uint64_t)sh.staged, (uint64_t)sh.cb, (uint64_t)sh.depth,
+        (uint64_t)sh.staged, (uint64_t)sh.cb, (uint64_t)sh.depth, (uint64_t)sh.panel,
         (uint64_t)per_vec, (uint64_t)slots, (uint64_t)(uintptr_t)xb, (uint64_t)(uintptr_t)partial,
         (uint64_t)(uintptr_t)dotsum, (uint64_t)(uintptr_t)mu_dev, (uint64_t)(uintptr_t)mupv_dev,
         (uint64_t)(uintptr_t)tiles, (uint64_t)(uintptr_t)seg.row0, (uint64_t)(uintptr_t)status,
@@ -499,14 +517,12 @@ dos_kpm_opts default_opts() {
 // than 2x idle lanes, and tile counts of 1x to 32x the resident blocks, time
 // sweeps of 16 and 48 Chebyshev steps with CUDA events; the difference / 32 is
 // the per-step time (fixed per-call costs cancel).  Best of three runs (one when
-// a step takes more than 2 ms).
-// Row length (elements) of one vector panel of an n_v-vector sweep.
-static int panel_ld(int n_v, int precision) {
-    const int vpt = precision == DOS_PREC_F64 ? 2 : 4;
-    const int n_panels = (n_v + kPanelMax - 1) / kPanelMax;
-    const int panel_nv = (n_v + n_panels - 1) / n_panels;
-    return (panel_nv + vpt - 1) / vpt * vpt;
-}
+// a step takes more than 2 ms).  Vector panels narrower than 256 (launch.panel)
+// are not searched: on the lattice and on the power-law graph every narrower
+// width measured slower per step of all n_v vectors (each pass re-reads A and
+// pays the per-nonzero costs again), so they are left to callers short of
+// device memory.
+static int panel_ld(int n_v, int precision) { return panels_of(n_v, 0, precision).ld; }
 
 Shape tune_shape(dos_ctx *ctx, const dos_csr *A, int B, const int64_t *seg_rows, int n_v,
                  int precision, double *best_ms, cudaStream_t s) {
@@ -816,6 +832,7 @@ int dos_tune(dos_ctx *ctx, const dos_csr *A, int B, const int64_t *seg_rows, int
             best->depth = sh.staged == 2 ? tmag_depth(sh.block, sh.team, panel_ld(n_v, precision),
                                                       precision == DOS_PREC_F64 ? 8 : 4, sh.depth)
                                          : 0;
+            best->panel = 0;
         }
     });
 }

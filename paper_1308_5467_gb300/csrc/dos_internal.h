@@ -87,6 +87,7 @@ struct Shape {
                      // 3 direct loads with the tile's CSR staged (step_csrs_kernel)
     int cb = 16;     // bytes per chunk: 16, or 32 (direct loads, staged 0 or 3)
     int depth = 0;   // TMA gathers: batches in flight per team (2, 4, 8; 0: by shared memory)
+    int panel = 0;   // vectors per pass over A (0: up to 256)
 };
 
 // Cached CUDA graph for one sweep configuration.

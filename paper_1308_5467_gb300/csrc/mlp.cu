@@ -596,7 +596,7 @@ int dos_mlp_save(dos_mlp *mlp, const char *path, void *stream) {
         DOS_CUDA_TRY(cudaMemcpyAsync(host.data(), mlp->params, np * 4, cudaMemcpyDeviceToHost, s));
         DOS_CUDA_TRY(cudaMemcpyAsync(host.data() + np, mlp->m, 2 * np * 4, cudaMemcpyDeviceToHost,
                                      s));
-        DOS_CUDA_TRY(cudaStreamSynchronize(s));
+        check_status(mlp, s);   // synchronises; no checkpoint of a step whose products timed out
         std::vector<unsigned char> b;
         b.reserve(kHeaderBytes + (size_t)(12 * np) + 8);
         b.insert(b.end(), kMagic, kMagic + 8);

@@ -49,7 +49,7 @@ class dos_csr(C.Structure):
 class dos_launch(C.Structure):
     _fields_ = [("team", C.c_int32), ("chunks", C.c_int32), ("block", C.c_int32),
                 ("tiles", C.c_int32), ("staged", C.c_int32), ("chunk_bytes", C.c_int32),
-                ("depth", C.c_int32)]
+                ("depth", C.c_int32), ("panel", C.c_int32)]
 
 
 class dos_kpm_opts(C.Structure):
@@ -271,7 +271,7 @@ class Context:
         if launch:
             o.launch = dos_launch(*[int(launch.get(k, 0))
                                     for k in ("team", "chunks", "block", "tiles", "staged",
-                                              "chunk_bytes", "depth")])
+                                              "chunk_bytes", "depth", "panel")])
         return o
 
     def dos_kpm_moments(self, A: CSRArrays, lb: float, ub: float, M: int, n_v: int, seed: int,
@@ -317,7 +317,8 @@ class Context:
                                   C.byref(best), C.byref(ms), _stream_of(A.row_ptr)))
         return {"team": best.team, "chunks": best.chunks, "block": best.block,
                 "tiles": best.tiles, "staged": best.staged,
-                "chunk_bytes": best.chunk_bytes, "depth": best.depth}, ms.value
+                "chunk_bytes": best.chunk_bytes, "depth": best.depth,
+                "panel": best.panel}, ms.value
 
     def dos_reconstruct(self, mu, M: int, damping="jackson", lb: float = -1.0, ub: float = 1.0,
                         t=None, N_t: int = 1000, phi_hat=None, phi_lambda=None,

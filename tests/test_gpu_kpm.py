@@ -2,8 +2,9 @@
 
 Every comparison runs the library through its C ABI (ctypes binding) and the
 oracle on the same seeded inputs.  Tolerances (tests/tolerances.py, with the
-error model): FP64 form 1e-12 absolute per moment; FP32 form 2 u sqrt(k+1),
-u = 2^-24, against the FP64 oracle run on the FP32-rounded matrix values.
+error model): FP64 form 1e-12 absolute per moment; FP32 form
+u sqrt(k+1) (1/2 + 40/sqrt(N)), u = 2^-24, N the (row, vector) terms a moment
+averages, against the FP64 oracle run on the FP32-rounded matrix values.
 """
 import numpy as np
 import pytest
@@ -136,6 +137,54 @@ def test_vector_panels_large_n_v(ctx, precision):
     tol, tolt = (TOL64, TOL64) if precision == "f64" else (tol32(M, A.n), tol32(M, A.n * n_v))
     assert np.all(np.abs(pv - ref) <= tol), fp32_ratio(pv, ref)
     assert np.all(np.abs(mu - ref.mean(axis=0)) <= tolt), fp32_ratio(mu, ref.mean(axis=0))
+
+
+@pytest.mark.parametrize("precision", ["f64", "f32"])
+@pytest.mark.parametrize("n_v,launch", [
+    (64, {"panel": 4}), (64, {"panel": 8}), (64, {"panel": 16}),
+    (64, {"panel": 16, "staged": 3}), (64, {"panel": 16, "staged": 4}),
+    (64, {"panel": 16, "chunk_bytes": 32}), (64, {"panel": 32, "tiles": 5}),
+    (20, {"panel": 4}), (20, {"panel": 8}), (20, {"panel": 16})])
+def test_narrow_vector_panels_parity(ctx, precision, n_v, launch):
+    """Vectors swept in narrower panels (launch.panel: ceil(n_v / w) passes over A
+    of equal width, the last possibly narrower; 20 vectors in panels of 8 are three
+    of 7): per-vector and total moments against the oracle, on a lattice and on a
+    random matrix with empty rows and a dense row; the totals agree with the
+    one-pass sweep up to the order of their FP64 sums."""
+    dtype = np.float64 if precision == "f64" else np.float32
+    for A, lb, ub in ((anderson_3d(11, 6.0, seed=4), -9.6, 9.6),
+                      (random_symmetric(300, 0.03, 5, empty_rows=5, long_row=41), None, None)):
+        Aw = A.astype(dtype)
+        if lb is None:
+            lb, ub = obounds.bounds(A, "gershgorin", pad_frac=0.01)
+        M = 41
+        pv = np.empty((n_v, M + 1))
+        mu = ctx.dos_kpm_moments(dev(Aw), lb, ub, M, n_v, seed=6, precision=precision,
+                                 launch=launch, mu_per_vec=pv)
+        mu_tot = ctx.dos_kpm_moments(dev(Aw), lb, ub, M, n_v, seed=6, precision=precision,
+                                     launch=launch)
+        one_pass = ctx.dos_kpm_moments(dev(Aw), lb, ub, M, n_v, seed=6, precision=precision)
+        ref = okpm.kpm_moments_per_vector(Aw, lb, ub, M, n_v, seed=6)
+        tol, tolt = (TOL64, TOL64) if precision == "f64" else (tol32(M, A.n),
+                                                               tol32(M, A.n * n_v))
+        assert np.all(np.abs(pv - ref) <= tol), fp32_ratio(pv, ref)
+        assert np.all(np.abs(mu - ref.mean(axis=0)) <= tolt), fp32_ratio(mu, ref.mean(0))
+        assert np.all(np.abs(mu_tot - ref.mean(axis=0)) <= tolt), fp32_ratio(mu_tot, ref.mean(0))
+        if precision == "f64":
+            assert np.abs(mu_tot - one_pass).max() < 1e-13
+
+
+def test_tuned_shape_with_narrower_panels(ctx):
+    """The autotuner's shape (one pass: panel 0) and the same shape with the vectors
+    split into panels of 16 both match the oracle."""
+    A = anderson_3d(12, 5.0, seed=2).astype(np.float32)
+    shape, ms = ctx.dos_tune(dev(A), 48, "f32")
+    assert shape["panel"] == 0 and ms > 0
+    ref = okpm.kpm_moments(A, -9.0, 9.0, 30, 48, seed=2)
+    for launch in (shape, {**{k: v for k, v in shape.items() if k != "tiles"}, "panel": 16}):
+        mu = ctx.dos_kpm_moments(dev(A), -9.0, 9.0, 30, 48, seed=2, precision="f32",
+                                 launch=launch)
+        assert np.all(np.abs(mu - ref) <= tol32(30, A.n * 48)), fp32_ratio(mu, ref)
 
 
 def test_vec_offset_shards_union(ctx):
