@@ -640,7 +640,7 @@ def run_batched(args, w, world, rank, local, device):
             ms = float(t.item())
         return ms, out, prof
 
-    ctx.dos_tune(A, n_v, prec, seg_rows=seg)   # autotuned launch shape, cached in the context
+    tuned_b = ctx.dos_tune(A, n_v, prec, seg_rows=seg)[0]   # autotuned shape, cached in ctx
     with ClockSampler(gpu_id_for(local)) as clk:
         ms, (lb, ub, mu), prof = timed(lambda: step(A, prec), args.steps, args.warmup, True)
     value = units * world / (ms * 1e-3)
@@ -721,10 +721,12 @@ def run_batched(args, w, world, rank, local, device):
             "dtype": "f32" if prec == "f32" else "f64", "data": "synthetic",
             "config": {"workload": "batched", "desc": w["desc"], "B": len(mats), "n": n_rows,
                        "nnz": nnz, "M": M, "n_v": n_v, "precision": prec, "pdl": not args.no_pdl,
+                       "launch": tuned_b,
                        "l2": "inputs larger than L2: %.0f MB per fused step" % (alg / 1e6)},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"],
                          "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"], "traffic": None,
                          "peak_source": peak_kind, "launch_ms": launch_ms,
+                         "kernel": step_kernel_name(tuned_b, prec),
                          "algorithmic_bytes_per_launch": alg},
             "forms": forms, "e1_sampled": float(np.mean(errs[prec])),
             "gpu_launches": prof["launches"], "clocks": clk.summary(), "e2e": e2e,

@@ -247,6 +247,7 @@ struct StepParams {
     long long spin_cycles;  // staged kernel: wait limit in SM clock cycles
     int stall_test; // staged kernel, tests only: over-count the expected bytes so a
                     // wait never completes and must run out
+    int rev;        // direct kernel: walk each tile's rows from its last row down
 };
 
 // Deterministic block reduction of one accumulator set into out[0..pv).
@@ -368,8 +369,11 @@ __device__ __forceinline__ void block_reduce_scalar(const Acc &acc, double *out,
 // FIRST: the step X_1 = B X_0 (no X_{k-1}; also accumulates X_0 . X_0).  Being a
 // template parameter, the 249-of-250 ordinary steps carry no branch on it, which
 // frees registers and lets the compiler schedule the gathers of a batch together.
+// Threads that hold at most 32 bytes of a row (CPT * CB <= 32) fit in 64 registers:
+// four blocks per SM; wider ones keep their batch of gathers in up to 80: three.
 template <typename T, int G, int CPT, bool PV, int CB, bool FIRST>
-__global__ void __launch_bounds__(kBlock, 3) step_kernel(const StepParams<T> p) {
+__global__ void __launch_bounds__(kBlock, CPT * CB <= 32 ? 4 : 3)
+    step_kernel(const StepParams<T> p) {
     constexpr int VPT = CB / (int)sizeof(T);  // vector entries per chunk
     using Acc = typename Traits<T>::Acc;
     constexpr int TPW = 32 / G;  // teams per warp
@@ -415,13 +419,19 @@ __global__ void __launch_bounds__(kBlock, 3) step_kernel(const StepParams<T> p) 
 #pragma unroll
     for (int cc = 0; cc < CPT; ++cc) valid[cc] = (g + cc * G) < p.n_chunks;
 
-    int row = rb + team;
+    // Row idx of the tile (idx = team, team + n_teams, ...) is tile row rb + idx, or
+    // re - 1 - idx on steps that walk the tile backwards: consecutive steps then meet
+    // first the rows the previous step wrote last, while they are still in L2.
+    const int cnt = re - rb;
+    const int rdir = p.rev ? -1 : 1, rorg = p.rev ? re - 1 : rb;
+    int idx = team;
+    int row = rorg + rdir * idx;
     int e0 = 0, e1 = 0;
-    if (row < re) {
+    if (idx < cnt) {
         e0 = __ldg(row_ptr + row);
         e1 = __ldg(row_ptr + row + 1);
     }
-    while (row < re) {
+    while (idx < cnt) {
         const size_t roff = (size_t)row * ld;
         T xk[CPT][VPT], xo[CPT][VPT];
 #pragma unroll
@@ -432,9 +442,10 @@ __global__ void __launch_bounds__(kBlock, 3) step_kernel(const StepParams<T> p) 
                 if (!first) load_chunk_prev(xn + roff + off, xo[cc]);
             }
         }
-        const int nrow = row + n_teams;
+        const int nidx = idx + n_teams;
+        const int nrow = rorg + rdir * nidx;
         int ne0 = 0, ne1 = 0;
-        if (nrow < re) {
+        if (nidx < cnt) {
             ne0 = __ldg(row_ptr + nrow);
             ne1 = __ldg(row_ptr + nrow + 1);
         }
@@ -496,6 +507,7 @@ __global__ void __launch_bounds__(kBlock, 3) step_kernel(const StepParams<T> p) 
             acc_add(accS[0][0], ss);
             if (first) acc_add(acc0[0][0], zz);
         }
+        idx = nidx;
         row = nrow;
         e0 = ne0;
         e1 = ne1;
@@ -1704,6 +1716,7 @@ static void launch_step_t(const SweepArgs &a, int k, int slot, cudaStream_t s) {
     p.status = a.status;
     p.spin_cycles = a.spin_cycles > 0 ? a.spin_cycles : 2000000000LL;  // ~1 s
     p.stall_test = a.stall_test;
+    p.rev = k & 1;
     if (a.shape.staged == 1) {
         auto fn = pick_staged<T>(a.shape.team, a.shape.chunks, a.per_vec != 0);
         if (!fn) throw Error{DOS_EINVAL, "unsupported staged launch shape"};
