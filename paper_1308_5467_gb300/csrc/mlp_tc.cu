@@ -3,32 +3,37 @@
 //   C = epilogue(A B^T),  A: M x K and B: N x K bfloat16, row-major with K
 //   contiguous (leading dimensions multiples of 8 elements), FP32 accumulation.
 //
-// One CTA of 128 threads computes a 128 x 128 tile of C:
-//   * one thread streams K-slices of 64 elements (128 bytes of a row) of A and B
-//     into a ring of shared-memory stages with TMA (cp.async.bulk.tensor, 128-byte
-//     swizzle, rows past M, N or K filled with zeros), each completing on the
-//     stage's "full" mbarrier;
-//   * the same thread issues tcgen05.mma (kind::f16: BF16 operands, FP32
+// Persistent, warp-specialised kernel: one CTA of ten warps per SM walks the
+// 128 x 128 output tiles t = blockIdx.x, blockIdx.x + gridDim.x, ... (row-block
+// major, so CTAs running together share the A rows of a row block in L2):
+//   * warp 0 (one thread) streams K-slices of 64 elements (128 bytes of a row) of
+//     A and B into a ring of four shared-memory stages with TMA
+//     (cp.async.bulk.tensor, 128-byte swizzle, rows past M, N or K filled with
+//     zeros), each completing on the stage's "full" mbarrier;
+//   * warp 1 (one thread) issues tcgen05.mma (kind::f16: BF16 operands, FP32
 //     accumulator in tensor memory, M = N = 128, K = 16 per instruction, four per
-//     slice) and tcgen05.commit to the stage's "empty" mbarrier, which fires when
-//     the MMAs reading the stage are done; the stage of the previous slice is
-//     refilled while the current slice's MMAs run;
-//   * a last commit to "done" releases the four warps, which read the
-//     accumulator with tcgen05.ld (warp w owns tensor-memory lanes 32w..32w+31,
-//     the tile's rows) into an FP32 tile in the (now idle) stage memory, padded to
-//     129 columns so that neither a thread writing its row nor a warp reading a
-//     row or a column conflicts on banks; the epilogue then leaves the tile in two
-//     coalesced passes, row by row for the row-major outputs (bias and mask read
-//     along the row) and column by column for the transposed bf16 copy.
-// Every mbarrier wait is bounded (spin cycles): a wait that runs out sets status
-// bit 8, the CTA waits (bounded again) for what it issued, frees its tensor
-// memory and skips the stores.
+//     slice) and tcgen05.commit to the stage's "empty" mbarrier, which frees the
+//     stage when its MMAs are done; two accumulators (2 x 128 tensor-memory
+//     columns) alternate between tiles, and a commit to the accumulator's "full"
+//     mbarrier hands a finished tile to the epilogue;
+//   * warps 2-9 read the accumulator with tcgen05.ld (warp w reaches tensor-memory
+//     lanes 32 (w mod 4) .. +31, the tile's rows, and takes half of the columns),
+//     apply the epilogue and store each thread's 32 consecutive columns with
+//     16-byte vector stores (the transposed bf16 copy column by column,
+//     consecutive lanes on consecutive rows), then release the accumulator on its
+//     "empty" mbarrier -- so one tile's epilogue overlaps the next tile's loads
+//     and products.
+// Every mbarrier wait is bounded (spin cycles) and also gives up when another
+// role has: a wait that runs out sets status bit 8 and an abort flag that ends
+// every role's loop; the CTA then waits (bounded again) for the copies and
+// products it issued, frees its tensor memory and returns.
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <cudaTypedefs.h>
 #include <stdint.h>
 
+#include <algorithm>
 #include <mutex>
 
 #include "dos_internal.h"
@@ -38,12 +43,14 @@ namespace {
 
 typedef __nv_bfloat16 bf16;
 
-// Three stages (99 KB of shared memory) leave room for two CTAs per SM, so one
-// tile's epilogue overlaps another's loads and products.
-constexpr int kBM = 128, kBN = 128, kBK = 64, kStages = 3, kThreads = 128;
+// Four stages of operands (128 KB of shared memory): one CTA per SM (six stages
+// measured the same).  Eight epilogue warps: two per tensor-memory lane quadrant,
+// each taking half the columns.
+constexpr int kBM = 128, kBN = 128, kBK = 64, kStages = 4, kEpiWarps = 8;
+constexpr int kThreads = 64 + 32 * kEpiWarps;
 constexpr uint32_t kTileBytes = kBM * kBK * 2;     // one operand slice: 128 rows x 128 B
 constexpr uint32_t kStageBytes = 2 * kTileBytes;   // A and B (kBN == kBM)
-constexpr uint32_t kTmemCols = kBN;                // FP32 accumulator: one column per n
+constexpr uint32_t kTmemCols = 2 * kBN;            // two FP32 accumulators, one column per n
 constexpr size_t kSmemBytes = 1024 + (size_t)kStages * kStageBytes + 256;
 
 // Instruction descriptor of tcgen05.mma .kind::f16: D FP32 (bits 4-5 = 1), A and B
@@ -75,6 +82,9 @@ __device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(saddr(bar)),
                  "r"(bytes)
                  : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(saddr(bar)) : "memory");
 }
 __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
     uint32_t done;
@@ -150,137 +160,252 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
     for (int j = 0; j < 32; ++j) v[j] = __uint_as_float(r[j]);
 }
 
+// Bounded wait that also gives up once another role has set the abort flag.
+__device__ __forceinline__ bool mbar_wait_or_abort(uint64_t *bar, uint32_t parity,
+                                                   long long limit, volatile int *abort) {
+    const long long t0 = clock64();
+    while (!mbar_try_wait(bar, parity)) {
+        if (*abort) return false;
+        if (clock64() - t0 > limit) return false;
+    }
+    return true;
+}
+__device__ __forceinline__ void fail(volatile int *abort, int *status) {
+    *abort = 1;
+    atomicOr(status, 8);
+}
+__device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
+    const __nv_bfloat162 h = __floats2bfloat162_rn(lo, hi);
+    return *reinterpret_cast<const uint32_t *>(&h);
+}
+
+// Epilogue of one thread: row `row` (< M), the 32 columns c0 .. c0+31 (those < N)
+// of the accumulator in v.
 template <int EPI>
-__global__ void __launch_bounds__(kThreads, 2)
+__device__ __forceinline__ void epilogue_row(const TcGemm &g, int row, int c0, float (&v)[32]) {
+    const int ncol = min(32, g.N - c0);
+    const bool full = ncol == 32;
+    if (EPI == TC_EPI_BIAS_RELU_BF16 || EPI == TC_EPI_BIAS_F32) {
+        float b[32];
+        if (full && (((uintptr_t)(g.bias + c0) & 15) == 0)) {
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                const float4 b4 = __ldg(reinterpret_cast<const float4 *>(g.bias + c0) + q);
+                b[4 * q] = b4.x;
+                b[4 * q + 1] = b4.y;
+                b[4 * q + 2] = b4.z;
+                b[4 * q + 3] = b4.w;
+            }
+        } else {
+#pragma unroll
+            for (int j = 0; j < 32; ++j) b[j] = j < ncol ? __ldg(g.bias + c0 + j) : 0.f;
+        }
+#pragma unroll
+        for (int j = 0; j < 32; ++j)
+            v[j] = EPI == TC_EPI_BIAS_RELU_BF16 ? fmaxf(v[j] + b[j], 0.f) : v[j] + b[j];
+    } else if (EPI == TC_EPI_MASK) {
+        const bf16 *mrow = (const bf16 *)g.mask + (size_t)row * g.ldm + c0;
+        if (full && ((g.ldm & 7) == 0) && (((uintptr_t)g.mask & 15) == 0)) {
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const uint4 m = __ldg(reinterpret_cast<const uint4 *>(mrow) + q);
+                const uint32_t w[4] = {m.x, m.y, m.z, m.w};
+#pragma unroll
+                for (int h = 0; h < 4; ++h) {
+                    const __nv_bfloat162 p2 = *reinterpret_cast<const __nv_bfloat162 *>(&w[h]);
+                    if (!(__low2float(p2) > 0.f)) v[q * 8 + 2 * h] = 0.f;
+                    if (!(__high2float(p2) > 0.f)) v[q * 8 + 2 * h + 1] = 0.f;
+                }
+            }
+        } else {
+#pragma unroll
+            for (int j = 0; j < 32; ++j)
+                if (j < ncol && !(__bfloat162float(mrow[j]) > 0.f)) v[j] = 0.f;
+        }
+    }
+    const size_t o = (size_t)row * g.ldc + c0;
+    // FP32 output
+    if (EPI != TC_EPI_BIAS_RELU_BF16) {
+        float *dst = g.Cf + o;
+        if (full && ((g.ldc & 3) == 0) && (((uintptr_t)g.Cf & 15) == 0)) {
+#pragma unroll
+            for (int q = 0; q < 8; ++q)
+                reinterpret_cast<float4 *>(dst)[q] =
+                    make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+        } else {
+#pragma unroll
+            for (int j = 0; j < 32; ++j)
+                if (j < ncol) dst[j] = v[j];
+        }
+    }
+    // bf16 output (always for BIAS_RELU_BF16; for MASK when Cb is given)
+    if (EPI == TC_EPI_BIAS_RELU_BF16 || (EPI == TC_EPI_MASK && g.Cb)) {
+        bf16 *dst = (bf16 *)g.Cb + o;
+        if (full && ((g.ldc & 7) == 0) && (((uintptr_t)g.Cb & 15) == 0)) {
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+                reinterpret_cast<uint4 *>(dst)[q] = make_uint4(
+                    pack_bf16(v[8 * q], v[8 * q + 1]), pack_bf16(v[8 * q + 2], v[8 * q + 3]),
+                    pack_bf16(v[8 * q + 4], v[8 * q + 5]), pack_bf16(v[8 * q + 6], v[8 * q + 7]));
+        } else {
+#pragma unroll
+            for (int j = 0; j < 32; ++j)
+                if (j < ncol) dst[j] = __float2bfloat16_rn(v[j]);
+        }
+    }
+}
+
+template <int EPI>
+__global__ void __launch_bounds__(kThreads, 1)
     gemm_tc_kernel(const __grid_constant__ CUtensorMap map_a,
                    const __grid_constant__ CUtensorMap map_b, const TcGemm g) {
     extern __shared__ uint8_t smem_raw[];
-    __shared__ int s_fail;
+    __shared__ volatile int s_abort;
+    __shared__ int s_issued, s_consumed;
     uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     uint64_t *full = (uint64_t *)(smem + (size_t)kStages * kStageBytes);
     uint64_t *empty = full + kStages;
-    uint64_t *done = empty + kStages;
-    uint32_t *tmem_slot = (uint32_t *)(done + 1);
+    uint64_t *acc_full = empty + kStages;   // 2: accumulator b holds a finished tile
+    uint64_t *acc_empty = acc_full + 2;     // 2: the epilogue has read accumulator b
+    uint64_t *drain = acc_empty + 2;        // every MMA issued has completed
+    uint32_t *tmem_slot = (uint32_t *)(drain + 1);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int m0 = blockIdx.y * kBM, n0 = blockIdx.x * kBN;
     const int nk = (g.K + kBK - 1) / kBK;
+    const int tiles_n = (g.N + kBN - 1) / kBN;
+    const int n_tiles = ((g.M + kBM - 1) / kBM) * tiles_n;
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < kStages; ++s) {
             mbar_init(&full[s], 1);
             mbar_init(&empty[s], 1);
         }
-        mbar_init(done, 1);
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&acc_full[b], 1);
+            mbar_init(&acc_empty[b], kEpiWarps);   // one arrival per epilogue warp
+        }
+        mbar_init(drain, 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-        s_fail = 0;
+        s_abort = 0;
+        s_issued = 0;
+        s_consumed = 0;
     }
-    if (warp == 0) tmem_alloc(tmem_slot, kTmemCols);
+    if (warp == 1) tmem_alloc(tmem_slot, kTmemCols);
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = *tmem_slot;
 
-    if (threadIdx.x == 0) {
-        auto load = [&](int kc) {
-            const int s = kc % kStages;
-            uint8_t *sa = smem + (size_t)s * kStageBytes;
-            mbar_expect_tx(&full[s], kStageBytes);
-            tma_load_2d(sa, &map_a, kc * kBK, m0, &full[s]);
-            tma_load_2d(sa + kTileBytes, &map_b, kc * kBK, n0, &full[s]);
-        };
-        const int pre = nk < kStages ? nk : kStages;
-        for (int kc = 0; kc < pre; ++kc) load(kc);
-        int issued = pre, consumed = 0;
-        bool ok = true;
-        for (int kc = 0; kc < nk; ++kc) {
-            const int s = kc % kStages;
-            if (!mbar_wait(&full[s], (kc / kStages) & 1, g.spin)) {
-                ok = false;
-                break;
+    if (warp == 0) {
+        // ---- producer: TMA loads of A and B slices into the stage ring ----
+        if (lane == 0) {
+            int it = 0;
+            for (int t = blockIdx.x; t < n_tiles && !s_abort; t += gridDim.x) {
+                const int m0 = (t / tiles_n) * kBM, n0 = (t % tiles_n) * kBN;
+                for (int kc = 0; kc < nk; ++kc, ++it) {
+                    const int s = it % kStages;
+                    if (!mbar_wait_or_abort(&empty[s], ((it / kStages) & 1) ^ 1, g.spin, &s_abort)) {
+                        if (!s_abort) fail(&s_abort, g.status);
+                        break;
+                    }
+                    uint8_t *sa = smem + (size_t)s * kStageBytes;
+                    mbar_expect_tx(&full[s], kStageBytes);
+                    tma_load_2d(sa, &map_a, kc * kBK, m0, &full[s]);
+                    tma_load_2d(sa + kTileBytes, &map_b, kc * kBK, n0, &full[s]);
+                    s_issued = it + 1;
+                }
             }
-            consumed = kc + 1;
-            const uint32_t sa = saddr(smem + (size_t)s * kStageBytes), sb = sa + kTileBytes;
-#pragma unroll
-            for (int kk = 0; kk < kBK / 16; ++kk)
-                mma_bf16(tmem, sw128_desc(sa + kk * 32), sw128_desc(sb + kk * 32),
-                         (kc | kk) != 0 ? 1u : 0u);
-            mma_commit(&empty[s]);
-            if (kc >= 1 && kc - 1 + kStages < nk) {  // refill the previous slice's stage
-                const int p = kc - 1;
-                if (!mbar_wait(&empty[p % kStages], (p / kStages) & 1, g.spin)) {
+        }
+        __syncwarp();
+    } else if (warp == 1) {
+        // ---- MMA issuer: products of each tile into accumulator (tile count & 1) ----
+        if (lane == 0) {
+            int it = 0, tc = 0;
+            bool ok = true;
+            for (int t = blockIdx.x; t < n_tiles && ok && !s_abort; t += gridDim.x, ++tc) {
+                const int b = tc & 1;
+                if (!mbar_wait_or_abort(&acc_empty[b], ((tc >> 1) & 1) ^ 1, g.spin, &s_abort)) {
                     ok = false;
                     break;
                 }
-                load(p + kStages);
-                issued = p + kStages + 1;
-            }
-        }
-        mma_commit(done);  // fires once every MMA issued above has completed
-        if (!ok) {
-            atomicOr(g.status, 8);
-            s_fail = 1;
-            for (int kc = consumed; kc < issued; ++kc)  // loads still writing shared memory
-                mbar_wait(&full[kc % kStages], (kc / kStages) & 1, g.spin);
-        }
-    }
-    bool waited = mbar_wait(done, 0, g.spin);
-    if (!waited) waited = mbar_wait(done, 0, g.spin);  // once more before giving up
-    if (!waited && lane == 0) atomicOr(g.status, 8);
-    const int bad = __syncthreads_or(!waited || s_fail);
-    tc_fence_after();
-
-    constexpr int kLd = kBN + 1;  // staged tile row stride (floats)
-    float *tile = reinterpret_cast<float *>(smem);
-    if (!bad) {
-        const int r = warp * 32 + lane;  // tile row of this thread's TMEM lane
-#pragma unroll 1
-        for (int c = 0; c < kBN / 32; ++c) {
-            if (n0 + c * 32 >= g.N) break;  // warp-uniform
-            float v[32];
-            tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(c * 32), v);
+                tc_fence_after();
+                const uint32_t d = tmem + (uint32_t)(b * kBN);
+                for (int kc = 0; kc < nk; ++kc, ++it) {
+                    const int s = it % kStages;
+                    if (!mbar_wait_or_abort(&full[s], (it / kStages) & 1, g.spin, &s_abort)) {
+                        ok = false;
+                        break;
+                    }
+                    tc_fence_after();
+                    s_consumed = it + 1;
+                    const uint32_t sa = saddr(smem + (size_t)s * kStageBytes), sb = sa + kTileBytes;
 #pragma unroll
-            for (int j = 0; j < 32; ++j) tile[r * kLd + c * 32 + j] = v[j];
+                    for (int kk = 0; kk < kBK / 16; ++kk)
+                        mma_bf16(d, sw128_desc(sa + kk * 32), sw128_desc(sb + kk * 32),
+                                 (kc | kk) != 0 ? 1u : 0u);
+                    mma_commit(&empty[s]);
+                }
+                if (!ok) break;
+                mma_commit(&acc_full[b]);
+            }
+            if (!ok && !s_abort) fail(&s_abort, g.status);
+            mma_commit(drain);  // fires once every MMA issued above has completed
+        }
+        __syncwarp();
+    } else {
+        // ---- epilogue: warps 2-9; warp w reads accumulator lanes 32 (w % 4) .. +31
+        // (tcgen05.ld reaches only its own quadrant) and column chunks 2h, 2h + 1 of
+        // the four, h = (w - 2) / 4 ----
+        const int quad = warp & 3, half = (warp - 2) >> 2;
+        int tc = 0;
+        for (int t = blockIdx.x; t < n_tiles; t += gridDim.x, ++tc) {
+            const int b = tc & 1;
+            const bool got = mbar_wait_or_abort(&acc_full[b], (tc >> 1) & 1, g.spin, &s_abort);
+            if (!__all_sync(0xffffffffu, got)) {
+                if (lane == 0 && !s_abort) fail(&s_abort, g.status);
+                break;
+            }
+            tc_fence_after();
+            const int m0 = (t / tiles_n) * kBM, n0 = (t % tiles_n) * kBN;
+            const int row = m0 + quad * 32 + lane;
+#pragma unroll 1
+            for (int c = 2 * half; c < 2 * half + 2; ++c) {
+                const int c0 = n0 + c * 32;
+                if (c0 >= g.N) break;  // warp-uniform
+                float v[32];
+                tmem_ld32(tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(b * kBN + c * 32), v);
+                if (row < g.M) {
+                    epilogue_row<EPI>(g, row, c0, v);
+                    if (g.Ct) {  // transposed bf16 copy: lanes write consecutive rows
+#pragma unroll
+                        for (int j = 0; j < 32; ++j)
+                            if (c0 + j < g.N)
+                                ((bf16 *)g.Ct)[(size_t)(c0 + j) * g.ldt + row] =
+                                    __float2bfloat16_rn(v[j]);
+                    }
+                }
+            }
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&acc_empty[b]);
         }
     }
+
     __syncthreads();
-    if (!bad) {
-        const int rows = min(kBM, g.M - m0), cols = min(kBN, g.N - n0);
-        // row-major outputs: a warp walks one row, lanes over consecutive columns
-        for (int idx = threadIdx.x; idx < rows * kBN; idx += kThreads) {
-            const int rr = idx / kBN, cc = idx - rr * kBN;
-            if (cc >= cols) continue;
-            const int row = m0 + rr, col = n0 + cc;
-            float x = tile[rr * kLd + cc];
-            const size_t o = (size_t)row * g.ldc + col;
-            if (EPI == TC_EPI_BIAS_RELU_BF16) {
-                x = fmaxf(x + g.bias[col], 0.f);
-                ((bf16 *)g.Cb)[o] = __float2bfloat16_rn(x);
-            } else if (EPI == TC_EPI_BIAS_F32) {
-                g.Cf[o] = x + g.bias[col];
-            } else if (EPI == TC_EPI_MASK) {
-                x = __bfloat162float(((const bf16 *)g.mask)[(size_t)row * g.ldm + col]) > 0.f
-                        ? x : 0.f;
-                g.Cf[o] = x;
-                if (g.Cb) ((bf16 *)g.Cb)[o] = __float2bfloat16_rn(x);
-            } else {
-                g.Cf[o] = x;
-            }
-            tile[rr * kLd + cc] = x;  // the epilogue's value, for the transposed pass
+    // Teardown: wait (bounded) for the products and copies this CTA issued, then
+    // free the tensor memory.
+    if (threadIdx.x == 32) {
+        if (!mbar_wait(drain, 0, g.spin)) {
+            if (!mbar_wait(drain, 0, g.spin)) atomicOr(g.status, 8);
         }
-        if (g.Ct) {
-            __syncthreads();
-            // transposed bf16 copy: a warp walks one column, lanes over consecutive rows
-            for (int idx = threadIdx.x; idx < cols * kBM; idx += kThreads) {
-                const int cc = idx / kBM, rr = idx - cc * kBM;
-                if (rr >= rows) continue;
-                ((bf16 *)g.Ct)[(size_t)(n0 + cc) * g.ldt + m0 + rr] =
-                    __float2bfloat16_rn(tile[rr * kLd + cc]);
-            }
-        }
+    }
+    if (threadIdx.x == 0 && s_abort) {
+        for (int it = s_consumed; it < s_issued; ++it)  // loads still writing shared memory
+            mbar_wait(&full[it % kStages], (it / kStages) & 1, g.spin);
     }
     tc_fence_before();
     __syncthreads();
-    if (warp == 0) tmem_dealloc(tmem, kTmemCols);
+    tc_fence_after();
+    if (warp == 1) tmem_dealloc(tmem, kTmemCols);
 }
 
 using EncodeFn = PFN_cuTensorMapEncodeTiled_v12000;
@@ -327,7 +452,14 @@ void launch_epi(const CUtensorMap &ma, const CUtensorMap &mb, const TcGemm &g, c
                                     (int)kSmemBytes);
     });
     DOS_CUDA_TRY(attr);
-    const dim3 grid((g.N + kBN - 1) / kBN, (g.M + kBM - 1) / kBM);
+    static int sms = 0;
+    if (!sms) {
+        int dev = 0;
+        DOS_CUDA_TRY(cudaGetDevice(&dev));
+        DOS_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    }
+    const int64_t tiles = (int64_t)((g.N + kBN - 1) / kBN) * ((g.M + kBM - 1) / kBM);
+    const int grid = (int)std::min<int64_t>(tiles, sms);
     gemm_tc_kernel<EPI><<<grid, kThreads, kSmemBytes, s>>>(ma, mb, g);
     DOS_LAUNCHED();
 }
