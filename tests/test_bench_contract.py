@@ -60,3 +60,15 @@ def test_cpu_baseline_reports_all_cores_and_one():
     assert cb["cores"] >= 1 and "start vectors" in cb["sample"]
     st = cb["single_thread"]
     assert st["cores"] == 1 and st["value"] > 0 and "1 thread" in st["sample"]
+
+
+def test_panel_geometry_matches_the_library_rule():
+    """Passes of at most w = min(panel or 256, 256) vectors, equal widths (the last may
+    be narrower), rows padded to whole 16-byte chunks -- the rule of launch.panel."""
+    import bench
+    assert bench.panel_geometry(256, 0, "f32") == (1, 256, 256)
+    assert bench.panel_geometry(20, 8, "f32") == (3, 7, 8)
+    assert bench.panel_geometry(700, 0, "f32") == (3, 234, 236)
+    assert bench.panel_geometry(700, 0, "f64") == (3, 234, 234)
+    assert bench.panel_geometry(64, 16, "f64") == (4, 16, 16)
+    assert bench.panel_geometry(5, 4096, "f32") == (1, 5, 8)
