@@ -286,12 +286,12 @@ int dos_kpm_moments_batched(dos_ctx *ctx, const dos_csr *A, int B, const int64_t
  * run -- applications whose device memory is reserved up front by their own
  * pool allocator (so a library's cudaMalloc fails or evicts the pool's cache),
  * and services held to a fixed memory budget or latency target, where
- * cudaMalloc / cudaFree may synchronise the device.  It computes the same moments mu_0..mu_M as
- * dos_kpm_moments (single matrix, start-vector counter b = 0, vector offset
- * 0) but keeps all intermediates in one fixed 64 MiB device array that is part
- * of the library image (every GPU that loads the library holds it until the
- * process exits), so the caller passes only inputs and outputs and no
- * context is needed.  It works on the calling thread's current device.
+ * cudaMalloc / cudaFree may synchronise the device.  It computes the same
+ * moments mu_0..mu_M as dos_kpm_moments (single matrix, start-vector counter
+ * b = 0, vector offset 0) but keeps all intermediates in one fixed 64 MiB
+ * device array that is part of the library image (every GPU that loads the
+ * library holds it until the process exits), so the caller passes only inputs
+ * and outputs and no context is needed.  It works on the calling thread's current device.
  *   A: all three arrays in DEVICE memory (checked: a host array returns
  *      DOS_EINVAL before any work is queued); values FP64 for DOS_PREC_F64,
  *      FP32 for DOS_PREC_F32_ACC64 (no conversion copy is made).
@@ -302,8 +302,9 @@ int dos_kpm_moments_batched(dos_ctx *ctx, const dos_csr *A, int B, const int64_t
  *      work is queued.
  *   The first call on a device looks up the array's device address with
  *   cudaGetSymbolAddress (in host code the array's name is only a stand-in for
- *   it); make that first call before any stream capture.  Every call uses the same array and leaves its contents behind
- *   (the kernels re-initialise what they read); calls that overlap on the GPU
+ *   it); make that first call before any stream capture.  Every call uses the
+ *   same array and leaves its contents behind (the kernels re-initialise what
+ *   they read); calls that overlap on the GPU
  *   -- from several host threads or streams -- race on it and must be
  *   serialised by the caller.  Synchronises `stream` (to check the CSR
  *   structure and the spectrum).
